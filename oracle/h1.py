@@ -1,0 +1,337 @@
+"""Oracle: randomized H^1 compression by peeling with graph-coloured test matrices.
+
+TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
+
+Follows Algorithm 4.1 (randomized compression of an H^1 matrix) level by level,
+with the per-block factorisation of Algorithm 2.1 (two randomized samples), the
+leaf extraction of Section 4.1.3, the apply of the compressed operator and the
+relative-error estimate of Section 5.  All arithmetic is FP64 NumPy.  All index
+sets refer to the Morton-permuted point order of oracle.tree.
+
+Readings of points where the paper is silent, garbled or inconsistent:
+  * Peel (Alg. 4.1 writes A^(l); Sec. 4.1.2 subtracts A^(2) at level 3): the
+    samples of level l are Y = A Omega - A^(l-1) Omega, with A^(l-1) the sum of
+    the factors of all levels 2..l-1; the leaf step subtracts levels 2..L.
+  * qr(Y, k) (Sec. 2.4 "partial QR"): column-pivoted Householder QR; with a
+    fixed rank k the first k columns of Q are kept; with a tolerance tau, k is
+    the number of pivots with |R_jj| > tau |R_11|; k <= min(rows, r).  Columns
+    of Q are signed so that R_jj >= 0.
+  * Core (eq. solveforb drops the transposes; Alg. 2.1 fixes them):
+      B = (G_alpha^T U)^+ (G_alpha^T Y(I_alpha, c)) (V^T G_beta)^+,
+    with G_alpha the Psi-side block of alpha and G_beta the Omega-side block of
+    beta; A(I_alpha, I_beta) ~ U B V^T.
+  * V of pair (alpha, beta) comes from Z(I_beta, c') where c' is the colour of
+    the pair (beta, alpha): the rank structure is symmetric, so one colouring
+    serves both Omega and Psi (Alg. 4.1 allows reusing the test matrices).
+  * Leaf test matrices have m_max columns per colour, m_max = the largest leaf.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+import scipy.linalg
+
+from . import graph as og
+from . import tree as ot
+from .philox import gaussian_block
+
+SIDE_OMEGA, SIDE_PSI, SIDE_START = 0, 1, 2
+
+
+# ----------------------------------------------------------------------------
+# Black-box operators (Section 1: the user can apply A and A^* to tall thin
+# matrices).  All act in the permuted point order.
+# ----------------------------------------------------------------------------
+
+def kernel_eval(kind: int, xa: np.ndarray, xb: np.ndarray) -> np.ndarray:
+    """K(x, y) for all pairs: log r, 1/(4 pi r), 1/r (zero where r = 0), exp(-r)."""
+    diff = xa[:, None, :] - xb[None, :, :]
+    r = np.sqrt(np.sum(diff * diff, axis=2))
+    pos = r > 0.0
+    rs = np.where(pos, r, 1.0)
+    if kind == 1:
+        return np.where(pos, np.log(rs), 0.0)
+    if kind == 2:
+        return np.where(pos, 1.0 / (4.0 * math.pi * rs), 0.0)
+    if kind == 3:
+        return np.where(pos, 1.0 / rs, 0.0)
+    if kind == 4:
+        return np.exp(-r)
+    raise ValueError(kind)
+
+
+class KernelOp:
+    """A(i, j) = K(x_i, x_j) evaluated on the fly (the matrix is symmetric)."""
+
+    def __init__(self, x_sorted: np.ndarray, kind: int, chunk_elems: int = 1 << 23):
+        self.x, self.kind, self.chunk = np.asarray(x_sorted, np.float64), kind, chunk_elems
+        self.n = self.x.shape[0]
+
+    def apply(self, X: np.ndarray) -> np.ndarray:
+        X = np.asarray(X, np.float64)
+        nz = np.flatnonzero(np.any(X != 0.0, axis=1))     # skip zero rows of X
+        Y = np.zeros((self.n, X.shape[1]))
+        if nz.size == 0:
+            return Y
+        rows = max(1, self.chunk // nz.size)
+        for s in range(0, self.n, rows):
+            e = min(self.n, s + rows)
+            Y[s:e] = kernel_eval(self.kind, self.x[s:e], self.x[nz]) @ X[nz]
+        return Y
+
+    def apply_t(self, X):
+        return self.apply(X)
+
+    def rows(self, idx: np.ndarray, X: np.ndarray) -> np.ndarray:
+        """(A X)(idx, :) only: used for sampled checks at full size."""
+        nz = np.flatnonzero(np.any(X != 0.0, axis=1))
+        return kernel_eval(self.kind, self.x[idx], self.x[nz]) @ X[nz]
+
+    def dense(self) -> np.ndarray:
+        return kernel_eval(self.kind, self.x, self.x)
+
+
+class DenseOp:
+    """A stored as a dense FP64 matrix (permuted order)."""
+
+    def __init__(self, a_sorted: np.ndarray):
+        self.a = np.asarray(a_sorted, np.float64)
+        self.n = self.a.shape[0]
+
+    def apply(self, X):
+        return self.a @ X
+
+    def apply_t(self, X):
+        return self.a.T @ X
+
+    def dense(self):
+        return self.a
+
+
+# ----------------------------------------------------------------------------
+# Factor storage
+# ----------------------------------------------------------------------------
+
+@dataclass
+class LevelFactors:
+    level: int
+    pairs: list                 # (alpha, beta) cut indices
+    rng_a: list                 # (start, end) of I_alpha
+    rng_b: list                 # (start, end) of I_beta
+    U: list = field(default_factory=list)
+    B: list = field(default_factory=list)
+    V: list = field(default_factory=list)
+    coloring: object = None
+    Y: np.ndarray | None = None  # peeled samples (kept for parity checks)
+    Z: np.ndarray | None = None
+
+
+@dataclass
+class LeafBlocks:
+    pairs: list
+    rng_a: list
+    rng_b: list
+    D: list
+    coloring: object
+    m_max: int
+    Y: np.ndarray | None = None
+
+
+@dataclass
+class H1Matrix:
+    tree: object
+    levels: dict                # l -> LevelFactors
+    leaf: LeafBlocks | None
+    r: int
+    matvec_cols: int = 0        # columns of Omega and Psi applied to A or A^*
+
+    def floats(self) -> int:
+        s = 0
+        for lf in self.levels.values():
+            s += sum(u.size for u in lf.U) + sum(b.size for b in lf.B) + sum(v.size for v in lf.V)
+        if self.leaf is not None:
+            s += sum(d.size for d in self.leaf.D)
+        return s
+
+
+def apply_levels(H: H1Matrix, levels, X: np.ndarray, transpose: bool = False) -> np.ndarray:
+    """A^(l) X restricted to the given admissible levels: sum of U B V^T blocks
+    (Section 4.1.2, level-truncated matrix)."""
+    out = np.zeros_like(X, dtype=np.float64)
+    for j in levels:
+        lf = H.levels[j]
+        for (a0, a1), (b0, b1), U, B, V in zip(lf.rng_a, lf.rng_b, lf.U, lf.B, lf.V):
+            if not transpose:
+                out[a0:a1] += U @ (B @ (V.T @ X[b0:b1]))
+            else:
+                out[b0:b1] += V @ (B.T @ (U.T @ X[a0:a1]))
+    return out
+
+
+def apply_h1(H: H1Matrix, X: np.ndarray, transpose: bool = False) -> np.ndarray:
+    """y = A~ x: all admissible blocks plus the leaf neighbour blocks (permuted order)."""
+    X = np.asarray(X, np.float64)
+    out = apply_levels(H, sorted(H.levels), X, transpose)
+    if H.leaf is not None:
+        for (a0, a1), (b0, b1), D in zip(H.leaf.rng_a, H.leaf.rng_b, H.leaf.D):
+            if not transpose:
+                out[a0:a1] += D @ X[b0:b1]
+            else:
+                out[b0:b1] += D.T @ X[a0:a1]
+    return out
+
+
+# ----------------------------------------------------------------------------
+# Per-block steps
+# ----------------------------------------------------------------------------
+
+def qr_trunc(P: np.ndarray, rank: int, tol: float, cap: int) -> np.ndarray:
+    """qr(P, k) of Section 2.4 (reading in the module docstring)."""
+    m, n = P.shape
+    kmax = min(m, n, cap)
+    if kmax == 0:
+        return np.zeros((m, 0))
+    Q, R, _ = scipy.linalg.qr(P, mode="economic", pivoting=True)
+    d = np.abs(np.diag(R))
+    if rank > 0:
+        k = min(rank, kmax)
+    else:
+        k = 0
+        while k < kmax and d[k] > tol * d[0] and d[0] > 0.0:
+            k += 1
+    s = np.where(np.diag(R)[:k] < 0.0, -1.0, 1.0)
+    return Q[:, :k] * s
+
+
+def core(Ga: np.ndarray, P: np.ndarray, Gb: np.ndarray, U: np.ndarray, V: np.ndarray) -> np.ndarray:
+    """B = (Ga^T U)^+ (Ga^T P) (V^T Gb)^+  (Alg. 2.1, last step)."""
+    M = Ga.T @ P
+    S1 = Ga.T @ U
+    S2 = Gb.T @ V
+    if U.shape[1] == 0 or V.shape[1] == 0:
+        return np.zeros((U.shape[1], V.shape[1]))
+    T = np.linalg.lstsq(S1, M, rcond=None)[0]          # k_U x r
+    return np.linalg.lstsq(S2, T.T, rcond=None)[0].T   # k_U x k_V
+
+
+def gaussians(tree, l: int, side: int, r: int, seed: int) -> np.ndarray:
+    """G_beta for every box beta of cut l, stacked in permuted order (N x r)."""
+    G = np.zeros((tree.n, r))
+    for i in range(len(tree.cuts[l])):
+        b = tree.box(l, i)
+        G[b.start:b.end] = gaussian_block(seed, side, l, b.gid, b.end - b.start, r)
+    return G
+
+
+def test_matrix(tree, l: int, col: og.Coloring, G: np.ndarray, r: int) -> np.ndarray:
+    """Omega_l: colour c has G_beta on the rows of every beta active in c (eq. neartestmatrices)."""
+    Om = np.zeros((tree.n, col.n_colors * r))
+    for c in range(col.n_colors):
+        for b in col.active(c):
+            s, e = tree.rng(l, b)
+            Om[s:e, c * r:(c + 1) * r] = G[s:e]
+    return Om
+
+
+# ----------------------------------------------------------------------------
+# Algorithm 4.1
+# ----------------------------------------------------------------------------
+
+def compress(tree, op, r: int, rank: int = 0, tol: float = 0.0, seed: int = 0,
+             keep_samples: bool = False, levels_only: bool = False) -> H1Matrix:
+    """Randomized compression of an H^1 matrix (Algorithm 4.1)."""
+    if (rank > 0) == (tol > 0.0):
+        raise ValueError("exactly one of rank > 0 or tol > 0")
+    H = H1Matrix(tree, {}, None, r)
+    L = tree.L
+    for l in range(2, L + 1):
+        pairs = ot.admissible_pairs(tree, l)
+        lf = LevelFactors(l, pairs, [tree.rng(l, a) for a, _ in pairs],
+                          [tree.rng(l, b) for _, b in pairs])
+        if not pairs:
+            H.levels[l] = lf
+            continue
+        col = og.color_level(tree, l)
+        lf.coloring = col
+        GO = gaussians(tree, l, SIDE_OMEGA, r, seed)
+        GP = gaussians(tree, l, SIDE_PSI, r, seed)
+        Om = test_matrix(tree, l, col, GO, r)
+        Ps = test_matrix(tree, l, col, GP, r)
+        coarse = sorted(H.levels)
+        Y = op.apply(Om) - apply_levels(H, coarse, Om)
+        Z = op.apply_t(Ps) - apply_levels(H, coarse, Ps, transpose=True)
+        H.matvec_cols += Om.shape[1] + Ps.shape[1]
+        pcol = col.pair_color
+        pindex = {pq: i for i, pq in enumerate(pairs)}
+        for i, (a, b) in enumerate(pairs):
+            (a0, a1), (b0, b1) = lf.rng_a[i], lf.rng_b[i]
+            c = pcol[i]
+            ct = pcol[pindex[(b, a)]]
+            P = Y[a0:a1, c * r:(c + 1) * r]
+            U = qr_trunc(P, rank, tol, r)
+            V = qr_trunc(Z[b0:b1, ct * r:(ct + 1) * r], rank, tol, r)
+            B = core(GP[a0:a1], P, GO[b0:b1], U, V)
+            lf.U.append(U)
+            lf.B.append(B)
+            lf.V.append(V)
+        if keep_samples:
+            lf.Y, lf.Z = Y, Z
+        H.levels[l] = lf
+    if levels_only:
+        return H
+    H.leaf = extract_leaf(H, op, keep_samples)
+    return H
+
+
+def extract_leaf(H: H1Matrix, op, keep_samples: bool = False) -> LeafBlocks:
+    """Section 4.1.3: identity test matrices recover the leaf neighbour blocks."""
+    tree = H.tree
+    L = tree.L
+    pairs = ot.near_pairs(tree, L)
+    col = og.color_leaf(tree)
+    m_max = max(tree.box(L, i).end - tree.box(L, i).start for i in range(len(tree.cuts[L])))
+    Om = np.zeros((tree.n, col.n_colors * m_max))
+    for c in range(col.n_colors):
+        for b in col.active(c):
+            s, e = tree.rng(L, b)
+            Om[s:e, c * m_max:c * m_max + (e - s)] = np.eye(e - s)
+    Y = op.apply(Om) - apply_levels(H, sorted(H.levels), Om)
+    H.matvec_cols += Om.shape[1]
+    pcol = col.pair_color
+    rng_a = [tree.rng(L, a) for a, _ in pairs]
+    rng_b = [tree.rng(L, b) for _, b in pairs]
+    D = []
+    for i, (a, b) in enumerate(pairs):
+        (a0, a1), (b0, b1) = rng_a[i], rng_b[i]
+        c = pcol[i]
+        D.append(Y[a0:a1, c * m_max:c * m_max + (b1 - b0)].copy())
+    return LeafBlocks(pairs, rng_a, rng_b, D, col, m_max, Y if keep_samples else None)
+
+
+# ----------------------------------------------------------------------------
+# Accuracy (Section 5): E = ||A_c - A|| / ||A|| by 20 power iterations
+# ----------------------------------------------------------------------------
+
+def power_norm(apply, apply_t, n: int, iters: int, seed: int) -> float:
+    """Spectral norm by the power method on M^T M from a Philox Gaussian start."""
+    v = gaussian_block(seed, SIDE_START, 0, 0, n, 1)[:, 0]
+    v /= np.linalg.norm(v)
+    lam = 0.0
+    for _ in range(iters):
+        w = apply_t(apply(v[:, None]))[:, 0]
+        lam = np.linalg.norm(w)
+        if lam == 0.0:
+            return 0.0
+        v = w / lam
+    return math.sqrt(lam)
+
+
+def relative_error(H: H1Matrix, op, iters: int = 20, seed: int = 1) -> float:
+    n = H.tree.n
+    diff = lambda X: apply_h1(H, X) - op.apply(X)
+    diff_t = lambda X: apply_h1(H, X, transpose=True) - op.apply_t(X)
+    num = power_norm(diff, diff_t, n, iters, seed)
+    den = power_norm(op.apply, op.apply_t, n, iters, seed)
+    return num / den if den > 0 else 0.0
