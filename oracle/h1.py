@@ -12,10 +12,14 @@ Readings of points where the paper is silent, garbled or inconsistent:
   * Peel (Alg. 4.1 writes A^(l); Sec. 4.1.2 subtracts A^(2) at level 3): the
     samples of level l are Y = A Omega - A^(l-1) Omega, with A^(l-1) the sum of
     the factors of all levels 2..l-1; the leaf step subtracts levels 2..L.
-  * qr(Y, k) (Sec. 2.4 "partial QR"): column-pivoted Householder QR; with a
-    fixed rank k the first k columns of Q are kept; with a tolerance tau, k is
-    the number of pivots with |R_jj| > tau |R_11|; k <= min(rows, r).  Columns
-    of Q are signed so that R_jj >= 0.
+  * qr(Y, k) (Sec. 2.4 "partial QR"): column-pivoted Householder QR with the
+    column norms recomputed exactly at every step (so any two implementations
+    pick the same pivots unless two norms tie to rounding); with a fixed rank k
+    the first k columns of Q are kept; with a tolerance tau, k is the number of
+    pivots with |R_jj| > tau |R_11|; k <= min(rows, r).  Columns of Q are signed
+    so that R_jj >= 0.
+  * The pseudo-inverses of the core are least-squares solves through a
+    Householder QR of the r x k factor (full column rank).
   * Core (eq. solveforb drops the transposes; Alg. 2.1 fixes them):
       B = (G_alpha^T U)^+ (G_alpha^T Y(I_alpha, c)) (V^T G_beta)^+,
     with G_alpha the Psi-side block of alpha and G_beta the Omega-side block of
@@ -187,22 +191,70 @@ def apply_h1(H: H1Matrix, X: np.ndarray, transpose: bool = False) -> np.ndarray:
 # Per-block steps
 # ----------------------------------------------------------------------------
 
+def pivoted_qr(P: np.ndarray, kmax: int, rank: int, tol: float):
+    """Column-pivoted Householder QR (Businger-Golub), steps in order: at step s
+    the remaining column of largest norm (norms recomputed exactly over rows
+    s.., lowest index on ties) is swapped to position s, and one Householder
+    reflection zeroes it below the diagonal.  Stops after `rank` steps (fixed
+    rank) or before the first pivot whose norm is <= tol times the first
+    pivot's (tolerance), and never after kmax steps.
+    Returns (Q_k with R_jj >= 0, k)."""
+    A = np.array(P, dtype=np.float64, copy=True)
+    m, n = A.shape
+    vs, taus, betas = [], [], []
+    n0 = 0.0
+    k = 0
+    for s in range(kmax):
+        norms = np.sum(A[s:, s:] ** 2, axis=0)
+        piv = s + int(np.argmax(norms))               # first maximum
+        nv = float(np.sqrt(norms[piv - s]))
+        if s == 0:
+            n0 = nv
+        if rank > 0:
+            if s >= rank:
+                break
+        elif not (n0 > 0.0) or not (nv > tol * n0):
+            break
+        A[:, [s, piv]] = A[:, [piv, s]]
+        x = A[s:, s].copy()
+        nx = float(np.sqrt(np.sum(x * x)))
+        v = x.copy()
+        if nx == 0.0:
+            tau, beta = 0.0, 0.0
+            v[:] = 0.0
+            v[0] = 1.0
+        else:
+            beta = -np.copysign(nx, x[0])
+            tau = (beta - x[0]) / beta
+            v[1:] = x[1:] / (x[0] - beta)
+            v[0] = 1.0
+        # apply H = I - tau v v^T to the trailing block
+        w = v @ A[s:, s:]
+        A[s:, s:] -= tau * np.outer(v, w)
+        vs.append(v)
+        taus.append(tau)
+        betas.append(beta)
+        k = s + 1
+    # Q_k = H_0 ... H_{k-1} [I_k; 0], columns signed so that R_jj >= 0
+    Q = np.zeros((m, k))
+    Q[:k, :k] = np.eye(k)
+    for s in range(k - 1, -1, -1):
+        v, tau = vs[s], taus[s]
+        Q[s:, :] -= tau * np.outer(v, v @ Q[s:, :])
+    for j in range(k):
+        if betas[j] < 0.0:
+            Q[:, j] = -Q[:, j]
+    return Q, k
+
+
 def qr_trunc(P: np.ndarray, rank: int, tol: float, cap: int) -> np.ndarray:
     """qr(P, k) of Section 2.4 (reading in the module docstring)."""
     m, n = P.shape
     kmax = min(m, n, cap)
     if kmax == 0:
         return np.zeros((m, 0))
-    Q, R, _ = scipy.linalg.qr(P, mode="economic", pivoting=True)
-    d = np.abs(np.diag(R))
-    if rank > 0:
-        k = min(rank, kmax)
-    else:
-        k = 0
-        while k < kmax and d[k] > tol * d[0] and d[0] > 0.0:
-            k += 1
-    s = np.where(np.diag(R)[:k] < 0.0, -1.0, 1.0)
-    return Q[:, :k] * s
+    Q, _ = pivoted_qr(P, kmax, rank, tol)
+    return Q
 
 
 def core(Ga: np.ndarray, P: np.ndarray, Gb: np.ndarray, U: np.ndarray, V: np.ndarray) -> np.ndarray:
@@ -212,8 +264,15 @@ def core(Ga: np.ndarray, P: np.ndarray, Gb: np.ndarray, U: np.ndarray, V: np.nda
     S2 = Gb.T @ V
     if U.shape[1] == 0 or V.shape[1] == 0:
         return np.zeros((U.shape[1], V.shape[1]))
-    T = np.linalg.lstsq(S1, M, rcond=None)[0]          # k_U x r
-    return np.linalg.lstsq(S2, T.T, rcond=None)[0].T   # k_U x k_V
+    T = lstsq_qr(S1, M)            # (Ga^T U)^+ M,            k_U x r
+    return lstsq_qr(S2, T.T).T     # T (V^T Gb)^+ = (S2^+ T^T)^T, k_U x k_V
+
+
+def lstsq_qr(S: np.ndarray, R: np.ndarray) -> np.ndarray:
+    """Least-squares solution of S X = R for S of full column rank, through a
+    Householder QR of S and a triangular solve (S^+ R)."""
+    Q, Rs = np.linalg.qr(S)
+    return scipy.linalg.solve_triangular(Rs, Q.T @ R, lower=False)
 
 
 def gaussians(tree, l: int, side: int, r: int, seed: int) -> np.ndarray:

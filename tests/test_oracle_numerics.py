@@ -203,3 +203,30 @@ def test_matvec_count_formula():
     chis = [lf.coloring.n_colors for lf in H.levels.values()]
     assert H.matvec_cols == 2 * w.r * sum(chis) + H.leaf.m_max * H.leaf.coloring.n_colors
     assert all(c <= 6 for c in chis) and H.leaf.coloring.n_colors <= 3
+
+
+def test_pivoted_qr_matches_lapack_without_near_ties():
+    """The oracle's own Businger-Golub QR picks LAPACK's pivots and returns the
+    same signed Q_k whenever no two column norms nearly tie."""
+    rng = np.random.default_rng(0)
+    for t in range(150):
+        m, n = int(rng.integers(3, 40)), int(rng.integers(2, 20))
+        P = rng.standard_normal((m, n)) @ np.diag(10.0 ** -rng.uniform(0, 8, n))
+        Q, k = h1.pivoted_qr(P, min(m, n), 0, 1e-6)
+        Q2, R2, piv = scipy.linalg.qr(P, mode="economic", pivoting=True)
+        d = np.abs(np.diag(R2))
+        k2 = int(np.sum(np.cumprod(d > 1e-6 * d[0])))
+        assert k == k2
+        assert np.allclose(Q, Q2[:, :k2] * np.where(np.diag(R2)[:k2] < 0, -1, 1), atol=1e-10)
+        assert np.allclose(Q.T @ Q, np.eye(k), atol=1e-13)
+
+
+def test_core_least_squares_equals_pseudo_inverse():
+    rng = np.random.default_rng(5)
+    Ga, Gb = rng.standard_normal((40, 12)), rng.standard_normal((30, 12))
+    U = np.linalg.qr(rng.standard_normal((40, 7)))[0]
+    V = np.linalg.qr(rng.standard_normal((30, 5)))[0]
+    P = rng.standard_normal((40, 12))
+    B = h1.core(Ga, P, Gb, U, V)
+    ref = np.linalg.pinv(Ga.T @ U) @ (Ga.T @ P) @ np.linalg.pinv(V.T @ Gb)
+    assert np.allclose(B, ref, rtol=1e-10, atol=1e-12)
