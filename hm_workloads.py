@@ -113,6 +113,7 @@ class Workload:
     uniform_depth: int = 0 # > 0: force a uniform tree of this depth
     dense: np.ndarray | None = field(default=None, repr=False)  # stored matrix op
     seed: int = SEED_BASE
+    oversample: int = 10   # p: tolerance mode keeps k <= r - p
 
     @property
     def n(self) -> int:

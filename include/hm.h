@@ -1,0 +1,205 @@
+/*
+ * hm.h -- C ABI of the GB300 (sm_103a) graph-coloured H^1 peeling compressor.
+ *
+ * Problem statement (Levitt & Martinsson, Section 1): a user can apply an
+ * N x N matrix A and its adjoint A^* to tall thin matrices, Y = A Omega and
+ * Z = A^* Psi.  From such products with structured random test matrices the
+ * library recovers an H^1 representation of A on a cluster tree of points:
+ * low-rank factors U B V^T for every admissible block of levels 2..L
+ * (Section 4.1, Algorithm 4.1) and dense neighbour blocks of the leaf level
+ * (Section 4.1.3).
+ *
+ * Conventions shared by every entry point
+ *  - Every call returns hm_status; no exception crosses the ABI.  On error the
+ *    context keeps its last consistent state and hm_last_error() describes the
+ *    failure; hm_destroy() is always safe.
+ *  - Calls run in order: hm_tree_build -> (hm_color, hm_sample)* / hm_compress
+ *    -> hm_apply, hm_relerr.  A call out of order returns HM_ESTATE.
+ *  - Pointers named *_dev are device pointers, owned by the caller, read during
+ *    the call only (inputs) or written before the call returns (outputs).
+ *    Pointers named *_host are host pointers, likewise owned by the caller.
+ *  - All device work is issued on the stream given to hm_create (a
+ *    cudaStream_t passed as void*; NULL = the legacy default stream).  Calls
+ *    that return sizes to the host (hm_tree_build, hm_color, hm_compress,
+ *    hm_get_info, hm_export) synchronise that stream; the others do not.
+ *  - The context owns every device buffer it allocates (tree, colourings,
+ *    samples, factors); hm_destroy frees them.
+ *  - Matrices at the boundary are column-major with leading dimension n and are
+ *    indexed in the caller's ORIGINAL point order.
+ */
+#ifndef HM_H
+#define HM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    HM_OK = 0,
+    HM_EINVAL = 1,    /* invalid argument (null pointer, bad size, bad mode) */
+    HM_ENOMEM = 2,    /* device or host allocation failed */
+    HM_ESTATE = 3,    /* call made out of order */
+    HM_ECUDA = 4,     /* a CUDA runtime call or kernel launch failed */
+    HM_EOP = 5,       /* the user's black-box operator returned non-zero */
+    HM_ETIMEOUT = 6,  /* a bounded device-side wait gave up */
+    HM_ENOTSUP = 7    /* outside the implemented limits (e.g. > 1024 colours) */
+} hm_status;
+
+/* Arithmetic of the built-in black-box contraction K(X, X) Omega.  The peel
+ * subtraction, the QR factorisations and the core solves are FP64 in both. */
+typedef enum {
+    HM_FP64 = 0,         /* FP64 kernel evaluation and FP64 products */
+    HM_MIXED_BF16X6 = 1  /* FP32 kernel evaluation, 3-piece BF16 split of both
+                            operands, 6 tcgen05 products, FP32 accumulation,
+                            FP64 output */
+} hm_precision;
+
+/* Kernel functions of the built-in operator (A_ij = K(x_i, x_j)). */
+enum {
+    HM_K_LOG = 1,        /* log|x - y|, 0 where x == y        */
+    HM_K_LAPLACE3D = 2,  /* 1 / (4 pi |x - y|), 0 where x == y */
+    HM_K_INVR = 3,       /* 1 / |x - y|, 0 where x == y        */
+    HM_K_EXP = 4         /* exp(-|x - y|)                       */
+};
+
+/* Kinds of black-box operator. */
+enum {
+    HM_OP_KERNEL = 0,    /* built-in: kernel function on the tree's points   */
+    HM_OP_DENSE = 1,     /* built-in: stored dense n x n matrix (device)     */
+    HM_OP_CALLBACK = 2   /* user routine, see hm_apply_fn                    */
+};
+
+#define HM_LEVEL_LEAF (-1)
+
+typedef struct hm_ctx hm_ctx;
+
+typedef struct {
+    int d;                /* dimension of the points: 1, 2 or 3 */
+    int leaf_size;        /* m: a box is split while it holds more than m points */
+    int uniform_depth;    /* 0: adaptive tree; > 0: split every box down to this level */
+    int r;                /* columns per colour of the Gaussian test matrices (k + p), 1..64 */
+    int oversample;       /* p: in tolerance mode k <= r - p (Section 2.5 suggests p = 10) */
+    int rank;             /* > 0: fixed rank k (<= r); exactly one of rank, tol is set */
+    double tol;           /* > 0: keep pivots with |R_jj| > tol |R_11| (at most r - p) */
+    int precision;        /* hm_precision */
+    int keep_samples;     /* non-zero: keep every level's peeled samples for hm_export */
+    uint64_t seed;        /* Philox4x32-10 key of all test matrices */
+} hm_config;
+
+/*
+ * User black box (Section 1): Y = A X when trans == 0, Y = A^* X when trans == 1.
+ * X_dev and Y_dev are device, column-major n x s (leading dimension n), in the
+ * original point order; the routine must enqueue its work on `stream` (or
+ * finish it before returning).  Return 0 on success; any other value makes the
+ * library call fail with HM_EOP.
+ */
+typedef int (*hm_apply_fn)(void *user, int trans, const double *X_dev, double *Y_dev,
+                           int64_t s, void *stream);
+
+typedef struct {
+    int kind;                 /* HM_OP_* */
+    int kernel;               /* HM_K_* for HM_OP_KERNEL */
+    const double *dense_dev;  /* HM_OP_DENSE: n x n column-major, original order */
+    hm_apply_fn apply;        /* HM_OP_CALLBACK */
+    void *user;               /* HM_OP_CALLBACK: passed back to apply */
+} hm_op;
+
+typedef struct {
+    int64_t n;
+    int L;                    /* depth of the tree */
+    int n_boxes;              /* boxes over all levels */
+    int colors[32];           /* chi_l per cut level (0 where none), index L+1 = leaf */
+    int64_t pairs[32];        /* admissible pairs per cut level; index L+1 = neighbour pairs */
+    int64_t vertices[32];     /* constraint sets per cut level; index L+1 = leaf */
+    int64_t matvec_cols;      /* columns of Omega and Psi applied to A or A^* */
+    int64_t factor_floats;    /* floats stored in U, B, V and the leaf blocks */
+    int max_rank;             /* largest k over all blocks */
+    double seconds_sample;    /* time in the black box during hm_compress */
+    double seconds_total;     /* wall time of hm_compress */
+} hm_info;
+
+/* Create a context.  cfg is copied.  stream: a cudaStream_t or NULL. */
+hm_status hm_create(hm_ctx **out, const hm_config *cfg, void *stream);
+
+/* Free the context and everything it owns.  Safe on NULL and after errors. */
+hm_status hm_destroy(hm_ctx *ctx);
+
+/*
+ * Section 3: cluster tree over n points (points_dev: device, n x d row-major
+ * FP64, original order), neighbour and interaction lists of every cut.  The
+ * points are copied into the context (permuted into Morton order).
+ */
+hm_status hm_tree_build(hm_ctx *ctx, const double *points_dev, int64_t n);
+
+/*
+ * Sections 4.1.2-4.1.3, Algorithm 2.3: build the constraint-incompatibility
+ * graph of cut `level` (2..L, or HM_LEVEL_LEAF for the leaf neighbour pairs)
+ * and colour it with DSatur.  *n_colors receives chi.
+ */
+hm_status hm_color(hm_ctx *ctx, int level, int *n_colors);
+
+/*
+ * Algorithm 4.1, sampling step of one level: draw the colour-masked Gaussian
+ * test matrices Omega_l and Psi_l (identity blocks for HM_LEVEL_LEAF) and store
+ * Y = A Omega_l and Z = A^* Psi_l (not yet peeled) in the context.
+ * Requires hm_color(level) first.
+ */
+hm_status hm_sample(hm_ctx *ctx, const hm_op *op, int level);
+
+/*
+ * Algorithm 4.1: the whole compression (colour, sample, peel, bases, cores for
+ * levels 2..L, then the leaf blocks).  Requires hm_tree_build.
+ */
+hm_status hm_compress(hm_ctx *ctx, const hm_op *op);
+
+/*
+ * y = A~ x (trans = 0) or A~^* x (trans = 1) with the compressed operator:
+ * x_dev, y_dev device, column-major n x nrhs, original order.
+ */
+hm_status hm_apply(hm_ctx *ctx, const double *x_dev, double *y_dev, int64_t nrhs, int trans);
+
+/*
+ * Section 5: E = ||A~ - A|| / ||A|| by `iters` power iterations (20 in the
+ * paper) on both operators from one Philox Gaussian start vector.
+ */
+hm_status hm_relerr(hm_ctx *ctx, const hm_op *op, int iters, double *err);
+
+hm_status hm_get_info(hm_ctx *ctx, hm_info *out);
+
+/* Export selectors for hm_export (structure and numbers, for tests). */
+enum {
+    HM_X_PERM = 1,        /* int32[n]: original index of each sorted point */
+    HM_X_LEVEL_BOXES = 2, /* int32[nb][8] of level `level`: start, end, a0, a1, a2, parent, leaf, gid */
+    HM_X_CUT = 3,         /* int32[nc][2] of cut `level`: box level, index within level */
+    HM_X_NEAR = 4,        /* int32: nc+1 CSR pointers then indices (cut `level`) */
+    HM_X_INTER = 5,       /* int32: nc+1 CSR pointers then indices */
+    HM_X_PAIR_VERTEX = 6, /* int32[n_pairs] (cut `level` or HM_LEVEL_LEAF) */
+    HM_X_VERTEX_COLOR = 7,/* int32[n_vertices] */
+    HM_X_VERTEX_BETA = 8, /* int32[n_vertices] */
+    HM_X_GAUSS = 9,       /* double[2][n][r]: Omega-side then Psi-side G, sorted order */
+    HM_X_SAMPLE_Y = 10,   /* double[chi][n][r']: colour-major, sorted order (r' = r or m_max) */
+    HM_X_SAMPLE_Z = 11,   /* double[chi][n][r] */
+    HM_X_PAIR_RANKS = 12, /* int32[n_pairs][2]: k_U, k_V */
+    HM_X_FACTORS = 13,    /* double: U arena, V arena, B arena concatenated */
+    HM_X_FACTOR_OFFS = 14,/* int64[n_pairs][3]: offsets of U, V, B in their arenas */
+    HM_X_LEAF_D = 15,     /* double: leaf blocks, row-major |I_a| x |I_b| per neighbour pair */
+    HM_X_VERTEX_DEGREE = 16 /* int32[n_vertices] */
+};
+
+/*
+ * Copy an exported array to host memory.  With host_buf == NULL only *bytes is
+ * set to the size needed; otherwise *bytes must be at least that size.
+ */
+hm_status hm_export(hm_ctx *ctx, int what, int level, void *host_buf, size_t *bytes);
+
+/* Human-readable description of the last error on this context. */
+const char *hm_last_error(const hm_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HM_H */

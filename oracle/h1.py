@@ -16,8 +16,10 @@ Readings of points where the paper is silent, garbled or inconsistent:
     column norms recomputed exactly at every step (so any two implementations
     pick the same pivots unless two norms tie to rounding); with a fixed rank k
     the first k columns of Q are kept; with a tolerance tau, k is the number of
-    pivots with |R_jj| > tau |R_11|; k <= min(rows, r).  Columns of Q are signed
-    so that R_jj >= 0.
+    pivots with |R_jj| > tau |R_11|.  Always k <= min(|I_alpha|, |I_beta|) (the
+    block's rank cannot exceed it) and, with a tolerance, k <= r - p so that the
+    core's r x k solves keep p rows of oversampling (Sec. 2.5: p = 10 is often
+    good).  Columns of Q are signed so that R_jj >= 0.
   * The pseudo-inverses of the core are least-squares solves through a
     Householder QR of the r x k factor (full column rank).
   * Core (eq. solveforb drops the transposes; Alg. 2.1 fixes them):
@@ -248,7 +250,7 @@ def pivoted_qr(P: np.ndarray, kmax: int, rank: int, tol: float):
 
 
 def qr_trunc(P: np.ndarray, rank: int, tol: float, cap: int) -> np.ndarray:
-    """qr(P, k) of Section 2.4 (reading in the module docstring)."""
+    """qr(P, k) of Section 2.4 (reading in the module docstring); k <= cap."""
     m, n = P.shape
     kmax = min(m, n, cap)
     if kmax == 0:
@@ -299,10 +301,11 @@ def test_matrix(tree, l: int, col: og.Coloring, G: np.ndarray, r: int) -> np.nda
 # ----------------------------------------------------------------------------
 
 def compress(tree, op, r: int, rank: int = 0, tol: float = 0.0, seed: int = 0,
-             keep_samples: bool = False, levels_only: bool = False) -> H1Matrix:
+             keep_samples: bool = False, levels_only: bool = False, oversample: int = 10) -> H1Matrix:
     """Randomized compression of an H^1 matrix (Algorithm 4.1)."""
     if (rank > 0) == (tol > 0.0):
         raise ValueError("exactly one of rank > 0 or tol > 0")
+    kcap = r if rank > 0 else r - oversample
     H = H1Matrix(tree, {}, None, r)
     L = tree.L
     for l in range(2, L + 1):
@@ -329,8 +332,9 @@ def compress(tree, op, r: int, rank: int = 0, tol: float = 0.0, seed: int = 0,
             c = pcol[i]
             ct = pcol[pindex[(b, a)]]
             P = Y[a0:a1, c * r:(c + 1) * r]
-            U = qr_trunc(P, rank, tol, r)
-            V = qr_trunc(Z[b0:b1, ct * r:(ct + 1) * r], rank, tol, r)
+            cap = min(kcap, a1 - a0, b1 - b0)    # rank(A(I_a, I_b)) <= min(|I_a|, |I_b|)
+            U = qr_trunc(P, rank, tol, cap)
+            V = qr_trunc(Z[b0:b1, ct * r:(ct + 1) * r], rank, tol, cap)
             B = core(GP[a0:a1], P, GO[b0:b1], U, V)
             lf.U.append(U)
             lf.B.append(B)

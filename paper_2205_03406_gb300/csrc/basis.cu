@@ -1,0 +1,464 @@
+// Per-pair bases and cores of one level (Algorithm 2.1 applied to every
+// admissible block, Algorithm 4.1), and the leaf blocks (Section 4.1.3).
+//
+//  K9   U_{alpha,beta} = qr(Y(I_alpha, c), k): column-pivoted Householder QR of
+//       the peeled sample tile, in place, one CTA per tile.  Pivot = the column
+//       of largest remaining norm (norms recomputed exactly each step, lowest
+//       index on ties); k is fixed, or the number of pivots whose norm exceeds
+//       tol times the first; the explicit Q columns are signed so that
+//       R_jj >= 0.  The same kernel factors every Z tile; V of pair
+//       (alpha, beta) is the Q of the Z tile of the pair (beta, alpha).
+//  K10  B = (G_alpha^T U)^+ (G_alpha^T Y(I_alpha, c)) (V^T G_beta)^+ with
+//       G_alpha the Psi-side block of alpha and G_beta the Omega-side block of
+//       beta, by Householder QR of the two r x k matrices and triangular solves
+//       (one warp per pair).
+//  K11  D_{alpha,beta} = Y_leaf(I_alpha, c m_max + [0, |I_beta|)).
+#include "ctx.cuh"
+
+#include <algorithm>
+
+namespace hm {
+
+// M_p = G^Psi(I_alpha)^T P_p  (r x r), before the tile is factored in place
+__global__ void __launch_bounds__(256) k_core_M(const int *tile_alpha, const int *tile_color, const int *ent, int64_t n,
+                                                int r, const double *Y, const double *GP, double *M) {
+    __shared__ double gs[32][64], ps[32][64];
+    const int64_t p = blockIdx.x;
+    const int *e = ent + (int64_t)tile_alpha[p] * ENT_FIELDS;
+    const int s0 = e[3], m = e[4] - e[3];
+    const double *P = Y + ((int64_t)tile_color[p] * n + s0) * r;
+    double acc[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) acc[q] = 0.0;
+    for (int i0 = 0; i0 < m; i0 += 32) {
+        const int mm = min(32, m - i0);
+        for (int o = threadIdx.x; o < 32 * r; o += 256) {
+            const int i = o / r, j = o % r;
+            gs[i][j] = (i < mm) ? GP[(int64_t)(s0 + i0 + i) * r + j] : 0.0;
+            ps[i][j] = (i < mm) ? P[(int64_t)(i0 + i) * r + j] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+            const int o = threadIdx.x + q * 256;
+            if (o < r * r) {
+                const int a = o / r, b = o % r;
+                double s = acc[q];
+                for (int i = 0; i < mm; ++i) s = fma(gs[i][a], ps[i][b], s);
+                acc[q] = s;
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+        const int o = threadIdx.x + q * 256;
+        if (o < r * r) M[p * r * r + o] = acc[q];
+    }
+}
+
+// Column-pivoted Householder QR of one tile (m x r, row-major), in place;
+// on exit the first k columns hold Q_k with R_jj >= 0.
+__global__ void __launch_bounds__(256) k_qr_tiles(const int *tile_alpha, const int *tile_beta, const int *tile_color,
+                                                  const int *ent, int64_t n, int r, int cap, int rank, double tol,
+                                                  double *Ybase, int *kout) {
+    __shared__ double red[8][64];
+    __shared__ double nrm[64], tau[64], beta[64];
+    __shared__ int sh_piv, sh_stop;
+    __shared__ double sh_scale, sh_n0;
+    const int64_t p = blockIdx.x;
+    const int *e = ent + (int64_t)tile_alpha[p] * ENT_FIELDS;
+    const int m = e[4] - e[3];
+    double *A = Ybase + ((int64_t)tile_color[p] * n + e[3]) * r;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int *eb = ent + (int64_t)tile_beta[p] * ENT_FIELDS;
+    // the block A(I_alpha, I_beta) has rank <= min(|I_alpha|, |I_beta|)
+    const int kmax = min(min(m, eb[4] - eb[3]), min(r, cap));
+    int k = 0;
+    for (int s = 0; s < kmax; ++s) {
+        // exact norms of the trailing columns
+        for (int h = 0; h < 2; ++h) {
+            const int j = lane + 32 * h;
+            double acc = 0.0;
+            if (j >= s && j < r)
+                for (int i = s + w; i < m; i += 8) acc = fma(A[(int64_t)i * r + j], A[(int64_t)i * r + j], acc);
+            red[w][j] = acc;
+        }
+        __syncthreads();
+        if (threadIdx.x < r) {
+            double t = 0.0;
+            for (int u = 0; u < 8; ++u) t += red[u][threadIdx.x];
+            nrm[threadIdx.x] = t;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int piv = s;
+            for (int j = s + 1; j < r; ++j)
+                if (nrm[j] > nrm[piv]) piv = j;
+            const double nv = sqrt(nrm[piv]);
+            if (s == 0) sh_n0 = nv;
+            int stop = 0;
+            if (rank > 0) stop = (s >= rank);
+            else stop = !(sh_n0 > 0.0) || !(nv > tol * sh_n0);
+            sh_piv = piv;
+            sh_stop = stop;
+        }
+        __syncthreads();
+        if (sh_stop) break;
+        const int piv = sh_piv;
+        if (piv != s) {
+            for (int i = threadIdx.x; i < m; i += blockDim.x) {
+                const double a = A[(int64_t)i * r + s];
+                A[(int64_t)i * r + s] = A[(int64_t)i * r + piv];
+                A[(int64_t)i * r + piv] = a;
+            }
+            if (threadIdx.x == 0) nrm[s] = nrm[piv];
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const double x0 = A[(int64_t)s * r + s];
+            const double nx = sqrt(nrm[s]);
+            if (nx == 0.0) {
+                tau[s] = 0.0;
+                beta[s] = 0.0;
+                sh_scale = 0.0;
+            } else {
+                const double b = -copysign(nx, x0);
+                tau[s] = (b - x0) / b;
+                beta[s] = b;
+                sh_scale = 1.0 / (x0 - b);
+                A[(int64_t)s * r + s] = b;
+            }
+        }
+        __syncthreads();
+        const double sc = sh_scale, ts = tau[s];
+        for (int i = s + 1 + threadIdx.x; i < m; i += blockDim.x) A[(int64_t)i * r + s] *= sc;
+        __syncthreads();
+        // apply H = I - tau v v^T (v = [1; A(s+1:m, s)]) to columns s+1..r-1
+        for (int h = 0; h < 2; ++h) {
+            const int j = lane + 32 * h;
+            double acc = 0.0;
+            if (j > s && j < r)
+                for (int i = s + 1 + w; i < m; i += 8) acc = fma(A[(int64_t)i * r + s], A[(int64_t)i * r + j], acc);
+            red[w][j] = acc;
+        }
+        __syncthreads();
+        if (threadIdx.x < r && threadIdx.x > s) {
+            double t = A[(int64_t)s * r + threadIdx.x];
+            for (int u = 0; u < 8; ++u) t += red[u][threadIdx.x];
+            nrm[threadIdx.x] = t;  // reuse as w_j
+        }
+        __syncthreads();
+        for (int o = threadIdx.x; o < m * r; o += blockDim.x) {
+            const int i = o / r, j = o % r;
+            if (j <= s || i < s) continue;
+            const double vi = (i == s) ? 1.0 : A[(int64_t)i * r + s];
+            A[(int64_t)i * r + j] -= ts * vi * nrm[j];
+        }
+        __syncthreads();
+        k = s + 1;
+    }
+    // explicit Q_k (backward accumulation of the reflectors)
+    for (int j = k - 1; j >= 0; --j) {
+        const double tj = tau[j];
+        if (j < k - 1) {
+            for (int h = 0; h < 2; ++h) {
+                const int t = lane + 32 * h;
+                double acc = 0.0;
+                if (t > j && t < k)
+                    for (int i = j + 1 + w; i < m; i += 8) acc = fma(A[(int64_t)i * r + j], A[(int64_t)i * r + t], acc);
+                red[w][t] = acc;
+            }
+            __syncthreads();
+            if (threadIdx.x > j && threadIdx.x < k) {
+                double t = A[(int64_t)j * r + threadIdx.x];
+                for (int u = 0; u < 8; ++u) t += red[u][threadIdx.x];
+                nrm[threadIdx.x] = t;
+            }
+            __syncthreads();
+            for (int o = threadIdx.x; o < m * k; o += blockDim.x) {
+                const int i = o / k, t = o % k;
+                if (t <= j || i < j) continue;
+                const double vi = (i == j) ? 1.0 : A[(int64_t)i * r + j];
+                A[(int64_t)i * r + t] -= tj * vi * nrm[t];
+            }
+            __syncthreads();
+        }
+        for (int i = threadIdx.x; i < m; i += blockDim.x) {
+            double v;
+            if (i < j) v = 0.0;
+            else if (i == j) v = 1.0 - tj;
+            else v = -tj * A[(int64_t)i * r + j];
+            A[(int64_t)i * r + j] = v;
+        }
+        __syncthreads();
+    }
+    // R_jj >= 0
+    for (int o = threadIdx.x; o < m * k; o += blockDim.x) {
+        const int i = o / k, j = o % k;
+        if (beta[j] < 0.0) A[(int64_t)i * r + j] = -A[(int64_t)i * r + j];
+    }
+    if (threadIdx.x == 0) kout[p] = k;
+}
+
+__global__ void k_factor_sizes(const int *pair_alpha, const int *pair_col, const int *pairT, const int *kY,
+                               const int *kZ, const int *ent, int64_t np, int *kU, int *kV, int64_t *sU, int64_t *sV,
+                               int64_t *sB) {
+    int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (p >= np) return;
+    const int *ea = ent + (int64_t)pair_alpha[p] * ENT_FIELDS, *eb = ent + (int64_t)pair_col[p] * ENT_FIELDS;
+    const int ku = kY[p], kv = kZ[pairT[p]];
+    kU[p] = ku;
+    kV[p] = kv;
+    sU[p] = (int64_t)(ea[4] - ea[3]) * ku;
+    sV[p] = (int64_t)(eb[4] - eb[3]) * kv;
+    sB[p] = (int64_t)ku * kv;
+}
+
+__global__ void k_pack(const int *pair_alpha, const int *pair_col, const int *pair_color, const int *pairT,
+                       const int *ent, int64_t n, int r, const int *kU, const int *kV, const int64_t *offU,
+                       const int64_t *offV, const double *Y, const double *Z, double *U, double *V) {
+    const int64_t p = blockIdx.x;
+    const int *ea = ent + (int64_t)pair_alpha[p] * ENT_FIELDS, *eb = ent + (int64_t)pair_col[p] * ENT_FIELDS;
+    const int ma = ea[4] - ea[3], mb = eb[4] - eb[3], ku = kU[p], kv = kV[p];
+    const double *Yt = Y + ((int64_t)pair_color[p] * n + ea[3]) * r;
+    const int pt = pairT[p];
+    const double *Zt = Z + ((int64_t)pair_color[pt] * n + eb[3]) * r;
+    for (int o = threadIdx.x; o < ma * ku; o += blockDim.x) U[offU[p] + o] = Yt[(int64_t)(o / ku) * r + o % ku];
+    for (int o = threadIdx.x; o < mb * kv; o += blockDim.x) V[offV[p] + o] = Zt[(int64_t)(o / kv) * r + o % kv];
+}
+
+// --- warp-level small dense helpers (row-major, leading dimension ld) -------
+
+// Householder QR of A (m x k), R in the upper triangle, v below (v0 = 1).
+__device__ void warp_house_qr(double *A, int m, int k, int ld, double *tau) {
+    const int lane = threadIdx.x & 31;
+    for (int s = 0; s < k; ++s) {
+        double ss = 0.0;
+        for (int i = s + lane; i < m; i += 32) ss = fma(A[i * ld + s], A[i * ld + s], ss);
+        ss = warp_sum(ss);
+        const double x0 = A[s * ld + s], nx = sqrt(ss);
+        double t = 0.0, b = 0.0, sc = 0.0;
+        if (nx > 0.0) {
+            b = -copysign(nx, x0);
+            t = (b - x0) / b;
+            sc = 1.0 / (x0 - b);
+        }
+        __syncwarp();
+        for (int i = s + 1 + lane; i < m; i += 32) A[i * ld + s] *= sc;
+        if (lane == 0) {
+            tau[s] = t;
+            if (nx > 0.0) A[s * ld + s] = b;
+        }
+        __syncwarp();
+        for (int j = s + 1 + lane; j < k; j += 32) {
+            double wv = A[s * ld + j];
+            for (int i = s + 1; i < m; ++i) wv = fma(A[i * ld + s], A[i * ld + j], wv);
+            A[s * ld + j] -= t * wv;
+            for (int i = s + 1; i < m; ++i) A[i * ld + j] -= t * A[i * ld + s] * wv;
+        }
+        __syncwarp();
+    }
+}
+
+// X (m x nc) := Q^T X for the reflectors stored in A (m x k)
+__device__ void warp_apply_qt(const double *A, int m, int k, int lda, const double *tau, double *X, int nc, int ldx) {
+    const int lane = threadIdx.x & 31;
+    for (int s = 0; s < k; ++s) {
+        const double t = tau[s];
+        for (int j = lane; j < nc; j += 32) {
+            double wv = X[s * ldx + j];
+            for (int i = s + 1; i < m; ++i) wv = fma(A[i * lda + s], X[i * ldx + j], wv);
+            X[s * ldx + j] -= t * wv;
+            for (int i = s + 1; i < m; ++i) X[i * ldx + j] -= t * A[i * lda + s] * wv;
+        }
+        __syncwarp();
+    }
+}
+
+// X (k x nc) := R^{-1} X, R the k x k upper triangle of A
+__device__ void warp_back_solve(const double *A, int k, int lda, double *X, int nc, int ldx) {
+    const int lane = threadIdx.x & 31;
+    for (int j = lane; j < nc; j += 32)
+        for (int i = k - 1; i >= 0; --i) {
+            double v = X[i * ldx + j];
+            for (int t = i + 1; t < k; ++t) v -= A[i * lda + t] * X[t * ldx + j];
+            X[i * ldx + j] = v / A[i * lda + i];
+        }
+    __syncwarp();
+}
+
+// one warp per pair: B = (GP_a^T U)^+ M (GO_b^T V)^{+T}
+__global__ void __launch_bounds__(32) k_core(const int *pair_alpha, const int *pair_col, const int *ent, int r,
+                                             const int *kU, const int *kV, const int64_t *offU, const int64_t *offV,
+                                             const int64_t *offB, const double *U, const double *V, const double *GO,
+                                             const double *GP, const double *M, double *B) {
+    extern __shared__ double sm[];
+    const int64_t p = blockIdx.x;
+    const int ku = kU[p], kv = kV[p];
+    if (ku == 0 || kv == 0) return;
+    const int lane = threadIdx.x;
+    double *S1 = sm;              // r x ku  (ld r)
+    double *S2 = S1 + r * r;      // r x kv
+    double *Mx = S2 + r * r;      // r x r, then X^T
+    double *X = Mx + r * r;       // ku x r, then Bt
+    double *tau = X + r * r;      // r
+    const int *ea = ent + (int64_t)pair_alpha[p] * ENT_FIELDS, *eb = ent + (int64_t)pair_col[p] * ENT_FIELDS;
+    const int sa = ea[3], ma = ea[4] - ea[3], sb = eb[3], mb = eb[4] - eb[3];
+    const double *Up = U + offU[p], *Vp = V + offV[p];
+    for (int o = lane; o < r * ku; o += 32) {
+        const int a = o / ku, u = o % ku;
+        double s = 0.0;
+        for (int i = 0; i < ma; ++i) s = fma(GP[(int64_t)(sa + i) * r + a], Up[(int64_t)i * ku + u], s);
+        S1[a * r + u] = s;
+    }
+    for (int o = lane; o < r * kv; o += 32) {
+        const int a = o / kv, v = o % kv;
+        double s = 0.0;
+        for (int i = 0; i < mb; ++i) s = fma(GO[(int64_t)(sb + i) * r + a], Vp[(int64_t)i * kv + v], s);
+        S2[a * r + v] = s;
+    }
+    for (int o = lane; o < r * r; o += 32) Mx[o] = M[p * r * r + o];
+    __syncwarp();
+    // X = R1^{-1} (Q1^T M)(0:ku, :)
+    warp_house_qr(S1, r, ku, r, tau);
+    warp_apply_qt(S1, r, ku, r, tau, Mx, r, r);
+    warp_back_solve(S1, ku, r, Mx, r, r);
+    // Bt = R2^{-1} (Q2^T X^T)(0:kv, :) with X^T (r x ku) stored in X
+    for (int o = lane; o < r * ku; o += 32) {
+        const int a = o / ku, u = o % ku;
+        X[a * r + u] = Mx[u * r + a];
+    }
+    __syncwarp();
+    warp_house_qr(S2, r, kv, r, tau);
+    warp_apply_qt(S2, r, kv, r, tau, X, ku, r);
+    warp_back_solve(S2, kv, r, X, ku, r);
+    double *Bp = B + offB[p];
+    for (int o = lane; o < ku * kv; o += 32) {
+        const int u = o / kv, v = o % kv;
+        Bp[o] = X[v * r + u];
+    }
+}
+
+Err bases_and_cores(hm_ctx *c, int level) {
+    cudaStream_t st = c->st;
+    Coloring &g = c->colorings[level];
+    if ((int)c->factors.size() < c->L + 1) c->factors.resize(c->L + 1);
+    Factors &f = c->factors[level];
+    f = Factors();
+    f.n_pairs = g.n_pairs;
+    const int64_t np = g.n_pairs;
+    const int r = c->cfg.r;
+    const int64_t n = c->n;
+    const Cut &cu = c->cuts[level];
+    if (np == 0) {
+        f.done = true;
+        return ok();
+    }
+    // M = G_alpha^T P for every pair (tile p is read only by pair p)
+    HM_TRY(ensure(c->scratch_a, (size_t)np * r * r * sizeof(double)));
+    k_core_M<<<(int)np, 256, 0, st>>>(g.pair_alpha.as<int>(), g.pair_color.as<int>(), cu.ent.as<int>(), n, r,
+                                      c->cur.Y.as<double>(), c->GP.as<double>(), c->scratch_a.as<double>());
+    HM_LAUNCH("core_M");
+    // QR of every Y tile and every Z tile
+    DBuf kY, kZ;
+    HM_TRY(alloc(kY, np * sizeof(int)));
+    HM_TRY(alloc(kZ, np * sizeof(int)));
+    const int cap = c->cfg.rank > 0 ? r : r - c->cfg.oversample;
+    k_qr_tiles<<<(int)np, 256, 0, st>>>(g.pair_alpha.as<int>(), cu.int_idx.as<int>(), g.pair_color.as<int>(),
+                                        cu.ent.as<int>(), n, r, cap, c->cfg.rank, c->cfg.tol, c->cur.Y.as<double>(),
+                                        kY.as<int>());
+    k_qr_tiles<<<(int)np, 256, 0, st>>>(g.pair_alpha.as<int>(), cu.int_idx.as<int>(), g.pair_color.as<int>(),
+                                        cu.ent.as<int>(), n, r, cap, c->cfg.rank, c->cfg.tol, c->cur.Z.as<double>(),
+                                        kZ.as<int>());
+    HM_LAUNCH("qr_tiles");
+    HM_TRY(alloc(f.kU, np * sizeof(int)));
+    HM_TRY(alloc(f.kV, np * sizeof(int)));
+    DBuf sz;
+    HM_TRY(alloc(sz, 3 * (np + 1) * sizeof(int64_t)));
+    int64_t *sU = sz.as<int64_t>(), *sV = sU + (np + 1), *sB = sV + (np + 1);
+    k_factor_sizes<<<ceil_div(np, 256), 256, 0, st>>>(g.pair_alpha.as<int>(), cu.int_idx.as<int>(),
+                                                      g.pair_T.as<int>(), kY.as<int>(), kZ.as<int>(), cu.ent.as<int>(),
+                                                      np, f.kU.as<int>(), f.kV.as<int>(), sU, sV, sB);
+    HM_LAUNCH("factor_sizes");
+    HM_TRY(alloc(f.offU, (np + 1) * sizeof(int64_t)));
+    HM_TRY(alloc(f.offV, (np + 1) * sizeof(int64_t)));
+    HM_TRY(alloc(f.offB, (np + 1) * sizeof(int64_t)));
+    HM_TRY(scan_exclusive(sU, f.offU.as<int64_t>(), np, st));
+    HM_TRY(scan_exclusive(sV, f.offV.as<int64_t>(), np, st));
+    HM_TRY(scan_exclusive(sB, f.offB.as<int64_t>(), np, st));
+    HM_TRY(read_scalar(f.nU, f.offU.as<int64_t>() + np, st));
+    HM_TRY(read_scalar(f.nV, f.offV.as<int64_t>() + np, st));
+    HM_TRY(read_scalar(f.nB, f.offB.as<int64_t>() + np, st));
+    HM_TRY(alloc(f.U, std::max<int64_t>(f.nU, 1) * sizeof(double)));
+    HM_TRY(alloc(f.V, std::max<int64_t>(f.nV, 1) * sizeof(double)));
+    HM_TRY(alloc(f.B, std::max<int64_t>(f.nB, 1) * sizeof(double)));
+    k_pack<<<(int)np, 128, 0, st>>>(g.pair_alpha.as<int>(), cu.int_idx.as<int>(), g.pair_color.as<int>(),
+                                    g.pair_T.as<int>(), cu.ent.as<int>(), n, r, f.kU.as<int>(), f.kV.as<int>(),
+                                    f.offU.as<int64_t>(), f.offV.as<int64_t>(), c->cur.Y.as<double>(),
+                                    c->cur.Z.as<double>(), f.U.as<double>(), f.V.as<double>());
+    HM_LAUNCH("pack");
+    const size_t smem = (4 * (size_t)r * r + r) * sizeof(double);
+    HM_CUDA(cudaFuncSetAttribute(k_core, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_core<<<(int)np, 32, smem, st>>>(g.pair_alpha.as<int>(), cu.int_idx.as<int>(), cu.ent.as<int>(), r,
+                                      f.kU.as<int>(), f.kV.as<int>(), f.offU.as<int64_t>(), f.offV.as<int64_t>(),
+                                      f.offB.as<int64_t>(), f.U.as<double>(), f.V.as<double>(), c->GO.as<double>(),
+                                      c->GP.as<double>(), c->scratch_a.as<double>(), f.B.as<double>());
+    HM_LAUNCH("core");
+    std::vector<int> hk;
+    HM_TRY(to_host(hk, f.kU.p, np, st));
+    f.max_k = 0;
+    for (int v : hk) f.max_k = std::max(f.max_k, v);
+    HM_TRY(to_host(hk, f.kV.p, np, st));
+    for (int v : hk) f.max_k = std::max(f.max_k, v);
+    f.done = true;
+    return ok();
+}
+
+// ---------------------------------------------------------------------------
+// K11 leaf blocks
+// ---------------------------------------------------------------------------
+
+__global__ void k_leaf_sizes(const int *pair_alpha, const int *pair_col, const int *ent, int64_t np, int64_t *sz) {
+    int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (p >= np) return;
+    const int *ea = ent + (int64_t)pair_alpha[p] * ENT_FIELDS, *eb = ent + (int64_t)pair_col[p] * ENT_FIELDS;
+    sz[p] = (int64_t)(ea[4] - ea[3]) * (eb[4] - eb[3]);
+}
+
+__global__ void k_leaf_extract(const int *pair_alpha, const int *pair_col, const int *pair_color, const int *ent,
+                               int64_t n, int m, const int64_t *off, const double *Y, double *D) {
+    const int64_t p = blockIdx.x;
+    const int *ea = ent + (int64_t)pair_alpha[p] * ENT_FIELDS, *eb = ent + (int64_t)pair_col[p] * ENT_FIELDS;
+    const int ma = ea[4] - ea[3], mb = eb[4] - eb[3];
+    const double *Yt = Y + ((int64_t)pair_color[p] * n + ea[3]) * m;
+    for (int o = threadIdx.x; o < ma * mb; o += blockDim.x) D[off[p] + o] = Yt[(int64_t)(o / mb) * m + o % mb];
+}
+
+Err extract_leaf(hm_ctx *c) {
+    cudaStream_t st = c->st;
+    const Coloring &g = c->colorings[c->L + 1];
+    const Cut &cu = c->cuts[c->L];
+    Leaf &lf = c->leaf;
+    lf = Leaf();
+    lf.n_pairs = g.n_pairs;
+    lf.m_max = g.m_cols;
+    const int64_t np = g.n_pairs;
+    DBuf sz;
+    HM_TRY(alloc(sz, (np + 1) * sizeof(int64_t)));
+    HM_TRY(alloc(lf.offD, (np + 1) * sizeof(int64_t)));
+    k_leaf_sizes<<<ceil_div(np, 256), 256, 0, st>>>(g.pair_alpha.as<int>(), cu.near_idx.as<int>(), cu.ent.as<int>(), np,
+                                                    sz.as<int64_t>());
+    HM_LAUNCH("leaf_sizes");
+    HM_TRY(scan_exclusive(sz.as<int64_t>(), lf.offD.as<int64_t>(), np, st));
+    HM_TRY(read_scalar(lf.nD, lf.offD.as<int64_t>() + np, st));
+    HM_TRY(alloc(lf.D, std::max<int64_t>(lf.nD, 1) * sizeof(double)));
+    k_leaf_extract<<<(int)np, 128, 0, st>>>(g.pair_alpha.as<int>(), cu.near_idx.as<int>(), g.pair_color.as<int>(),
+                                            cu.ent.as<int>(), c->n, g.m_cols, lf.offD.as<int64_t>(),
+                                            c->cur.Y.as<double>(), lf.D.as<double>());
+    HM_LAUNCH("leaf_extract");
+    lf.done = true;
+    return ok();
+}
+
+}  // namespace hm

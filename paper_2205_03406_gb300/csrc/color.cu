@@ -1,0 +1,496 @@
+// Constraint-incompatibility graph and DSatur colouring on the GPU
+// (Definition 4.1, Algorithm 2.3, Sections 4.1.2-4.1.3).
+//
+//  K4  vertices: the sampling constraint of pair (alpha, beta) is fixed by the
+//      key (beta, S_alpha), S_alpha = near(alpha) u int(alpha) (near(alpha) only
+//      for the leaf neighbour pairs).  A pair is a new vertex unless an earlier
+//      pair (alpha' < alpha, same beta) has the same S; such an alpha' must lie
+//      in S_alpha, so the test only scans S_alpha.  Vertex ids are in order of
+//      first occurrence.
+//      Edges: u ~ v iff beta_u != beta_v and (beta_u in S_v or beta_v in S_u).
+//      By the symmetry of the lists, beta_u in S_v <=> alpha_v in S(beta_u), so
+//      the neighbours of u are the vertices whose beta lies in S_u and the
+//      vertices of pairs whose row box lies in S(beta_u).  Each CTA marks them
+//      in a shared-memory bitmap and reads the sorted list back out of it.
+//  K5  DSatur in one CTA: the uncoloured vertex with the largest (saturation,
+//      degree, -id) takes the smallest colour unused by its neighbours.
+//      Vertices are spread over 1024 buckets whose maxima live in shared memory;
+//      each step re-scans only the bucket of the coloured vertex.
+#include "ctx.cuh"
+
+#include <algorithm>
+
+namespace hm {
+
+constexpr int DS_BUCKETS = 1024;
+constexpr int VID_BITS = 20;                 // vertex ids < 2^20
+constexpr unsigned long long VID_MASK = (1ull << VID_BITS) - 1;
+constexpr int DEG_SHIFT = 20, SAT_SHIFT = 40;
+constexpr unsigned long long UNCOLORED = 1ull << 62;
+constexpr int FORB_WORDS = MAX_COLORS / 32;
+
+__device__ __forceinline__ int find_in(const int *a, int lo, int hi, int key) {
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if (a[mid] < key) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+__global__ void k_pair_alpha(const int *ptr, int nc, int *alpha) {
+    int a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= nc) return;
+    for (int p = ptr[a]; p < ptr[a + 1]; ++p) alpha[p] = a;
+}
+
+// transpose index and first-occurrence test of every pair
+__global__ void k_pair_keys(const int *ptr, const int *col, const int *alpha, int64_t np, const int *sptr,
+                            const int *sidx, int *pairT, int64_t *first, int *rep) {
+    int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (p >= np) return;
+    const int a = alpha[p], b = col[p];
+    pairT[p] = ptr[b] + find_in(col, ptr[b], ptr[b + 1], a) - ptr[b];
+    const int s0 = sptr[a], s1 = sptr[a + 1];
+    int r = -1;
+    for (int t = s0; t < s1 && r < 0; ++t) {
+        const int a2 = sidx[t];
+        if (a2 >= a) break;
+        const int q = find_in(col, ptr[a2], ptr[a2 + 1], b);
+        if (q >= ptr[a2 + 1] || col[q] != b) continue;
+        if (sptr[a2 + 1] - sptr[a2] != s1 - s0) continue;
+        bool same = true;
+        for (int u = 0; u < s1 - s0 && same; ++u) same = sidx[sptr[a2] + u] == sidx[s0 + u];
+        if (same) r = q;
+    }
+    first[p] = (r < 0);
+    rep[p] = (r < 0) ? (int)p : r;
+}
+
+__global__ void k_vertex_ids(const int64_t *first, const int64_t *scan, const int *rep, const int *col,
+                             int64_t np, int *pair_vertex, int *vertex_pair, int *vertex_beta) {
+    int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (p >= np) return;
+    const int v = (int)scan[rep[p]];
+    pair_vertex[p] = v;
+    if (first[p]) {
+        vertex_pair[v] = (int)p;
+        vertex_beta[v] = col[p];
+    }
+}
+
+// vertices grouped by beta, in vertex order: box b's vertices are the first
+// occurrences among the pairs (a, b), a in list(b), taken in order of a.
+__global__ void k_vby_beta(const int *ptr, const int *pairT, const int64_t *first, const int *pair_vertex,
+                           int nc, int pass, int *cnt, const int64_t *off, int *out) {
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nc) return;
+    int k = 0;
+    for (int t = ptr[b]; t < ptr[b + 1]; ++t) {
+        const int p = pairT[t];  // pair (a, b)
+        if (first[p]) {
+            if (pass) out[off[b] + k] = pair_vertex[p];
+            ++k;
+        }
+    }
+    if (!pass) cnt[b] = k;
+}
+
+// neighbours of vertex u through a shared-memory bitmap over all vertices
+__global__ void k_edges(int64_t nv, const int *vertex_pair, const int *vertex_beta, const int *alpha,
+                        const int *ptr, const int *pair_vertex, const int *sptr, const int *sidx,
+                        const int *vb_ptr, const int *vb_idx, int pass, int *deg, const int64_t *adj_ptr,
+                        int *adj) {
+    extern __shared__ unsigned int bm[];
+    __shared__ int wsum[32];
+    const int u = blockIdx.x;
+    const int nw = (int)((nv + 31) >> 5);
+    for (int i = threadIdx.x; i < nw; i += blockDim.x) bm[i] = 0u;
+    __syncthreads();
+    const int au = alpha[vertex_pair[u]], bu = vertex_beta[u];
+    // beta_v in S_u, beta_v != beta_u
+    for (int t = sptr[au]; t < sptr[au + 1]; ++t) {
+        const int g = sidx[t];
+        if (g == bu) continue;
+        for (int q = vb_ptr[g] + threadIdx.x; q < vb_ptr[g + 1]; q += blockDim.x) {
+            const int v = vb_idx[q];
+            atomicOr(&bm[v >> 5], 1u << (v & 31));
+        }
+    }
+    // alpha_v in S(beta_u), beta_v != beta_u
+    for (int t = sptr[bu]; t < sptr[bu + 1]; ++t) {
+        const int a2 = sidx[t];
+        for (int p = ptr[a2] + threadIdx.x; p < ptr[a2 + 1]; p += blockDim.x) {
+            const int v = pair_vertex[p];
+            if (vertex_beta[v] == bu) continue;
+            atomicOr(&bm[v >> 5], 1u << (v & 31));
+        }
+    }
+    __syncthreads();
+    // contiguous word ranges per thread -> sorted output
+    const int per = (nw + blockDim.x - 1) / blockDim.x;
+    const int w0 = threadIdx.x * per, w1 = min(nw, w0 + per);
+    int c = 0;
+    for (int w = w0; w < w1; ++w) c += __popc(bm[w]);
+    if (!pass) {
+        c = block_sum(c, wsum);
+        if (threadIdx.x == 0) deg[u] = c;
+        return;
+    }
+    // exclusive prefix of c across threads
+    __shared__ int pre[1024];
+    pre[threadIdx.x] = c;
+    __syncthreads();
+    for (int o = 1; o < blockDim.x; o <<= 1) {
+        int v = (threadIdx.x >= o) ? pre[threadIdx.x - o] : 0;
+        __syncthreads();
+        pre[threadIdx.x] += v;
+        __syncthreads();
+    }
+    int64_t o = adj_ptr[u] + pre[threadIdx.x] - c;
+    for (int w = w0; w < w1; ++w) {
+        unsigned int x = bm[w];
+        while (x) {
+            const int bit = __ffs(x) - 1;
+            x &= x - 1;
+            adj[o++] = w * 32 + bit;
+        }
+    }
+}
+
+__global__ void k_dsatur_init(int64_t nv, const int *deg, unsigned long long *key, unsigned int *forb) {
+    int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (v >= nv) return;
+    key[v] = UNCOLORED | ((unsigned long long)deg[v] << DEG_SHIFT) | (VID_MASK - (unsigned long long)v);
+    for (int w = 0; w < FORB_WORDS; ++w) forb[v * FORB_WORDS + w] = 0u;
+}
+
+__device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v) {
+    for (int o = 16; o > 0; o >>= 1) {
+        unsigned long long t = __shfl_xor_sync(0xffffffffu, v, o);
+        v = t > v ? t : v;
+    }
+    return v;
+}
+
+// One CTA of 1024 threads; exactly nv steps, no waits on other blocks.
+__global__ void __launch_bounds__(1024) k_dsatur(int64_t nv, const int64_t *adj_ptr, const int *adj,
+                                                 unsigned long long *key, unsigned int *forb, int *color,
+                                                 int *status /* [0] = colours, [1] = error */) {
+    __shared__ unsigned long long bmax[DS_BUCKETS];
+    __shared__ unsigned long long red[32];
+    __shared__ int sel_v, sel_c, ncol;
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    unsigned long long m = 0;
+    for (int64_t v = t; v < nv; v += DS_BUCKETS) m = key[v] > m ? key[v] : m;
+    bmax[t] = m;
+    if (t == 0) ncol = 0;
+    __syncthreads();
+    for (int64_t step = 0; step < nv; ++step) {
+        unsigned long long k = warp_max_u64(bmax[t]);
+        if (lane == 0) red[w] = k;
+        __syncthreads();
+        if (w == 0) {
+            k = warp_max_u64(red[lane]);
+            const int v = (int)(VID_MASK - (k & VID_MASK));
+            // smallest colour not forbidden for v
+            const unsigned int word = forb[(int64_t)v * FORB_WORDS + lane];
+            const unsigned int freebits = ~word;
+            const unsigned int has = __ballot_sync(0xffffffffu, freebits != 0u);
+            if (lane == 0) {
+                sel_v = v;
+                sel_c = -1;
+            }
+            __syncwarp();
+            if (has) {
+                const int l0 = __ffs(has) - 1;
+                if (lane == l0) sel_c = l0 * 32 + __ffs(freebits) - 1;
+            }
+        }
+        __syncthreads();
+        const int v = sel_v, c = sel_c;
+        if (c < 0) {
+            if (t == 0) status[1] = 1;
+            return;  // uniform: every thread reads the same sel_c
+        }
+        const unsigned int bit = 1u << (c & 31);
+        for (int64_t e = adj_ptr[v] + t; e < adj_ptr[v + 1]; e += blockDim.x) {
+            const int u = adj[e];
+            unsigned long long ku = key[u];
+            if (ku & UNCOLORED) {
+                unsigned int *f = &forb[(int64_t)u * FORB_WORDS + (c >> 5)];
+                const unsigned int fw = *f;
+                if (!(fw & bit)) {
+                    *f = fw | bit;
+                    ku += 1ull << SAT_SHIFT;
+                    key[u] = ku;
+                    atomicMax(&bmax[u & (DS_BUCKETS - 1)], ku);
+                }
+            }
+        }
+        if (t == 0) {
+            key[v] = 0ull;
+            color[v] = c;
+            if (c + 1 > ncol) ncol = c + 1;
+        }
+        __syncthreads();
+        if (w == 0) {
+            const int b = v & (DS_BUCKETS - 1);
+            unsigned long long mm = 0;
+            for (int64_t x = b + (int64_t)lane * DS_BUCKETS; x < nv; x += 32ll * DS_BUCKETS)
+                mm = key[x] > mm ? key[x] : mm;
+            mm = warp_max_u64(mm);
+            if (lane == 0) bmax[b] = mm;
+        }
+        __syncthreads();
+    }
+    if (t == 0) status[0] = ncol;
+}
+
+__global__ void k_pair_color(const int *pair_vertex, const int *vertex_color, int64_t np, int *pair_color) {
+    int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (p < np) pair_color[p] = vertex_color[pair_vertex[p]];
+}
+
+__global__ void k_act_mark(const int *vertex_beta, const int *vertex_color, int64_t nv, int nc,
+                           unsigned char *act) {
+    int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (v < nv) act[(int64_t)vertex_color[v] * nc + vertex_beta[v]] = 1;
+}
+
+// colour c -> sorted active entries; one CTA per colour
+__global__ void k_act_by_color(const unsigned char *act, int nc, int pass, int *cnt, const int64_t *off,
+                               int *out) {
+    __shared__ int wsum[32];
+    __shared__ int pre[1024];
+    const int c = blockIdx.x;
+    const unsigned char *row = act + (int64_t)c * nc;
+    const int per = (nc + blockDim.x - 1) / blockDim.x;
+    const int b0 = threadIdx.x * per, b1 = min(nc, b0 + per);
+    int k = 0;
+    for (int b = b0; b < b1; ++b) k += row[b];
+    if (!pass) {
+        k = block_sum(k, wsum);
+        if (threadIdx.x == 0) cnt[c] = k;
+        return;
+    }
+    pre[threadIdx.x] = k;
+    __syncthreads();
+    for (int o = 1; o < blockDim.x; o <<= 1) {
+        int v = (threadIdx.x >= o) ? pre[threadIdx.x - o] : 0;
+        __syncthreads();
+        pre[threadIdx.x] += v;
+        __syncthreads();
+    }
+    int64_t o = off[c] + pre[threadIdx.x] - k;
+    for (int b = b0; b < b1; ++b)
+        if (row[b]) out[o++] = b;
+}
+
+// entry -> sorted colours it is active in
+__global__ void k_act_by_entry(const unsigned char *act, int nc, int chi, int pass, int *cnt,
+                               const int64_t *off, int *out) {
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nc) return;
+    int k = 0;
+    for (int c = 0; c < chi; ++c)
+        if (act[(int64_t)c * nc + b]) {
+            if (pass) out[off[b] + k] = c;
+            ++k;
+        }
+    if (!pass) cnt[b] = k;
+}
+
+__global__ void k_act_sizes(const int *act_box, int64_t na, const int *ent, int *sz) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= na) return;
+    const int *e = ent + (int64_t)act_box[i] * ENT_FIELDS;
+    sz[i] = e[4] - e[3];
+}
+
+// rows of every (colour, active entry): one warp per entry
+__global__ void k_act_rows(const int *act_box, int64_t na, const int *ent, const int64_t *rowoff, int *rows) {
+    int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (i >= na) return;
+    const int *e = ent + (int64_t)act_box[i] * ENT_FIELDS;
+    for (int r = e[3] + lane; r < e[4]; r += 32) rows[rowoff[i] + (r - e[3])] = r;
+}
+
+Err color_cut(hm_ctx *c, int level, bool leaf) {
+    cudaStream_t st = c->st;
+    const int l = leaf ? c->L : level;
+    if (l < 0 || l > c->L) return fail(HM_EINVAL, "colour: level out of range");
+    Cut &cu = c->cuts[l];
+    const int idx = leaf ? c->L + 1 : level;
+    if ((int)c->colorings.size() < c->L + 2) c->colorings.resize(c->L + 2);
+    Coloring &g = c->colorings[idx];
+    g = Coloring();
+    g.leaf = leaf;
+    g.level = l;
+    g.pair_ptr = leaf ? cu.near_ptr.as<int>() : cu.int_ptr.as<int>();
+    g.pair_col = leaf ? cu.near_idx.as<int>() : cu.int_idx.as<int>();
+    g.n_pairs = leaf ? cu.n_near : cu.n_int;
+    const int *sptr = leaf ? cu.near_ptr.as<int>() : cu.s_ptr.as<int>();
+    const int *sidx = leaf ? cu.near_idx.as<int>() : cu.s_idx.as<int>();
+    const int nc = cu.nc;
+    const int64_t np = g.n_pairs;
+    g.m_cols = c->cfg.r;
+    if (leaf) g.m_cols = cu.max_rows;
+    if (np == 0) {
+        g.done = true;
+        g.n_colors = 0;
+        std::vector<int> z(1, 0);
+        HM_TRY(to_dev(g.act_ptr, z, st));
+        std::vector<int> zc(nc + 1, 0);
+        HM_TRY(to_dev(g.ent_cptr, zc, st));
+        std::vector<int64_t> z64(1, 0);
+        HM_TRY(to_dev(g.act_rows_ptr, z64, st));
+        return ok();
+    }
+
+    HM_TRY(alloc(g.pair_alpha, np * sizeof(int)));
+    HM_TRY(alloc(g.pair_T, np * sizeof(int)));
+    HM_TRY(alloc(g.pair_vertex, np * sizeof(int)));
+    HM_TRY(alloc(g.pair_color, np * sizeof(int)));
+    DBuf first, fscan, rep;
+    HM_TRY(alloc(first, (np + 1) * sizeof(int64_t)));
+    HM_TRY(alloc(fscan, (np + 1) * sizeof(int64_t)));
+    HM_TRY(alloc(rep, np * sizeof(int)));
+    k_pair_alpha<<<ceil_div(nc, 128), 128, 0, st>>>(g.pair_ptr, nc, g.pair_alpha.as<int>());
+    k_pair_keys<<<ceil_div(np, 128), 128, 0, st>>>(g.pair_ptr, g.pair_col, g.pair_alpha.as<int>(), np, sptr, sidx,
+                                                   g.pair_T.as<int>(), first.as<int64_t>(), rep.as<int>());
+    HM_LAUNCH("pair_keys");
+    HM_TRY(scan_exclusive(first.as<int64_t>(), fscan.as<int64_t>(), np, st));
+    HM_TRY(read_scalar(g.n_vertices, fscan.as<int64_t>() + np, st));
+    const int64_t nv = g.n_vertices;
+    if (nv > (int64_t)VID_MASK) return fail(HM_ENOTSUP, "colour: more than 2^20 constraint sets");
+    HM_TRY(alloc(g.vertex_pair, nv * sizeof(int)));
+    HM_TRY(alloc(g.vertex_beta, nv * sizeof(int)));
+    HM_TRY(alloc(g.vertex_color, nv * sizeof(int)));
+    HM_TRY(alloc(g.vertex_degree, nv * sizeof(int)));
+    k_vertex_ids<<<ceil_div(np, 256), 256, 0, st>>>(first.as<int64_t>(), fscan.as<int64_t>(), rep.as<int>(),
+                                                    g.pair_col, np, g.pair_vertex.as<int>(),
+                                                    g.vertex_pair.as<int>(), g.vertex_beta.as<int>());
+    HM_LAUNCH("vertex_ids");
+
+    // vertices by beta
+    DBuf vcnt, vptr64, vptr, vidx;
+    HM_TRY(alloc(vcnt, nc * sizeof(int)));
+    HM_TRY(alloc(vptr64, (nc + 1) * sizeof(int64_t)));
+    HM_TRY(alloc(vidx, nv * sizeof(int)));
+    k_vby_beta<<<ceil_div(nc, 128), 128, 0, st>>>(g.pair_ptr, g.pair_T.as<int>(), first.as<int64_t>(),
+                                                  g.pair_vertex.as<int>(), nc, 0, vcnt.as<int>(), nullptr, nullptr);
+    HM_TRY(scan_counts_i32(vcnt.as<int>(), vptr64.as<int64_t>(), nc, st, c->scan_tmp));
+    k_vby_beta<<<ceil_div(nc, 128), 128, 0, st>>>(g.pair_ptr, g.pair_T.as<int>(), first.as<int64_t>(),
+                                                  g.pair_vertex.as<int>(), nc, 1, nullptr, vptr64.as<int64_t>(),
+                                                  vidx.as<int>());
+    HM_LAUNCH("vby_beta");
+    {
+        std::vector<int64_t> h;
+        HM_TRY(to_host(h, vptr64.p, nc + 1, st));
+        std::vector<int> h32(h.begin(), h.end());
+        HM_TRY(to_dev(vptr, h32, st));
+    }
+
+    // edges
+    const size_t bm_bytes = (size_t)((nv + 31) / 32) * 4;
+    if (bm_bytes > 200 * 1024) return fail(HM_ENOTSUP, "colour: vertex bitmap exceeds shared memory");
+    HM_CUDA(cudaFuncSetAttribute(k_edges, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    DBuf adj_ptr, adj;
+    HM_TRY(alloc(adj_ptr, (nv + 1) * sizeof(int64_t)));
+    k_edges<<<(int)nv, 256, bm_bytes, st>>>(nv, g.vertex_pair.as<int>(), g.vertex_beta.as<int>(),
+                                            g.pair_alpha.as<int>(), g.pair_ptr, g.pair_vertex.as<int>(), sptr, sidx,
+                                            vptr.as<int>(), vidx.as<int>(), 0, g.vertex_degree.as<int>(), nullptr,
+                                            nullptr);
+    HM_LAUNCH("edges count");
+    HM_TRY(scan_counts_i32(g.vertex_degree.as<int>(), adj_ptr.as<int64_t>(), nv, st, c->scan_tmp));
+    int64_t n_adj = 0;
+    HM_TRY(read_scalar(n_adj, adj_ptr.as<int64_t>() + nv, st));
+    g.n_edges = n_adj / 2;
+    HM_TRY(alloc(adj, n_adj * sizeof(int)));
+    k_edges<<<(int)nv, 256, bm_bytes, st>>>(nv, g.vertex_pair.as<int>(), g.vertex_beta.as<int>(),
+                                            g.pair_alpha.as<int>(), g.pair_ptr, g.pair_vertex.as<int>(), sptr, sidx,
+                                            vptr.as<int>(), vidx.as<int>(), 1, nullptr, adj_ptr.as<int64_t>(),
+                                            adj.as<int>());
+    HM_LAUNCH("edges fill");
+
+    // DSatur
+    DBuf key, forb, status;
+    HM_TRY(alloc(key, nv * sizeof(unsigned long long)));
+    HM_TRY(alloc(forb, nv * FORB_WORDS * sizeof(unsigned int)));
+    HM_TRY(alloc(status, 2 * sizeof(int)));
+    HM_CUDA(cudaMemsetAsync(status.p, 0, 2 * sizeof(int), st));
+    k_dsatur_init<<<ceil_div(nv, 256), 256, 0, st>>>(nv, g.vertex_degree.as<int>(), key.as<unsigned long long>(),
+                                                      forb.as<unsigned int>());
+    k_dsatur<<<1, 1024, 0, st>>>(nv, adj_ptr.as<int64_t>(), adj.as<int>(), key.as<unsigned long long>(),
+                                 forb.as<unsigned int>(), g.vertex_color.as<int>(), status.as<int>());
+    HM_LAUNCH("dsatur");
+    int hs[2];
+    HM_CUDA(cudaMemcpyAsync(hs, status.p, sizeof(hs), cudaMemcpyDeviceToHost, st));
+    HM_CUDA(cudaStreamSynchronize(st));
+    if (hs[1]) return fail(HM_ENOTSUP, "colour: more than 1024 colours");
+    g.n_colors = hs[0];
+    const int chi = g.n_colors;
+    k_pair_color<<<ceil_div(np, 256), 256, 0, st>>>(g.pair_vertex.as<int>(), g.vertex_color.as<int>(), np,
+                                                    g.pair_color.as<int>());
+    HM_LAUNCH("pair_color");
+
+    // active tables
+    DBuf act, cnt, off64;
+    HM_TRY(alloc(act, (size_t)chi * nc));
+    HM_CUDA(cudaMemsetAsync(act.p, 0, (size_t)chi * nc, st));
+    k_act_mark<<<ceil_div(nv, 256), 256, 0, st>>>(g.vertex_beta.as<int>(), g.vertex_color.as<int>(), nv, nc,
+                                                   act.as<unsigned char>());
+    HM_TRY(alloc(cnt, std::max(chi, nc) * sizeof(int)));
+    HM_TRY(alloc(off64, (std::max(chi, nc) + 1) * sizeof(int64_t)));
+    k_act_by_color<<<chi, 1024, 0, st>>>(act.as<unsigned char>(), nc, 0, cnt.as<int>(), nullptr, nullptr);
+    HM_TRY(scan_counts_i32(cnt.as<int>(), off64.as<int64_t>(), chi, st, c->scan_tmp));
+    std::vector<int64_t> hoff;
+    HM_TRY(to_host(hoff, off64.p, chi + 1, st));
+    const int64_t na = hoff[chi];
+    HM_TRY(alloc(g.act_box, na * sizeof(int)));
+    k_act_by_color<<<chi, 1024, 0, st>>>(act.as<unsigned char>(), nc, 1, nullptr, off64.as<int64_t>(),
+                                         g.act_box.as<int>());
+    HM_LAUNCH("act_by_color");
+    {
+        std::vector<int> h32(hoff.begin(), hoff.end());
+        HM_TRY(to_dev(g.act_ptr, h32, st));
+    }
+    k_act_by_entry<<<ceil_div(nc, 128), 128, 0, st>>>(act.as<unsigned char>(), nc, chi, 0, cnt.as<int>(), nullptr,
+                                                      nullptr);
+    HM_TRY(scan_counts_i32(cnt.as<int>(), off64.as<int64_t>(), nc, st, c->scan_tmp));
+    {
+        std::vector<int64_t> h;
+        HM_TRY(to_host(h, off64.p, nc + 1, st));
+        HM_TRY(alloc(g.ent_col, std::max<int64_t>(h[nc], 1) * sizeof(int)));
+        k_act_by_entry<<<ceil_div(nc, 128), 128, 0, st>>>(act.as<unsigned char>(), nc, chi, 1, nullptr,
+                                                          off64.as<int64_t>(), g.ent_col.as<int>());
+        HM_LAUNCH("act_by_entry");
+        std::vector<int> h32(h.begin(), h.end());
+        HM_TRY(to_dev(g.ent_cptr, h32, st));
+    }
+    // rows of each colour
+    {
+        DBuf sz, rowoff;
+        HM_TRY(alloc(sz, std::max<int64_t>(na, 1) * sizeof(int)));
+        HM_TRY(alloc(rowoff, (na + 1) * sizeof(int64_t)));
+        k_act_sizes<<<ceil_div(na, 256), 256, 0, st>>>(g.act_box.as<int>(), na, cu.ent.as<int>(), sz.as<int>());
+        HM_TRY(scan_counts_i32(sz.as<int>(), rowoff.as<int64_t>(), na, st, c->scan_tmp));
+        std::vector<int64_t> hro;
+        HM_TRY(to_host(hro, rowoff.p, na + 1, st));
+        g.n_act_rows = hro[na];
+        HM_TRY(alloc(g.act_rows, std::max<int64_t>(g.n_act_rows, 1) * sizeof(int)));
+        k_act_rows<<<ceil_div(na * 32, 256), 256, 0, st>>>(g.act_box.as<int>(), na, cu.ent.as<int>(),
+                                                           rowoff.as<int64_t>(), g.act_rows.as<int>());
+        HM_LAUNCH("act_rows");
+        std::vector<int64_t> crp(chi + 1);
+        for (int k = 0; k <= chi; ++k) crp[k] = hro[hoff[k]];
+        HM_TRY(to_dev(g.act_rows_ptr, crp, st));
+    }
+    HM_CUDA(cudaStreamSynchronize(st));
+    g.done = true;
+    return ok();
+}
+
+}  // namespace hm

@@ -1,0 +1,149 @@
+// Internal state of one compression job (the opaque hm_ctx of hm.h) and the
+// interfaces between the modules: tree.cu, color.cu, sample.cu, sample_tc.cu,
+// peel.cu, basis.cu, apply.cu and the C ABI in hm_api.cu.
+#pragma once
+
+#include "common.cuh"
+
+namespace hm {
+
+constexpr int QBITS = 21;       // integer grid: 2^21 cells per dimension
+constexpr int MAX_LEVELS = 22;  // levels 0..21
+constexpr int MAX_COLORS = 1024;
+constexpr int BOX_FIELDS = 8;   // start, end, a0, a1, a2, parent, leaf, gid
+constexpr int ENT_FIELDS = 8;   // level, index, gid, start, end, a0, a1, a2
+
+// One level of the tree: its boxes, BOX_FIELDS int32 each.
+struct Level {
+    int nb = 0;
+    DBuf box;
+};
+
+// A cut: level-l boxes plus carried leaves of coarser levels, in Morton order.
+struct Cut {
+    int nc = 0;
+    DBuf ent;        // int32 [nc][ENT_FIELDS]
+    DBuf parent;     // int32 [nc]: entry of cut l-1 holding this entry (l >= 1)
+    DBuf kid_begin;  // int32 [nc]: first entry of cut l+1 inside this entry
+    DBuf kid_end;    // int32 [nc]
+    DBuf pt2ent;     // int32 [n]: entry holding each sorted point
+    DBuf near_ptr, near_idx;  // CSR, sorted by entry
+    DBuf int_ptr, int_idx;
+    DBuf s_ptr, s_idx;        // near u int, sorted (the constraint zero sets)
+    int64_t n_near = 0, n_int = 0;
+    int max_rows = 0;         // largest entry
+};
+
+// Graph colouring of one cut (admissible pairs) or of the leaf neighbour pairs.
+struct Coloring {
+    bool done = false;
+    bool leaf = false;
+    int level = 0;            // cut level whose pairs are coloured
+    int64_t n_pairs = 0, n_vertices = 0, n_edges = 0;
+    int n_colors = 0;
+    const int *pair_ptr = nullptr;   // CSR of pairs by row entry (borrowed: int or near list)
+    const int *pair_col = nullptr;
+    DBuf pair_alpha;      // int32 [n_pairs]
+    DBuf pair_T;          // int32 [n_pairs]: index of the transposed pair (beta, alpha)
+    DBuf pair_vertex;     // int32 [n_pairs]
+    DBuf pair_color;      // int32 [n_pairs]
+    DBuf vertex_pair;     // int32 [n_vertices]: first pair of each vertex
+    DBuf vertex_beta;     // int32
+    DBuf vertex_color;    // int32
+    DBuf vertex_degree;   // int32
+    DBuf act_ptr, act_box;     // colour -> active entries (CSR, sorted)
+    DBuf ent_cptr, ent_col;    // entry -> colours it is active in (CSR, sorted)
+    DBuf act_rows_ptr;         // colour -> offset into act_rows (int64, chi+1)
+    DBuf act_rows;             // int32: rows (sorted points) active in each colour
+    int64_t n_act_rows = 0;
+    int m_cols = 0;            // columns per colour: r, or m_max at the leaf
+};
+
+// Low-rank factors of one level: U_p (|I_a| x kU, row-major), V_p (|I_b| x kV),
+// B_p (kU x kV, row-major) for every admissible pair p.
+struct Factors {
+    bool done = false;
+    int64_t n_pairs = 0;
+    DBuf kU, kV;              // int32
+    DBuf offU, offV, offB;    // int64 element offsets
+    DBuf U, V, B;
+    int64_t nU = 0, nV = 0, nB = 0;
+    int max_k = 0;
+};
+
+struct Leaf {
+    bool done = false;
+    int64_t n_pairs = 0;
+    DBuf offD;                // int64
+    DBuf D;
+    int64_t nD = 0;
+    int m_max = 0;
+};
+
+struct Samples {
+    int level = -100;
+    int chi = 0, cols = 0;    // colours, columns per colour
+    DBuf Y, Z;                // double [chi][n][cols]
+};
+
+}  // namespace hm
+
+struct hm_ctx {
+    hm_config cfg;
+    cudaStream_t st = nullptr;
+    std::string last_error;
+    int stage = 0;            // 0 created, 1 tree built, 2 compressed
+
+    // points
+    int64_t n = 0;
+    int d = 0;
+    double lo[3] = {0, 0, 0};
+    double side = 1.0;
+    hm::DBuf xs;              // double [n][3], sorted (Morton) order; unused dims are 0
+    hm::DBuf perm;            // int32 [n]: original index of sorted point i
+    hm::DBuf qs;              // int32 [n][3]: grid coordinates, sorted order
+
+    int L = 0;
+    std::vector<hm::Level> levels;
+    std::vector<hm::Cut> cuts;
+    std::vector<int> level_off;     // gid offset of each level
+
+    std::vector<hm::Coloring> colorings;   // index l (2..L); index L+1 = leaf
+    std::vector<hm::Factors> factors;      // index l
+    hm::Leaf leaf;
+    std::vector<hm::Samples> kept;         // per level when cfg.keep_samples
+    hm::Samples cur;                       // the current level's samples
+    hm::DBuf GO, GP;                       // current level's Gaussians [n][r]
+    int gauss_level = -100;
+
+    // scratch
+    hm::DBuf scratch_a, scratch_b, scratch_c, scratch_d, scan_tmp;
+
+    hm_info info;
+    double t_sample = 0.0;
+};
+
+namespace hm {
+
+// tree.cu
+Err build_tree(hm_ctx *c, const double *points_dev, int64_t n);
+// color.cu
+Err color_cut(hm_ctx *c, int level, bool leaf);
+// sample.cu
+Err make_gaussians(hm_ctx *c, int level);
+Err sample_level(hm_ctx *c, const hm_op *op, int level, bool leaf);
+Err op_apply_dense_vectors(hm_ctx *c, const hm_op *op, const double *x_sorted, double *y_sorted,
+                           int nrhs, int trans);
+// sample_tc.cu
+Err sample_tc(hm_ctx *c, int level, int kernel);
+bool tc_supported(const hm_ctx *c);
+// peel.cu
+Err peel_level(hm_ctx *c, int level, bool leaf);
+// basis.cu
+Err bases_and_cores(hm_ctx *c, int level);
+Err extract_leaf(hm_ctx *c);
+// apply.cu
+Err apply_sorted(hm_ctx *c, const double *x_sorted, double *y_sorted, int nrhs, int trans);
+Err permute_rows(hm_ctx *c, const double *in, double *out, int nrhs, bool to_sorted);
+
+}  // namespace hm

@@ -1,0 +1,526 @@
+// C ABI of include/hm.h: argument checks, call-order state machine, the
+// level loop of Algorithm 4.1, apply, the Section 5 error estimate and exports.
+#include "ctx.cuh"
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+
+namespace hm {
+thread_local cudaStream_t g_alloc_stream = nullptr;
+}
+
+using namespace hm;
+
+namespace {
+
+struct StreamScope {
+    cudaStream_t prev;
+    explicit StreamScope(cudaStream_t s) : prev(g_alloc_stream) { g_alloc_stream = s; }
+    ~StreamScope() { g_alloc_stream = prev; }
+};
+
+hm_status finish(hm_ctx *c, const Err &e) {
+    if (e) {
+        c->last_error = e.msg;
+        return e.code;
+    }
+    return HM_OK;
+}
+
+hm_status bad(hm_ctx *c, hm_status code, const char *msg) {
+    if (c) c->last_error = msg;
+    return code;
+}
+
+__global__ void k_start_vector(int64_t n, unsigned long long seed, double *x) {
+    // Philox Gaussian start vector, counter (0, i, 0, 2 << 8), duplicated in both columns
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const unsigned int M0 = 0xD2511F53u, M1 = 0xCD9E8D57u, W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+    uint4 c = make_uint4(0u, (unsigned)i, 0u, 2u << 8);
+    uint2 k = make_uint2((unsigned)(seed & 0xffffffffu), (unsigned)(seed >> 32));
+    for (int r = 0; r < 10; ++r) {
+        if (r) {
+            k.x += W0;
+            k.y += W1;
+        }
+        const unsigned int hi0 = __umulhi(M0, c.x), lo0 = M0 * c.x;
+        const unsigned int hi1 = __umulhi(M1, c.z), lo1 = M1 * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    }
+    const unsigned long long a = ((unsigned long long)c.y << 32) | c.x, b = ((unsigned long long)c.w << 32) | c.z;
+    const double u1 = __dmul_rn(__dadd_rn((double)(a >> 12), 0.5), 0x1.0p-52);
+    const double u2 = __dmul_rn(__dadd_rn((double)(b >> 12), 0.5), 0x1.0p-52);
+    const double z = __dmul_rn(sqrt(__dmul_rn(-2.0, log(u1))), cos(__dmul_rn(2.0 * M_PI, u2)));
+    x[i * 2] = z;
+    x[i * 2 + 1] = z;
+}
+
+__global__ void k_colsq(const double *x, int64_t n, int nrhs, double *out) {
+    __shared__ double sh[32];
+    for (int j = 0; j < nrhs; ++j) {
+        double s = 0.0;
+        for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+            s = fma(x[i * nrhs + j], x[i * nrhs + j], s);
+        s = block_sum(s, sh);
+        if (threadIdx.x == 0) atomicAdd(&out[j], s);
+    }
+}
+
+__global__ void k_axpby2(const double *a, const double *b, int64_t n, double *out) {
+    // out(:,0) = a(:,0) - b(:,0); out(:,1) = b(:,1)
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    out[i * 2] = a[i * 2] - b[i * 2];
+    out[i * 2 + 1] = b[i * 2 + 1];
+}
+
+__global__ void k_scale2(double *x, int64_t n, double s0, double s1) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    x[i * 2] *= s0;
+    x[i * 2 + 1] *= s1;
+}
+
+Err op_apply_vectors(hm_ctx *c, const hm_op *op, const double *x, double *y, int trans, DBuf &t1, DBuf &t2) {
+    // y = A x or A^* x for row-major sorted [n][2] vectors
+    if (op->kind == HM_OP_CALLBACK) {
+        HM_TRY(ensure(t1, c->n * 2 * sizeof(double)));
+        HM_TRY(ensure(t2, c->n * 2 * sizeof(double)));
+        // sorted row-major -> original column-major
+        HM_TRY(permute_rows(c, x, t1.as<double>(), 2, false));
+        const int rc = op->apply(op->user, trans, t1.as<double>(), t2.as<double>(), 2, (void *)c->st);
+        if (rc) return fail(HM_EOP, "black-box operator returned " + std::to_string(rc));
+        return permute_rows(c, t2.as<double>(), y, 2, true);
+    }
+    return op_apply_dense_vectors(c, op, x, y, 2, trans);
+}
+
+}  // namespace
+
+extern "C" {
+
+hm_status hm_create(hm_ctx **out, const hm_config *cfg, void *stream) {
+    if (!out || !cfg) return HM_EINVAL;
+    *out = nullptr;
+    if (cfg->d < 1 || cfg->d > 3 || cfg->leaf_size < 1 || cfg->r < 1 || cfg->r > 64) return HM_EINVAL;
+    if ((cfg->rank > 0) == (cfg->tol > 0.0) || cfg->rank > cfg->r || cfg->rank < 0 || !(cfg->tol >= 0.0))
+        return HM_EINVAL;
+    if (cfg->tol > 0.0 && (cfg->oversample < 0 || cfg->oversample >= cfg->r)) return HM_EINVAL;
+    if (cfg->precision != HM_FP64 && cfg->precision != HM_MIXED_BF16X6) return HM_EINVAL;
+    if (cfg->uniform_depth < 0 || cfg->uniform_depth > QBITS) return HM_EINVAL;
+    hm_ctx *c = new (std::nothrow) hm_ctx();
+    if (!c) return HM_ENOMEM;
+    c->cfg = *cfg;
+    c->st = (cudaStream_t)stream;
+    std::memset(&c->info, 0, sizeof(c->info));
+    int dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess) {
+        cudaMemPool_t pool;
+        if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+            uint64_t thr = UINT64_MAX;
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+        }
+    }
+    cudaGetLastError();
+    *out = c;
+    return HM_OK;
+}
+
+hm_status hm_destroy(hm_ctx *c) {
+    if (!c) return HM_OK;
+    {
+        StreamScope ss(c->st);
+        cudaStream_t st = c->st;
+        delete c;
+        cudaStreamSynchronize(st);
+    }
+    cudaGetLastError();
+    return HM_OK;
+}
+
+hm_status hm_tree_build(hm_ctx *c, const double *points_dev, int64_t n) {
+    if (!c) return HM_EINVAL;
+    if (!points_dev || n < 1 || n > (1ll << 30)) return bad(c, HM_EINVAL, "tree_build: bad points or n");
+    StreamScope ss(c->st);
+    c->colorings.clear();
+    c->factors.clear();
+    c->kept.clear();
+    c->leaf = Leaf();
+    c->stage = 0;
+    Err e = build_tree(c, points_dev, n);
+    if (e) return finish(c, e);
+    c->colorings.resize(c->L + 2);
+    c->factors.resize(c->L + 1);
+    c->stage = 1;
+    return HM_OK;
+}
+
+hm_status hm_color(hm_ctx *c, int level, int *n_colors) {
+    if (!c) return HM_EINVAL;
+    if (c->stage < 1) return bad(c, HM_ESTATE, "color: build the tree first");
+    const bool leaf = level == HM_LEVEL_LEAF;
+    if (!leaf && (level < 2 || level > c->L)) return bad(c, HM_EINVAL, "color: level out of range");
+    StreamScope ss(c->st);
+    Err e = color_cut(c, level, leaf);
+    if (e) return finish(c, e);
+    if (n_colors) *n_colors = c->colorings[leaf ? c->L + 1 : level].n_colors;
+    return HM_OK;
+}
+
+hm_status hm_sample(hm_ctx *c, const hm_op *op, int level) {
+    if (!c || !op) return HM_EINVAL;
+    if (c->stage < 1) return bad(c, HM_ESTATE, "sample: build the tree first");
+    const bool leaf = level == HM_LEVEL_LEAF;
+    if (!leaf && (level < 2 || level > c->L)) return bad(c, HM_EINVAL, "sample: level out of range");
+    const int idx = leaf ? c->L + 1 : level;
+    if (!c->colorings[idx].done) return bad(c, HM_ESTATE, "sample: colour the level first");
+    if (op->kind == HM_OP_CALLBACK && !op->apply) return bad(c, HM_EINVAL, "sample: null callback");
+    if (op->kind == HM_OP_DENSE && !op->dense_dev) return bad(c, HM_EINVAL, "sample: null dense matrix");
+    StreamScope ss(c->st);
+    Err e;
+    if (!leaf) e = make_gaussians(c, level);
+    if (!e) e = sample_level(c, op, level, leaf);
+    if (!e) {
+        cudaError_t ce = cudaStreamSynchronize(c->st);
+        if (ce != cudaSuccess) e = fail(HM_ECUDA, cudaGetErrorString(ce));
+    }
+    return finish(c, e);
+}
+
+static Err keep_current(hm_ctx *c, int idx, bool leaf) {
+    if (!c->cfg.keep_samples) return ok();
+    if ((int)c->kept.size() < c->L + 2) c->kept.resize(c->L + 2);
+    Samples &k = c->kept[idx];
+    const Samples &s = c->cur;
+    k.level = s.level;
+    k.chi = s.chi;
+    k.cols = s.cols;
+    const size_t bytes = (size_t)s.chi * c->n * s.cols * sizeof(double);
+    HM_TRY(alloc(k.Y, bytes));
+    HM_CUDA(cudaMemcpyAsync(k.Y.p, s.Y.p, bytes, cudaMemcpyDeviceToDevice, c->st));
+    if (!leaf) {
+        HM_TRY(alloc(k.Z, bytes));
+        HM_CUDA(cudaMemcpyAsync(k.Z.p, s.Z.p, bytes, cudaMemcpyDeviceToDevice, c->st));
+    }
+    return ok();
+}
+
+static Err compress_all(hm_ctx *c, const hm_op *op) {
+    const auto t0 = std::chrono::steady_clock::now();
+    std::vector<cudaEvent_t> ev;
+    auto rec = [&](void) -> Err {
+        cudaEvent_t e;
+        HM_CUDA(cudaEventCreate(&e));
+        HM_CUDA(cudaEventRecord(e, c->st));
+        ev.push_back(e);
+        return ok();
+    };
+    Err err;
+    int64_t cols_total = 0;
+    for (int l = 2; l <= c->L && !err; ++l) {
+        err = color_cut(c, l, false);
+        if (err) break;
+        const Coloring &g = c->colorings[l];
+        if (g.n_pairs == 0 || g.n_colors == 0) {
+            c->factors[l] = Factors();
+            c->factors[l].done = true;
+            continue;
+        }
+        if ((err = make_gaussians(c, l))) break;
+        if ((err = rec())) break;
+        if ((err = sample_level(c, op, l, false))) break;
+        if ((err = rec())) break;
+        cols_total += 2ll * g.n_colors * g.m_cols;
+        if ((err = peel_level(c, l, false))) break;
+        if ((err = keep_current(c, l, false))) break;
+        if ((err = bases_and_cores(c, l))) break;
+    }
+    if (!err) err = color_cut(c, 0, true);
+    if (!err) {
+        const Coloring &g = c->colorings[c->L + 1];
+        if (!(err = rec()) && !(err = sample_level(c, op, HM_LEVEL_LEAF, true)) && !(err = rec())) {
+            cols_total += (int64_t)g.n_colors * g.m_cols;
+            err = peel_level(c, 0, true);
+            if (!err) err = keep_current(c, c->L + 1, true);
+            if (!err) err = extract_leaf(c);
+        }
+    }
+    cudaError_t ce = cudaStreamSynchronize(c->st);
+    if (!err && ce != cudaSuccess) err = fail(HM_ECUDA, std::string("compress: ") + cudaGetErrorString(ce));
+    double ts = 0.0;
+    for (size_t i = 0; i + 1 < ev.size(); i += 2) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, ev[i], ev[i + 1]) == cudaSuccess) ts += ms * 1e-3;
+    }
+    for (auto e : ev) cudaEventDestroy(e);
+    if (err) return err;
+    c->t_sample = ts;
+    hm_info &in = c->info;
+    std::memset(&in, 0, sizeof(in));
+    in.n = c->n;
+    in.L = c->L;
+    for (auto &lv : c->levels) in.n_boxes += lv.nb;
+    int64_t floats = 0;
+    for (int l = 2; l <= c->L && l < 31; ++l) {
+        in.colors[l] = c->colorings[l].n_colors;
+        in.pairs[l] = c->colorings[l].n_pairs;
+        in.vertices[l] = c->colorings[l].n_vertices;
+        const Factors &f = c->factors[l];
+        floats += f.nU + f.nV + f.nB;
+        in.max_rank = std::max(in.max_rank, f.max_k);
+    }
+    if (c->L + 1 < 32) {
+        in.colors[c->L + 1] = c->colorings[c->L + 1].n_colors;
+        in.pairs[c->L + 1] = c->colorings[c->L + 1].n_pairs;
+        in.vertices[c->L + 1] = c->colorings[c->L + 1].n_vertices;
+    }
+    floats += c->leaf.nD;
+    in.factor_floats = floats;
+    in.matvec_cols = cols_total;
+    in.seconds_sample = ts;
+    in.seconds_total = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    return ok();
+}
+
+hm_status hm_compress(hm_ctx *c, const hm_op *op) {
+    if (!c || !op) return HM_EINVAL;
+    if (c->stage < 1) return bad(c, HM_ESTATE, "compress: build the tree first");
+    if (op->kind == HM_OP_CALLBACK && !op->apply) return bad(c, HM_EINVAL, "compress: null callback");
+    if (op->kind == HM_OP_DENSE && !op->dense_dev) return bad(c, HM_EINVAL, "compress: null dense matrix");
+    if (op->kind == HM_OP_KERNEL && (op->kernel < HM_K_LOG || op->kernel > HM_K_EXP))
+        return bad(c, HM_EINVAL, "compress: unknown kernel");
+    StreamScope ss(c->st);
+    c->stage = 1;
+    c->kept.clear();
+    Err e = compress_all(c, op);
+    if (e) return finish(c, e);
+    c->stage = 2;
+    return HM_OK;
+}
+
+hm_status hm_apply(hm_ctx *c, const double *x, double *y, int64_t nrhs, int trans) {
+    if (!c) return HM_EINVAL;
+    if (c->stage < 2) return bad(c, HM_ESTATE, "apply: compress first");
+    if (!x || !y || nrhs < 1 || nrhs > 64) return bad(c, HM_EINVAL, "apply: bad vectors");
+    StreamScope ss(c->st);
+    DBuf xs, ys;
+    Err e = alloc(xs, c->n * nrhs * sizeof(double));
+    if (!e) e = alloc(ys, c->n * nrhs * sizeof(double));
+    if (!e) e = permute_rows(c, x, xs.as<double>(), (int)nrhs, true);
+    if (!e) e = apply_sorted(c, xs.as<double>(), ys.as<double>(), (int)nrhs, trans ? 1 : 0);
+    if (!e) e = permute_rows(c, ys.as<double>(), y, (int)nrhs, false);
+    if (!e) {
+        cudaError_t ce = cudaStreamSynchronize(c->st);
+        if (ce != cudaSuccess) e = fail(HM_ECUDA, cudaGetErrorString(ce));
+    }
+    return finish(c, e);
+}
+
+hm_status hm_relerr(hm_ctx *c, const hm_op *op, int iters, double *err) {
+    if (!c || !op || !err) return HM_EINVAL;
+    if (c->stage < 2) return bad(c, HM_ESTATE, "relerr: compress first");
+    if (iters < 1) return bad(c, HM_EINVAL, "relerr: iters < 1");
+    StreamScope ss(c->st);
+    const int64_t n = c->n;
+    DBuf x, ax, hx, w, z1, z2, sq, t1, t2;
+    Err e;
+    auto run = [&]() -> Err {
+        HM_TRY(alloc(x, n * 2 * sizeof(double)));
+        HM_TRY(alloc(ax, n * 2 * sizeof(double)));
+        HM_TRY(alloc(hx, n * 2 * sizeof(double)));
+        HM_TRY(alloc(w, n * 2 * sizeof(double)));
+        HM_TRY(alloc(sq, 2 * sizeof(double)));
+        const int g = ceil_div(n, 256);
+        k_start_vector<<<g, 256, 0, c->st>>>(n, (unsigned long long)c->cfg.seed + 1ull, x.as<double>());
+        HM_LAUNCH("start_vector");
+        double lam[2] = {0, 0};
+        {  // normalise the start vector
+            HM_CUDA(cudaMemsetAsync(sq.p, 0, 2 * sizeof(double), c->st));
+            k_colsq<<<64, 256, 0, c->st>>>(x.as<double>(), n, 2, sq.as<double>());
+            double h[2];
+            HM_CUDA(cudaMemcpyAsync(h, sq.p, sizeof(h), cudaMemcpyDeviceToHost, c->st));
+            HM_CUDA(cudaStreamSynchronize(c->st));
+            k_scale2<<<g, 256, 0, c->st>>>(x.as<double>(), n, 1.0 / sqrt(h[0]), 1.0 / sqrt(h[1]));
+        }
+        for (int it = 0; it < iters; ++it) {
+            // w = M x: col 0 (A~ - A) x0, col 1 A x1
+            HM_TRY(op_apply_vectors(c, op, x.as<double>(), ax.as<double>(), 0, t1, t2));
+            HM_TRY(apply_sorted(c, x.as<double>(), hx.as<double>(), 2, 0));
+            k_axpby2<<<g, 256, 0, c->st>>>(hx.as<double>(), ax.as<double>(), n, w.as<double>());
+            // x = M^* w
+            HM_TRY(op_apply_vectors(c, op, w.as<double>(), ax.as<double>(), 1, t1, t2));
+            HM_TRY(apply_sorted(c, w.as<double>(), hx.as<double>(), 2, 1));
+            k_axpby2<<<g, 256, 0, c->st>>>(hx.as<double>(), ax.as<double>(), n, x.as<double>());
+            HM_LAUNCH("power step");
+            HM_CUDA(cudaMemsetAsync(sq.p, 0, 2 * sizeof(double), c->st));
+            k_colsq<<<64, 256, 0, c->st>>>(x.as<double>(), n, 2, sq.as<double>());
+            double h[2];
+            HM_CUDA(cudaMemcpyAsync(h, sq.p, sizeof(h), cudaMemcpyDeviceToHost, c->st));
+            HM_CUDA(cudaStreamSynchronize(c->st));
+            lam[0] = sqrt(h[0]);
+            lam[1] = sqrt(h[1]);
+            k_scale2<<<g, 256, 0, c->st>>>(x.as<double>(), n, lam[0] > 0 ? 1.0 / lam[0] : 0.0,
+                                           lam[1] > 0 ? 1.0 / lam[1] : 0.0);
+        }
+        *err = lam[1] > 0.0 ? sqrt(lam[0]) / sqrt(lam[1]) : 0.0;
+        return ok();
+    };
+    e = run();
+    return finish(c, e);
+}
+
+hm_status hm_get_info(hm_ctx *c, hm_info *out) {
+    if (!c || !out) return HM_EINVAL;
+    *out = c->info;
+    if (c->stage >= 1) {
+        out->n = c->n;
+        out->L = c->L;
+        int nb = 0;
+        for (auto &lv : c->levels) nb += lv.nb;
+        out->n_boxes = nb;
+    }
+    return HM_OK;
+}
+
+hm_status hm_export(hm_ctx *c, int what, int level, void *host_buf, size_t *bytes) {
+    if (!c || !bytes) return HM_EINVAL;
+    if (c->stage < 1) return bad(c, HM_ESTATE, "export: build the tree first");
+    StreamScope ss(c->st);
+    const bool leaf = level == HM_LEVEL_LEAF;
+    const int cl = leaf ? c->L : level;
+    const int idx = leaf ? c->L + 1 : level;
+    std::vector<std::pair<const void *, size_t>> parts;  // device pointers, bytes
+    std::vector<char> hostpart;                          // prepared on the host instead
+    auto need_cut = [&]() { return cl >= 0 && cl <= c->L; };
+    switch (what) {
+    case HM_X_PERM: parts.push_back({c->perm.p, (size_t)c->n * sizeof(int)}); break;
+    case HM_X_LEVEL_BOXES:
+        if (level < 0 || level > c->L) return bad(c, HM_EINVAL, "export: level");
+        parts.push_back({c->levels[level].box.p, (size_t)c->levels[level].nb * BOX_FIELDS * sizeof(int)});
+        break;
+    case HM_X_CUT:
+    case HM_X_NEAR:
+    case HM_X_INTER: {
+        if (!need_cut()) return bad(c, HM_EINVAL, "export: level");
+        const Cut &cu = c->cuts[cl];
+        if (what == HM_X_CUT) {
+            std::vector<int> ent;
+            Err e = to_host(ent, cu.ent.p, (size_t)cu.nc * ENT_FIELDS, c->st);
+            if (e) return finish(c, e);
+            std::vector<int> o(2 * (size_t)cu.nc);
+            for (int i = 0; i < cu.nc; ++i) {
+                o[2 * i] = ent[(size_t)i * ENT_FIELDS];
+                o[2 * i + 1] = ent[(size_t)i * ENT_FIELDS + 1];
+            }
+            hostpart.assign((char *)o.data(), (char *)(o.data() + o.size()));
+        } else {
+            const bool nr = what == HM_X_NEAR;
+            parts.push_back({nr ? cu.near_ptr.p : cu.int_ptr.p, (size_t)(cu.nc + 1) * sizeof(int)});
+            parts.push_back({nr ? cu.near_idx.p : cu.int_idx.p, (size_t)(nr ? cu.n_near : cu.n_int) * sizeof(int)});
+        }
+        break;
+    }
+    case HM_X_PAIR_VERTEX:
+    case HM_X_VERTEX_COLOR:
+    case HM_X_VERTEX_BETA:
+    case HM_X_VERTEX_DEGREE: {
+        if (idx < 0 || idx >= (int)c->colorings.size() || !c->colorings[idx].done)
+            return bad(c, HM_ESTATE, "export: level not coloured");
+        const Coloring &g = c->colorings[idx];
+        if (what == HM_X_PAIR_VERTEX) parts.push_back({g.pair_vertex.p, (size_t)g.n_pairs * sizeof(int)});
+        if (what == HM_X_VERTEX_COLOR) parts.push_back({g.vertex_color.p, (size_t)g.n_vertices * sizeof(int)});
+        if (what == HM_X_VERTEX_BETA) parts.push_back({g.vertex_beta.p, (size_t)g.n_vertices * sizeof(int)});
+        if (what == HM_X_VERTEX_DEGREE) parts.push_back({g.vertex_degree.p, (size_t)g.n_vertices * sizeof(int)});
+        break;
+    }
+    case HM_X_GAUSS:
+        if (c->gauss_level != level) return bad(c, HM_ESTATE, "export: Gaussians of that level are not current");
+        parts.push_back({c->GO.p, (size_t)c->n * c->cfg.r * sizeof(double)});
+        parts.push_back({c->GP.p, (size_t)c->n * c->cfg.r * sizeof(double)});
+        break;
+    case HM_X_SAMPLE_Y:
+    case HM_X_SAMPLE_Z: {
+        const Samples *s = nullptr;
+        if (c->cfg.keep_samples && idx < (int)c->kept.size() && c->kept[idx].Y.p) s = &c->kept[idx];
+        else if (c->cur.level == level) s = &c->cur;
+        if (!s) return bad(c, HM_ESTATE, "export: no samples for that level");
+        if (what == HM_X_SAMPLE_Z && leaf) return bad(c, HM_EINVAL, "export: the leaf step has no Z");
+        parts.push_back({what == HM_X_SAMPLE_Y ? s->Y.p : s->Z.p, (size_t)s->chi * c->n * s->cols * sizeof(double)});
+        break;
+    }
+    case HM_X_PAIR_RANKS:
+    case HM_X_FACTORS:
+    case HM_X_FACTOR_OFFS: {
+        if (level < 2 || level >= (int)c->factors.size() || !c->factors[level].done)
+            return bad(c, HM_ESTATE, "export: no factors for that level");
+        const Factors &f = c->factors[level];
+        const int64_t np = f.n_pairs;
+        if (what == HM_X_FACTORS) {
+            parts.push_back({f.U.p, (size_t)f.nU * sizeof(double)});
+            parts.push_back({f.V.p, (size_t)f.nV * sizeof(double)});
+            parts.push_back({f.B.p, (size_t)f.nB * sizeof(double)});
+        } else if (np > 0) {
+            if (what == HM_X_PAIR_RANKS) {
+                std::vector<int> ku, kv;
+                Err e = to_host(ku, f.kU.p, np, c->st);
+                if (!e) e = to_host(kv, f.kV.p, np, c->st);
+                if (e) return finish(c, e);
+                std::vector<int> o(2 * np);
+                for (int64_t p = 0; p < np; ++p) {
+                    o[2 * p] = ku[p];
+                    o[2 * p + 1] = kv[p];
+                }
+                hostpart.assign((char *)o.data(), (char *)(o.data() + o.size()));
+            } else {
+                std::vector<int64_t> a, b, d;
+                Err e = to_host(a, f.offU.p, np, c->st);
+                if (!e) e = to_host(b, f.offV.p, np, c->st);
+                if (!e) e = to_host(d, f.offB.p, np, c->st);
+                if (e) return finish(c, e);
+                std::vector<int64_t> o(3 * np);
+                for (int64_t p = 0; p < np; ++p) {
+                    o[3 * p] = a[p];
+                    o[3 * p + 1] = b[p];
+                    o[3 * p + 2] = d[p];
+                }
+                hostpart.assign((char *)o.data(), (char *)(o.data() + o.size()));
+            }
+        }
+        break;
+    }
+    case HM_X_LEAF_D:
+        if (!c->leaf.done) return bad(c, HM_ESTATE, "export: no leaf blocks");
+        parts.push_back({c->leaf.D.p, (size_t)c->leaf.nD * sizeof(double)});
+        break;
+    default: return bad(c, HM_EINVAL, "export: unknown selector");
+    }
+    size_t need = hostpart.size();
+    for (auto &pp : parts) need += pp.second;
+    if (!host_buf) {
+        *bytes = need;
+        return HM_OK;
+    }
+    if (*bytes < need) return bad(c, HM_EINVAL, "export: buffer too small");
+    char *dst = (char *)host_buf;
+    if (!hostpart.empty()) {
+        std::memcpy(dst, hostpart.data(), hostpart.size());
+        dst += hostpart.size();
+    }
+    for (auto &pp : parts) {
+        if (pp.second) {
+            cudaError_t ce = cudaMemcpyAsync(dst, pp.first, pp.second, cudaMemcpyDeviceToHost, c->st);
+            if (ce != cudaSuccess) return bad(c, HM_ECUDA, cudaGetErrorString(ce));
+        }
+        dst += pp.second;
+    }
+    if (cudaStreamSynchronize(c->st) != cudaSuccess) return bad(c, HM_ECUDA, "export: copy failed");
+    *bytes = need;
+    return HM_OK;
+}
+
+const char *hm_last_error(const hm_ctx *c) { return c ? c->last_error.c_str() : "null context"; }
+
+}  // extern "C"

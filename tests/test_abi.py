@@ -1,0 +1,69 @@
+"""The C-ABI library builds here, loads, and exports every symbol include/hm.h declares.
+
+CPU only: no compute call is made (there is no GPU in this container).
+"""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    text = open(os.path.join(ROOT, "include", "hm.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(hm_[a-z_]+)\s*\(", text)) - {"hm_apply_fn"})
+
+
+def test_library_builds_and_exports_all_declared_symbols():
+    import __graft_entry__
+    path = __graft_entry__._build_module().build()
+    lib = ctypes.CDLL(path)
+    syms = declared_symbols()
+    assert len(syms) >= 11
+    for s in syms:
+        assert hasattr(lib, s), f"libhm.so does not export {s}"
+    import paper_2205_03406_gb300 as hm
+    assert sorted(hm.EXPORTED) == syms
+
+
+def test_binding_struct_layouts_match_header(tmp_path):
+    """The ctypes mirrors have the sizes and field offsets the C compiler gives."""
+    import subprocess
+    import paper_2205_03406_gb300 as hm
+    src = tmp_path / "sizes.c"
+    src.write_text(
+        '#include <stdio.h>\n#include <stddef.h>\n#include "hm.h"\n'
+        'int main(void){printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(hm_config), sizeof(hm_op), sizeof(hm_info),'
+        ' offsetof(hm_config, seed), offsetof(hm_op, user), offsetof(hm_info, seconds_total)); return 0;}\n')
+    exe = tmp_path / "sizes"
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    got = [int(v) for v in subprocess.check_output([str(exe)]).split()]
+    want = [ctypes.sizeof(hm.hm_config), ctypes.sizeof(hm.hm_op), ctypes.sizeof(hm.hm_info),
+            hm.hm_config.seed.offset, hm.hm_op.user.offset, hm.hm_info.seconds_total.offset]
+    assert got == want
+
+
+def test_create_rejects_bad_configs_without_gpu():
+    """Argument checks happen before any CUDA work."""
+    import paper_2205_03406_gb300 as hm
+    bad = [hm.Settings(d=4), hm.Settings(d=3, r=0, rank=1), hm.Settings(d=3, r=65, rank=1),
+           hm.Settings(d=3, rank=0, tol=0.0), hm.Settings(d=3, rank=5, tol=1e-6),
+           hm.Settings(d=3, r=8, rank=9), hm.Settings(d=3, rank=4, precision=7)]
+    for s in bad:
+        with pytest.raises(hm.HMError) as ei:
+            hm.hm_create(s.to_c())
+        assert ei.value.status == hm.HM_EINVAL
+    assert hm.hm_destroy(None) == hm.HM_OK
+
+
+def test_no_cpu_fallback_in_product_package():
+    """The product package never imports the oracle."""
+    pkg = os.path.join(ROOT, "paper_2205_03406_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                src = open(os.path.join(dirpath, f)).read()
+                assert "oracle" not in src.replace("oracle's", ""), f

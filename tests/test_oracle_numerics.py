@@ -81,7 +81,7 @@ def test_exact_recovery_of_rank_k_hmatrix(geom):
     A = random_hmatrix(t, 6, 11)
     op = h1.DenseOp(A)
     for kw in ({"rank": 6}, {"tol": 1e-9}):
-        H = h1.compress(t, op, r=12, seed=5, **kw)
+        H = h1.compress(t, op, r=16, seed=5, **kw)
         Ac = h1.apply_h1(H, np.eye(t.n))
         err = np.linalg.norm(Ac - A) / np.linalg.norm(A)
         assert err < 1e-12, (kw, err)
