@@ -119,6 +119,10 @@ typedef struct {
     int max_rank;             /* largest k over all blocks */
     double seconds_sample;    /* time in the black box during hm_compress */
     double seconds_total;     /* wall time of hm_compress */
+    double seconds_phase[8];  /* device time per phase of hm_compress (CUDA events):
+                                 0 colouring, 1 test matrices, 2 black box (admissible
+                                 levels), 3 peel, 4 bases and cores, 5 leaf black box,
+                                 6 leaf peel and extraction, 7 unused */
 } hm_info;
 
 /* Create a context.  cfg is copied.  stream: a cudaStream_t or NULL. */

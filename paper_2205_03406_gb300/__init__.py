@@ -52,7 +52,10 @@ class hm_info(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("L", ctypes.c_int), ("n_boxes", ctypes.c_int),
                 ("colors", ctypes.c_int * 32), ("pairs", ctypes.c_int64 * 32), ("vertices", ctypes.c_int64 * 32),
                 ("matvec_cols", ctypes.c_int64), ("factor_floats", ctypes.c_int64), ("max_rank", ctypes.c_int),
-                ("seconds_sample", ctypes.c_double), ("seconds_total", ctypes.c_double)]
+                ("seconds_sample", ctypes.c_double), ("seconds_total", ctypes.c_double),
+                ("seconds_phase", ctypes.c_double * 8)]
+
+PHASES = ["colouring", "test matrices", "black box", "peel", "bases+cores", "leaf black box", "leaf peel+extract"]
 
 
 def _load():

@@ -102,6 +102,7 @@ struct hm_ctx {
     hm::DBuf xs;              // double [n][3], sorted (Morton) order; unused dims are 0
     hm::DBuf perm;            // int32 [n]: original index of sorted point i
     hm::DBuf qs;              // int32 [n][3]: grid coordinates, sorted order
+    hm::DBuf xdf;             // float4 [n][2]: double-float copy of xs (mixed precision)
 
     int L = 0;
     std::vector<hm::Level> levels;
@@ -136,6 +137,7 @@ Err op_apply_dense_vectors(hm_ctx *c, const hm_op *op, const double *x_sorted, d
                            int nrhs, int trans);
 // sample_tc.cu
 Err sample_tc(hm_ctx *c, int level, int kernel);
+Err sample_leaf_mixed(hm_ctx *c, int kernel);
 bool tc_supported(const hm_ctx *c);
 // peel.cu
 Err peel_level(hm_ctx *c, int level, bool leaf);

@@ -149,6 +149,7 @@ hm_status hm_tree_build(hm_ctx *c, const double *points_dev, int64_t n) {
     c->factors.clear();
     c->kept.clear();
     c->leaf = Leaf();
+    c->xdf.release();
     c->stage = 0;
     Err e = build_tree(c, points_dev, n);
     if (e) return finish(c, e);
@@ -210,18 +211,34 @@ static Err keep_current(hm_ctx *c, int idx, bool leaf) {
 
 static Err compress_all(hm_ctx *c, const hm_op *op) {
     const auto t0 = std::chrono::steady_clock::now();
-    std::vector<cudaEvent_t> ev;
-    auto rec = [&](void) -> Err {
+    // (phase, start event, end event) triples, read once at the end
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev;
+    int cur_phase = -1;
+    cudaEvent_t cur_start = nullptr;
+    auto begin = [&](int ph) -> Err {
+        HM_CUDA(cudaEventCreate(&cur_start));
+        HM_CUDA(cudaEventRecord(cur_start, c->st));
+        cur_phase = ph;
+        return ok();
+    };
+    auto end = [&]() -> Err {
         cudaEvent_t e;
         HM_CUDA(cudaEventCreate(&e));
         HM_CUDA(cudaEventRecord(e, c->st));
-        ev.push_back(e);
+        ev.push_back({cur_phase, {cur_start, e}});
+        cur_start = nullptr;
         return ok();
     };
+#define PHASE(ph, expr)                        \
+    do {                                       \
+        if ((err = begin(ph))) break;          \
+        if ((err = (expr))) { end(); break; }  \
+        if ((err = end())) break;              \
+    } while (0)
     Err err;
     int64_t cols_total = 0;
     for (int l = 2; l <= c->L && !err; ++l) {
-        err = color_cut(c, l, false);
+        PHASE(0, color_cut(c, l, false));
         if (err) break;
         const Coloring &g = c->colorings[l];
         if (g.n_pairs == 0 || g.n_colors == 0) {
@@ -229,37 +246,45 @@ static Err compress_all(hm_ctx *c, const hm_op *op) {
             c->factors[l].done = true;
             continue;
         }
-        if ((err = make_gaussians(c, l))) break;
-        if ((err = rec())) break;
-        if ((err = sample_level(c, op, l, false))) break;
-        if ((err = rec())) break;
+        PHASE(1, make_gaussians(c, l));
+        if (err) break;
+        PHASE(2, sample_level(c, op, l, false));
+        if (err) break;
         cols_total += 2ll * g.n_colors * g.m_cols;
-        if ((err = peel_level(c, l, false))) break;
+        PHASE(3, peel_level(c, l, false));
+        if (err) break;
         if ((err = keep_current(c, l, false))) break;
-        if ((err = bases_and_cores(c, l))) break;
+        PHASE(4, bases_and_cores(c, l));
     }
-    if (!err) err = color_cut(c, 0, true);
+    if (!err) PHASE(0, color_cut(c, 0, true));
     if (!err) {
         const Coloring &g = c->colorings[c->L + 1];
-        if (!(err = rec()) && !(err = sample_level(c, op, HM_LEVEL_LEAF, true)) && !(err = rec())) {
+        PHASE(5, sample_level(c, op, HM_LEVEL_LEAF, true));
+        if (!err) {
             cols_total += (int64_t)g.n_colors * g.m_cols;
-            err = peel_level(c, 0, true);
+            PHASE(6, peel_level(c, 0, true));
             if (!err) err = keep_current(c, c->L + 1, true);
-            if (!err) err = extract_leaf(c);
+            if (!err) PHASE(6, extract_leaf(c));
         }
     }
+#undef PHASE
+    if (cur_start) cudaEventDestroy(cur_start);
     cudaError_t ce = cudaStreamSynchronize(c->st);
     if (!err && ce != cudaSuccess) err = fail(HM_ECUDA, std::string("compress: ") + cudaGetErrorString(ce));
-    double ts = 0.0;
-    for (size_t i = 0; i + 1 < ev.size(); i += 2) {
+    double phase[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (auto &e : ev) {
         float ms = 0.f;
-        if (cudaEventElapsedTime(&ms, ev[i], ev[i + 1]) == cudaSuccess) ts += ms * 1e-3;
+        if (cudaEventElapsedTime(&ms, e.second.first, e.second.second) == cudaSuccess) phase[e.first] += ms * 1e-3;
+        cudaEventDestroy(e.second.first);
+        cudaEventDestroy(e.second.second);
     }
-    for (auto e : ev) cudaEventDestroy(e);
+    cudaGetLastError();
     if (err) return err;
+    const double ts = phase[2] + phase[5];
     c->t_sample = ts;
     hm_info &in = c->info;
     std::memset(&in, 0, sizeof(in));
+    for (int k = 0; k < 8; ++k) in.seconds_phase[k] = phase[k];
     in.n = c->n;
     in.L = c->L;
     for (auto &lv : c->levels) in.n_boxes += lv.nb;

@@ -305,6 +305,8 @@ Err sample_level(hm_ctx *c, const hm_op *op, int level, bool leaf) {
     if (op->kind != HM_OP_KERNEL && op->kind != HM_OP_DENSE) return fail(HM_EINVAL, "unknown operator kind");
     const OpDev o = make_opdev(c, op);
     const Cut &cu = c->cuts[g.level];
+    if (leaf && c->cfg.precision == HM_MIXED_BF16X6 && op->kind == HM_OP_KERNEL)
+        return sample_leaf_mixed(c, op->kernel);
     if (leaf) {
         dim3 grid(ceil_div(n, 64), chi, ceil_div(cols, 64));
         k_sample_leaf64<<<grid, 256, 0, c->st>>>(o, g.act_ptr.as<int>(), g.act_box.as<int>(), cu.ent.as<int>(), cols,

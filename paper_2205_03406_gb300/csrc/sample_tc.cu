@@ -1,11 +1,596 @@
-// Mixed-precision black-box contraction on the tcgen05 tensor cores (placeholder
-// until the kernel lands; the FP64 path is used meanwhile).
+// Mixed-precision black-box contraction on the 5th-generation tensor cores
+// (tcgen05, sm_103a): for colour c and a tile of 128 rows,
+//     [Y | Z](tile, c) = sum_{j in rows(c)} K(x_i, x_j) [G^Omega_j | G^Psi_j],
+// the sampling step of Algorithm 4.1 with the kernel matrix evaluated on the fly.
+//
+// Precision (HM_MIXED_BF16X6): K is evaluated in FP32 from double-float point
+// coordinates (x = hi + lo, both FP32), so differences of nearby points keep
+// FP32 accuracy; K and G are split into three BF16 pieces (h + m + l carries
+// 24 bits) and the six products hh, hm, mh, hl, mm, lh accumulate in FP32 in
+// tensor memory; the epilogue sums them small-to-large and writes FP64.
+//
+// Per level a pack kernel writes, for every colour, chunks of 64 active rows
+// in the exact shared-memory image the tensor core reads: the three BF16
+// pieces of [G^Omega | G^Psi]^T (K-major, 128-byte swizzle) followed by the
+// chunk's double-float coordinates.  The main kernel (one CTA per (tile,
+// colour)) streams chunks through two shared-memory stages:
+//   - one thread issues cp.async.bulk (TMA) copies of the next chunk,
+//   - eight producer warps evaluate the 128 x 64 kernel tile, split it and
+//     store it swizzled, then arrive on an mbarrier,
+//   - one thread of the MMA warp issues tcgen05.mma (M = 128, K = 16 per
+//     instruction, three instructions per K step: A_h x [B_h B_m B_l],
+//     A_m x [B_h B_m], A_l x B_h) and tcgen05.commit frees the stage,
+//   - the epilogue reads the accumulators with tcgen05.ld.
+// Every mbarrier wait is bounded; on expiry a status word is set and the CTA
+// drains and frees its tensor memory before returning.
 #include "ctx.cuh"
+
+#include <cuda_bf16.h>
+
+#include <cmath>
 
 namespace hm {
 
-bool tc_supported(const hm_ctx *) { return false; }
+namespace tc {
 
-Err sample_tc(hm_ctx *, int, int) { return fail(HM_ENOTSUP, "tcgen05 sample not built"); }
+constexpr int KC = 64;          // rows j per chunk (one 128-byte row of BF16)
+constexpr int TM = 128;         // rows i per tile (MMA M)
+constexpr int NPROD = 256;      // producer threads (8 warps)
+constexpr int NTHREADS = NPROD + 32;
+constexpr int A_PIECE = TM * 128;        // bytes of one A piece (16 KB)
+constexpr int COORD_BYTES = KC * 32;     // 64 entries x 8 floats
+constexpr unsigned long long WAIT_NS = 4000000000ull;  // 4 s per wait
+
+__host__ __device__ constexpr int b_bytes(int r) { return 3 * 2 * r * 128; }
+__host__ __device__ constexpr int chunk_bytes(int r) { return b_bytes(r) + COORD_BYTES; }
+__host__ __device__ constexpr int stage_bytes(int r) {
+    return ((3 * A_PIECE + chunk_bytes(r)) + 1023) / 1024 * 1024;
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ unsigned long long gtime() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait: false (and *status set) when the phase does not complete in
+// time or another thread has already given up.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *status,
+                                          bool abortable = true) {
+    if (mbar_try(bar, parity)) return true;
+    const unsigned long long t0 = gtime();
+    for (uint32_t it = 1;; ++it) {
+        if (mbar_try(bar, parity)) return true;
+        if ((it & 1023) == 0) {
+            if (abortable && *status) return false;
+            if (gtime() - t0 > WAIT_NS) {
+                *status = 1;
+                return false;
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
+// 1024 bytes apart (stride byte offset), descriptor version 1.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)1 << 16;              // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)(1024 >> 4) << 32;    // stride byte offset
+    d |= (uint64_t)1 << 46;              // version
+    d |= (uint64_t)2 << 61;              // 128-byte swizzle
+    return d;
+}
+
+// Instruction descriptor of kind::f16: BF16 A and B, FP32 D, K-major, M = 128.
+__host__ __device__ constexpr uint32_t idesc_bf16(int n) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+#pragma unroll
+    for (int k = 0; k < 16; ++k) v[k] = __uint_as_float(r[k]);
+}
+
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float *v) {
+    uint32_t r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+#pragma unroll
+    for (int k = 0; k < 8; ++k) v[k] = __uint_as_float(r[k]);
+}
+
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// kernel value up to the constant factor applied in the epilogue
+template <int KIND> __device__ __forceinline__ float kval(float r2) {
+    if (KIND == HM_K_EXP) return exp2f(-sqrtf(r2) * 1.4426950408889634f);
+    float v;
+    if (KIND == HM_K_LOG) v = __log2f(r2);
+    else v = rsqrtf(r2);
+    return r2 > 0.0f ? v : 0.0f;
+}
+
+__host__ __device__ constexpr double kscale(int kind) {
+    return kind == HM_K_LAPLACE3D ? 0.079577471545947667884 : (kind == HM_K_LOG ? 0.34657359027997265471 : 1.0);
+}
+
+// split v into three BF16 pieces (h + m + l = v to 24 bits)
+__device__ __forceinline__ void split3(float v, __nv_bfloat16 &h, __nv_bfloat16 &m, __nv_bfloat16 &l) {
+    h = __float2bfloat16_rn(v);
+    const float r1 = v - __bfloat162float(h);
+    m = __float2bfloat16_rn(r1);
+    const float r2 = r1 - __bfloat162float(m);
+    l = __float2bfloat16_rn(r2);
+}
+
+struct Params {
+    const float4 *xdf;         // sorted points, double-float: [n][2] = (hi xyz, lo xyz)
+    int64_t n;
+    int r;
+    const int64_t *chunk_off;  // per colour: first chunk (chi + 1)
+    const int64_t *rows_ptr;   // per colour: active rows offset (chi + 1)
+    const unsigned char *pack; // packed chunks
+    double *Y, *Z;             // [chi][n][r]
+    int *status;
+};
+
+template <int KIND>
+__global__ void __launch_bounds__(NTHREADS, 1) k_sample_tc(Params P) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    __shared__ uint64_t full_a[2], full_b[2], empty[2], accum;
+    __shared__ uint32_t tmem_slot;
+    unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const int r = P.r;
+    const int SB = stage_bytes(r);
+    const int CB = chunk_bytes(r);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int c = blockIdx.y;
+    const int64_t i0 = (int64_t)blockIdx.x * TM;
+    const int64_t nrows = P.rows_ptr[c + 1] - P.rows_ptr[c];
+    const int nchunks = (int)((nrows + KC - 1) / KC);
+    const unsigned char *gpack = P.pack + (size_t)P.chunk_off[c] * CB;
+    volatile int *status = P.status;
+
+    if (tid == 0) {
+        for (int s = 0; s < 2; ++s) {
+            mbar_init(&full_a[s], NPROD);
+            mbar_init(&full_b[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(&accum, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 8) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(
+                         smem_u32(&tmem_slot))
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_slot;
+    bool ok = true;
+
+    if (warp < 8) {
+        // ------------------------------------------------------------ producers
+        const int ck = lane & 7;                  // 16-byte chunk: k in [8 ck, 8 ck + 8)
+        float rx[4][6];                           // double-float coordinates of 4 rows
+        int mrow[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            mrow[u] = 16 * warp + (lane >> 3) + 4 * u;
+            const int64_t i = i0 + mrow[u];
+            float4 h = make_float4(3.0e18f, 3.0e18f, 3.0e18f, 0.f), l = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (i < P.n) {  // padding rows sit far away: K ~ 0 there
+                h = P.xdf[2 * i];
+                l = P.xdf[2 * i + 1];
+            }
+            rx[u][0] = h.x; rx[u][1] = h.y; rx[u][2] = h.z;
+            rx[u][3] = l.x; rx[u][4] = l.y; rx[u][5] = l.z;
+        }
+        int b_issued = 0, b_waited = 0;  // thread 0: bulk copies issued / consumed
+        if (tid == 0 && nchunks > 0) {
+            mbar_expect_tx(&full_b[0], CB);
+            bulk_g2s(smem + 3 * A_PIECE, gpack, CB, &full_b[0]);
+            b_issued = 1;
+        }
+        for (int q = 0; q < nchunks && ok; ++q) {
+            const int s = q & 1;
+            const uint32_t u = (uint32_t)(q >> 1);
+            if (tid == 0 && q + 1 < nchunks) {
+                const int s1 = (q + 1) & 1;
+                if (q + 1 >= 2) ok = mbar_wait(&empty[s1], ((uint32_t)((q + 1) >> 1) - 1) & 1, status);
+                if (ok) {
+                    mbar_expect_tx(&full_b[s1], CB);
+                    bulk_g2s(smem + s1 * SB + 3 * A_PIECE, gpack + (size_t)(q + 1) * CB, CB, &full_b[s1]);
+                    b_issued = q + 2;
+                }
+            }
+            if (q >= 2 && ok) ok = mbar_wait(&empty[s], (u - 1) & 1, status);
+            if (ok) ok = mbar_wait(&full_b[s], u & 1, status);
+            if (!ok) break;
+            b_waited = q + 1;
+            unsigned char *st = smem + s * SB;
+            const float4 *cd = reinterpret_cast<const float4 *>(st + 3 * A_PIECE + b_bytes(r));
+            float kv[4][8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                const float4 ch = cd[(8 * ck + e) * 2], cl = cd[(8 * ck + e) * 2 + 1];
+#pragma unroll
+                for (int uu = 0; uu < 4; ++uu) {
+                    const float dx = (rx[uu][0] - ch.x) + (rx[uu][3] - cl.x);
+                    const float dy = (rx[uu][1] - ch.y) + (rx[uu][4] - cl.y);
+                    const float dz = (rx[uu][2] - ch.z) + (rx[uu][5] - cl.z);
+                    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                    kv[uu][e] = kval<KIND>(r2);
+                }
+            }
+#pragma unroll
+            for (int uu = 0; uu < 4; ++uu) {
+                const int m = mrow[uu];
+                const int off = (m >> 3) * 1024 + (m & 7) * 128 + ((ck ^ (m & 7)) << 4);
+                __align__(16) __nv_bfloat16 ph[8], pm[8], pl[8];
+#pragma unroll
+                for (int e = 0; e < 8; ++e) split3(kv[uu][e], ph[e], pm[e], pl[e]);
+                *reinterpret_cast<uint4 *>(st + off) = *reinterpret_cast<const uint4 *>(ph);
+                *reinterpret_cast<uint4 *>(st + A_PIECE + off) = *reinterpret_cast<const uint4 *>(pm);
+                *reinterpret_cast<uint4 *>(st + 2 * A_PIECE + off) = *reinterpret_cast<const uint4 *>(pl);
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            mbar_arrive(&full_a[s]);
+        }
+        // never leave a bulk copy in flight: wait for the ones not consumed
+        if (tid == 0)
+            for (int k = b_waited; k < b_issued; ++k) mbar_wait(&full_b[k & 1], (uint32_t)(k >> 1) & 1, status, false);
+    } else if (lane == 0) {
+        // ------------------------------------------------------------ MMA issuer
+        const uint32_t id1 = idesc_bf16(6 * r), id2 = idesc_bf16(4 * r), id3 = idesc_bf16(2 * r);
+        int issued = 0;
+        for (int q = 0; q < nchunks && ok; ++q) {
+            const int s = q & 1;
+            const uint32_t u = (uint32_t)(q >> 1);
+            ok = mbar_wait(&full_a[s], u & 1, status) && mbar_wait(&full_b[s], u & 1, status);
+            if (!ok) break;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t sa = smem_u32(smem + s * SB);
+            const uint64_t ah = sw128_desc(sa), am = sw128_desc(sa + A_PIECE), al = sw128_desc(sa + 2 * A_PIECE);
+            const uint64_t bd = sw128_desc(sa + 3 * A_PIECE);
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) {
+                const uint32_t acc = (q > 0 || kk > 0) ? 1u : 0u;
+                const uint64_t adv = (uint64_t)(kk * 2);  // 32 bytes per K step, in 16-byte units
+                mma_bf16(tmem + 0, ah + adv, bd + adv, id1, acc);
+                mma_bf16(tmem + 6 * r, am + adv, bd + adv, id2, acc);
+                mma_bf16(tmem + 10 * r, al + adv, bd + adv, id3, acc);
+            }
+            mma_commit(&empty[s]);
+            issued = q + 1;
+        }
+        if (issued > 0) mma_commit(&accum);
+        else mbar_arrive(&accum);
+    }
+    __syncwarp();
+
+    // ---------------------------------------------------------------- epilogue
+    if (warp < 8) {
+        // the MMAs of this CTA must have finished before tensor memory is read or freed
+        const bool good = mbar_wait(&accum, 0, status, false) && *status == 0;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const int quarter = warp & 3, side = warp >> 2;
+        const int m = 32 * quarter + lane;
+        const int64_t i = i0 + m;
+        const uint32_t trow = tmem + ((uint32_t)(32 * quarter) << 16);
+        double *out = side ? P.Z : P.Y;
+        const float scale = (float)kscale(KIND);
+        for (int h = 0; h < r / 8; ++h) {  // 8 output columns per step
+            const int n = side * r + 8 * h;
+            float hh[8], hm[8], hl[8], mh[8], mm[8], lh[8];
+            tmem_ld8(trow + n, hh);
+            tmem_ld8(trow + 2 * r + n, hm);
+            tmem_ld8(trow + 4 * r + n, hl);
+            tmem_ld8(trow + 6 * r + n, mh);
+            tmem_ld8(trow + 8 * r + n, mm);
+            tmem_ld8(trow + 10 * r + n, lh);
+            tmem_wait_ld();
+            if (good && i < P.n) {
+                double *dst = out + ((int64_t)c * P.n + i) * r + 8 * h;
+#pragma unroll
+                for (int k = 0; k < 8; k += 2) {
+                    float a0 = 0.f, a1 = 0.f;
+                    if (nchunks > 0) {
+                        a0 = (((hl[k] + mm[k]) + lh[k]) + (hm[k] + mh[k]) + hh[k]) * scale;
+                        a1 = (((hl[k + 1] + mm[k + 1]) + lh[k + 1]) + (hm[k + 1] + mh[k + 1]) + hh[k + 1]) * scale;
+                    }
+                    *reinterpret_cast<double2 *>(dst + k) = make_double2((double)a0, (double)a1);
+                }
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 8) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
+    }
+}
+
+// ---------------------------------------------------------------------------
+// pack: chunk g of colour c holds rows j_{64q .. 64q+63} of rows(c)
+// ---------------------------------------------------------------------------
+
+// B image: row n' = piece * 2r + n (n < r: G^Omega column n, else G^Psi
+// column n - r), 64 BF16 of consecutive j per row, 128-byte swizzle.
+__global__ void k_pack_b(const int64_t *chunk_color_first, int chi, const int64_t *rows_ptr, const int *rows,
+                         const double *GO, const double *GP, int r, int64_t nchunks_total, unsigned char *pack) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int ncol = 2 * r;
+    if (t >= nchunks_total * ncol * 8) return;
+    const int64_t g = t / (ncol * 8);
+    const int rem = (int)(t - g * ncol * 8);
+    const int n = rem / 8, kg = rem % 8;
+    // colour of chunk g (chi is small: linear search)
+    int c = 0;
+    while (c + 1 < chi && chunk_color_first[c + 1] <= g) ++c;
+    const int64_t q = g - chunk_color_first[c];
+    const int64_t r0 = rows_ptr[c], r1 = rows_ptr[c + 1];
+    __align__(16) __nv_bfloat16 ph[8], pm[8], pl[8];
+    for (int e = 0; e < 8; ++e) {
+        const int64_t idx = r0 + q * KC + kg * 8 + e;
+        double v = 0.0;
+        if (idx < r1) {
+            const int j = rows[idx];
+            v = (n < r) ? GO[(int64_t)j * r + n] : GP[(int64_t)j * r + (n - r)];
+        }
+        const __nv_bfloat16 h = __double2bfloat16(v);
+        const double r1d = v - (double)__bfloat162float(h);
+        const __nv_bfloat16 m = __double2bfloat16(r1d);
+        const double r2d = r1d - (double)__bfloat162float(m);
+        ph[e] = h;
+        pm[e] = m;
+        pl[e] = __double2bfloat16(r2d);
+    }
+    unsigned char *base = pack + (size_t)g * chunk_bytes(r);
+    for (int piece = 0; piece < 3; ++piece) {
+        const int row = piece * ncol + n;
+        const int off = (row >> 3) * 1024 + (row & 7) * 128 + ((kg ^ (row & 7)) << 4);
+        const __nv_bfloat16 *src = piece == 0 ? ph : (piece == 1 ? pm : pl);
+        *reinterpret_cast<uint4 *>(base + off) = *reinterpret_cast<const uint4 *>(src);
+    }
+}
+
+// coordinates: entry k = (x_hi, y_hi, z_hi, pad, x_lo, y_lo, z_lo, pad)
+__global__ void k_pack_coords(const int64_t *chunk_color_first, int chi, const int64_t *rows_ptr, const int *rows,
+                              const float4 *xdf, int r, int64_t nchunks_total, unsigned char *pack) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= nchunks_total * KC) return;
+    const int64_t g = t / KC;
+    const int k = (int)(t - g * KC);
+    int c = 0;
+    while (c + 1 < chi && chunk_color_first[c + 1] <= g) ++c;
+    const int64_t idx = rows_ptr[c] + (g - chunk_color_first[c]) * KC + k;
+    float4 h = make_float4(1.0e18f, 1.0e18f, 1.0e18f, 0.f), l = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (idx < rows_ptr[c + 1]) {  // padding entries sit far away (and their G rows are zero)
+        const int j = rows[idx];
+        h = xdf[2 * (int64_t)j];
+        l = xdf[2 * (int64_t)j + 1];
+    }
+    float4 *dst = reinterpret_cast<float4 *>(pack + (size_t)g * chunk_bytes(r) + b_bytes(r)) + 2 * k;
+    dst[0] = h;
+    dst[1] = l;
+}
+
+// leaf black box, FP32 kernel values from double-float coordinates, FP64 output:
+// Y(i, c m + t) = sum over active boxes beta of K(i, start_beta + t)
+template <int KIND>
+__global__ void __launch_bounds__(256) k_sample_leaf32(const float4 *xdf, int64_t n, const int *act_ptr,
+                                                       const int *act_box, const int *ent, int m, double *out) {
+    const int c = blockIdx.y;
+    const int64_t i = (int64_t)blockIdx.x * 64 + (threadIdx.x >> 2);
+    const int ph = threadIdx.x & 3, t0 = blockIdx.z * 64;
+    if (i >= n) return;
+    const float4 ih = xdf[2 * i], il = xdf[2 * i + 1];
+    float acc[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) acc[q] = 0.0f;
+    for (int a = act_ptr[c]; a < act_ptr[c + 1]; ++a) {
+        const int *e = ent + (int64_t)act_box[a] * ENT_FIELDS;
+        const int s = e[3], len = e[4] - e[3];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+            const int t = t0 + q * 4 + ph;
+            if (t < len && t < m) {
+                const int64_t j = s + t;
+                const float4 jh = xdf[2 * j], jl = xdf[2 * j + 1];
+                const float dx = (ih.x - jh.x) + (il.x - jl.x);
+                const float dy = (ih.y - jh.y) + (il.y - jl.y);
+                const float dz = (ih.z - jh.z) + (il.z - jl.z);
+                acc[q] += kval<KIND>(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+            }
+        }
+    }
+    const double scale = kscale(KIND);
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+        const int t = t0 + q * 4 + ph;
+        if (t < m) out[((int64_t)c * n + i) * m + t] = (double)acc[q] * scale;
+    }
+}
+
+__global__ void k_make_xdf(const double *xs, int64_t n, float4 *xdf) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float h[3], l[3];
+    for (int d = 0; d < 3; ++d) {
+        const double x = xs[i * 3 + d];
+        h[d] = (float)x;
+        l[d] = (float)(x - (double)h[d]);
+    }
+    xdf[2 * i] = make_float4(h[0], h[1], h[2], 0.f);
+    xdf[2 * i + 1] = make_float4(l[0], l[1], l[2], 0.f);
+}
+
+}  // namespace tc
+
+// double-float copy of the sorted points (x = hi + lo, both FP32), made once
+static Err make_xdf(hm_ctx *c) {
+    if (c->xdf.p) return ok();
+    HM_TRY(alloc(c->xdf, (size_t)c->n * 2 * sizeof(float4)));
+    tc::k_make_xdf<<<ceil_div(c->n, 256), 256, 0, c->st>>>(c->xs.as<double>(), c->n, c->xdf.as<float4>());
+    HM_LAUNCH("make_xdf");
+    return ok();
+}
+
+bool tc_supported(const hm_ctx *c) {
+    const int r = c->cfg.r;
+    return r % 8 == 0 && r >= 8 && r <= 40;
+}
+
+Err sample_tc(hm_ctx *c, int level, int kernel) {
+    using namespace tc;
+    cudaStream_t st = c->st;
+    const Coloring &g = c->colorings[level];
+    const int chi = g.n_colors, r = c->cfg.r;
+    const int64_t n = c->n;
+    HM_TRY(make_xdf(c));  // the pack and main kernels read the double-float points
+    // chunk table per colour
+    std::vector<int64_t> rp;
+    HM_TRY(to_host(rp, g.act_rows_ptr.p, chi + 1, st));
+    std::vector<int64_t> cf(chi + 1, 0);
+    for (int k = 0; k < chi; ++k) cf[k + 1] = cf[k] + (rp[k + 1] - rp[k] + KC - 1) / KC;
+    const int64_t total = cf[chi];
+    DBuf cfd;
+    HM_TRY(to_dev(cfd, cf, st));
+    HM_TRY(ensure(c->scratch_b, (size_t)std::max<int64_t>(total, 1) * chunk_bytes(r)));
+    HM_TRY(ensure(c->scratch_c, sizeof(int)));
+    HM_CUDA(cudaMemsetAsync(c->scratch_c.p, 0, sizeof(int), st));
+    if (total > 0) {
+        k_pack_b<<<ceil_div(total * 2 * r * 8, 256), 256, 0, st>>>(
+            cfd.as<int64_t>(), chi, g.act_rows_ptr.as<int64_t>(), g.act_rows.as<int>(), c->GO.as<double>(),
+            c->GP.as<double>(), r, total, c->scratch_b.as<unsigned char>());
+        k_pack_coords<<<ceil_div(total * KC, 256), 256, 0, st>>>(cfd.as<int64_t>(), chi,
+                                                                  g.act_rows_ptr.as<int64_t>(), g.act_rows.as<int>(),
+                                                                  c->xdf.as<float4>(), r, total,
+                                                                  c->scratch_b.as<unsigned char>());
+        HM_LAUNCH("pack");
+    }
+    Params P;
+    P.xdf = c->xdf.as<float4>();
+    P.n = n;
+    P.r = r;
+    P.chunk_off = cfd.as<int64_t>();
+    P.rows_ptr = g.act_rows_ptr.as<int64_t>();
+    P.pack = c->scratch_b.as<unsigned char>();
+    P.Y = c->cur.Y.as<double>();
+    P.Z = c->cur.Z.as<double>();
+    P.status = c->scratch_c.as<int>();
+    const int smem = 2 * stage_bytes(r) + 1024;
+    dim3 grid(ceil_div(n, TM), chi);
+    switch (kernel) {
+#define LAUNCH(K)                                                                                   \
+    case K:                                                                                         \
+        HM_CUDA(cudaFuncSetAttribute(k_sample_tc<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)); \
+        k_sample_tc<K><<<grid, NTHREADS, smem, st>>>(P);                                            \
+        break;
+        LAUNCH(HM_K_LOG)
+        LAUNCH(HM_K_LAPLACE3D)
+        LAUNCH(HM_K_INVR)
+        LAUNCH(HM_K_EXP)
+#undef LAUNCH
+    default: return fail(HM_EINVAL, "sample_tc: unknown kernel");
+    }
+    HM_LAUNCH("sample_tc");
+    int status = 0;
+    HM_TRY(read_scalar(status, c->scratch_c.p, st));
+    if (status) return fail(HM_ETIMEOUT, "sample_tc: a pipeline wait expired");
+    return ok();
+}
+
+Err sample_leaf_mixed(hm_ctx *c, int kernel) {
+    using namespace tc;
+    const Coloring &g = c->colorings[c->L + 1];
+    const Cut &cu = c->cuts[c->L];
+    const int chi = g.n_colors, m = g.m_cols;
+    const int64_t n = c->n;
+    HM_TRY(make_xdf(c));
+    dim3 grid(ceil_div(n, 64), chi, ceil_div(m, 64));
+    switch (kernel) {
+#define LAUNCH(K)                                                                                       \
+    case K:                                                                                             \
+        k_sample_leaf32<K><<<grid, 256, 0, c->st>>>(c->xdf.as<float4>(), n, g.act_ptr.as<int>(),          \
+                                                     g.act_box.as<int>(), cu.ent.as<int>(), m, c->cur.Y.as<double>()); \
+        break;
+        LAUNCH(HM_K_LOG)
+        LAUNCH(HM_K_LAPLACE3D)
+        LAUNCH(HM_K_INVR)
+        LAUNCH(HM_K_EXP)
+#undef LAUNCH
+    default: return fail(HM_EINVAL, "sample_leaf_mixed: unknown kernel");
+    }
+    HM_LAUNCH("sample_leaf32");
+    return ok();
+}
 
 }  // namespace hm

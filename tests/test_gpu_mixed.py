@@ -1,0 +1,79 @@
+"""Mixed precision (tcgen05 split-BF16 black box) against the FP64 oracle.
+
+The black-box samples must match the FP64 products to FP32-class accuracy
+(<= 1e-6 relative per level), and the compressed operator must apply within
+the stated tolerance of the oracle's: 1e-6, or the workload's truncation
+tolerance when that is larger (a rank decision at the threshold may differ
+once the samples carry FP32-level rounding).
+"""
+import numpy as np
+import pytest
+
+import hm_workloads as W
+from oracle import graph as og
+from oracle import h1 as oh1
+from oracle import tree as ot
+
+from gpu_helpers import hm, oracle_op, run_gpu, samples
+
+pytestmark = pytest.mark.gpu
+
+MIXED = 1
+TOL_MIXED = 1e-6
+
+
+def mixed_workloads():
+    return {
+        "torus_6k": W.torus_laplace(n=6000, tol=1e-6, r=32),
+        "torus_ragged_r16": W.Workload("torus_ragged", W.torus(3333, 17), W.K_LAPLACE3D, leaf_size=23, r=16,
+                                       tol=1e-5, seed=99, oversample=6),
+        "sphere_invr_r24": W.Workload("sphere_invr", W.sphere(4001, 5), W.K_INVR, leaf_size=40, r=24, tol=1e-6,
+                                      seed=7, oversample=8),
+        "grid_log_r40": W.Workload("grid_log", W.grid2d(48), W.K_LOG, leaf_size=32, r=40, rank=20, seed=2),
+        "cube_exp_r8": W.Workload("cube_exp", np.random.default_rng(4).random((2100, 3)), W.K_EXP, leaf_size=40,
+                                  r=8, rank=4, seed=3),
+    }
+
+
+@pytest.mark.parametrize("name", list(mixed_workloads()))
+def test_mixed_raw_samples(name):
+    m = hm()
+    w = mixed_workloads()[name]
+    comp, _ = run_gpu(w, precision=MIXED, compress=False)
+    t = ot.build_tree(w.points, w.leaf_size, w.uniform_depth)
+    op = oracle_op(w, t)
+    for l in range(2, t.L + 1):
+        chi = comp.color(l)
+        if chi == 0:
+            continue
+        comp.sample(comp._op, l)
+        col = og.color_level(t, l)
+        GO, GP = oh1.gaussians(t, l, 0, w.r, w.seed), oh1.gaussians(t, l, 1, w.r, w.seed)
+        Yr = op.apply(oh1.test_matrix(t, l, col, GO, w.r))
+        Zr = op.apply_t(oh1.test_matrix(t, l, col, GP, w.r))
+        Y = samples(comp, m.HM_X_SAMPLE_Y, l, w.n, chi, w.r)
+        Z = samples(comp, m.HM_X_SAMPLE_Z, l, w.n, chi, w.r)
+        ey = np.linalg.norm(Y - Yr) / np.linalg.norm(Yr)
+        ez = np.linalg.norm(Z - Zr) / np.linalg.norm(Zr)
+        assert ey <= TOL_MIXED and ez <= TOL_MIXED, (l, ey, ez)
+        # every entry, relative to its row's scale
+        rowscale = np.linalg.norm(Yr, axis=1, keepdims=True) + 1e-300
+        assert np.max(np.abs(Y - Yr) / rowscale) <= 1e-5, l
+    comp.close()
+
+
+@pytest.mark.parametrize("name", list(mixed_workloads()))
+def test_mixed_compression_matches_oracle(name):
+    import torch
+    w = mixed_workloads()[name]
+    comp, info = run_gpu(w, precision=MIXED, keep=False)
+    t = ot.build_tree(w.points, w.leaf_size, w.uniform_depth)
+    H = oh1.compress(t, oracle_op(w, t), w.r, rank=w.rank, tol=w.tol, seed=w.seed, oversample=w.oversample)
+    x = np.random.default_rng(1).standard_normal((w.n, 3))
+    for trans in (0, 1):
+        y = comp.apply(torch.from_numpy(x).cuda(), trans=trans).cpu().numpy()
+        yr = np.empty_like(x)
+        yr[t.perm] = oh1.apply_h1(H, x[t.perm], transpose=bool(trans))
+        e = np.linalg.norm(y - yr) / np.linalg.norm(yr)
+        assert e <= max(TOL_MIXED, w.tol), (trans, e)
+    comp.close()
