@@ -1,0 +1,390 @@
+#!/usr/bin/env python3
+"""Benchmark: randomized H^1 compression with graph-coloured test matrices.
+
+Workload: 200,000 points uniform in parameter space on a torus (R = 1,
+rho = 0.3), kernel 1/(4 pi |x - y|) with zero diagonal evaluated on the fly,
+adaptive octree with leaves of at most 64 points, relative truncation
+tolerance 1e-6 (r = 32 columns per colour, oversampling 10), black-box
+contraction in split-BF16 on the tensor cores, FP64 peel/QR/cores.
+
+One step = the whole hot path on resident inputs: cluster tree and lists,
+colouring of every level, test matrices, black-box products, peeling, bases,
+cores, leaf blocks, and one apply of the compressed operator to a vector.
+value = jobs/s over all GPUs (each GPU compresses its own replica: weak
+scaling, no collective in the data path).  The e2e number adds the host->device
+copy of the points and of the apply vector and the device->host read of the
+result, from pinned host memory.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "time-to-compress (s) and jobs/s at stated rel. error; p50/p99 latency"
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+
+# dram bytes (read + write) per launch of the tensor-core contraction kernel,
+# from the ncu capture summarised in profiles/k_sample_tc_torus.md, valid for
+# the source whose sha256 prefix is recorded beside it
+TRAFFIC = {"file": "paper_2205_03406_gb300/csrc/sample_tc.cu", "sha256": None, "bytes_per_row": None}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=200_000)
+    ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
+    ap.add_argument("--relerr-iters", type=int, default=20)
+    ap.add_argument("--no-relerr", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def workload(n):
+    import hm_workloads as W
+    return W.torus_laplace(n=n, tol=1e-6, r=32)
+
+
+def config_of(args, w):
+    return {"workload": f"torus_laplace_{w.n}", "n": w.n, "geometry": "torus R=1 rho=0.3, uniform (u,v)",
+            "kernel": "1/(4 pi |x-y|), zero diagonal, on the fly", "leaf_size": w.leaf_size, "tol": w.tol,
+            "r": w.r, "oversample": w.oversample,
+            "precision": "split-BF16x6 tensor-core black box, FP64 peel/QR/cores"
+            if args.precision == "mixed" else "FP64 throughout",
+            "l2": "working set larger than L2 (samples ~5 GB per level); no flush", "seed": w.seed}
+
+
+# ---------------------------------------------------------------------------
+# clocks
+# ---------------------------------------------------------------------------
+
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.flush()
+        self.f.seek(0)
+        sms, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sms.append(float(p[1]))
+                mx = float(p[2])
+            except ValueError:
+                continue
+            for name, v in zip(names, p[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        os.unlink(self.f.name)
+        sms.sort()
+        med = sms[len(sms) // 2] if sms else None
+        return {"sm_mhz": med, "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sms)}
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return p, "measured"
+    except (OSError, ValueError):
+        return PEAKS_FALLBACK, "fallback"
+
+
+def roofline_tc(info, r: int):
+    """Tensor-core contraction: useful FP64-equivalent flops 4 n r sum_c |R_c|
+    per level (Y and Z), executed as 6 BF16 products each."""
+    useful = sum(4.0 * info.n * r * info.act_rows[l] for l in range(2, info.L + 1))
+    t = info.seconds_phase[7]
+    pk, src = peaks()
+    bf16_flops = 6.0 * useful
+    achieved = bf16_flops / t / 1e12 if t > 0 else 0.0
+    peak = float(pk["bf16_tflops_sustained"])
+    traffic = None
+    try:
+        src_path = os.path.join(ROOT, TRAFFIC["file"])
+        sha = hashlib.sha256(open(src_path, "rb").read()).hexdigest()[:16]
+        if TRAFFIC["sha256"] == sha and TRAFFIC["bytes_per_row"]:
+            rows = sum(info.act_rows[l] for l in range(2, info.L + 1))
+            traffic = TRAFFIC["bytes_per_row"] * rows
+    except OSError:
+        pass
+    return {"kernel": "k_sample_tc (split-BF16 kernel-matrix x Omega contraction)", "bound": "tensor",
+            "achieved": round(achieved, 2), "peak": peak, "unit": "TFLOP/s",
+            "frac": round(achieved / peak, 4), "peak_source": f"{src} bf16_tflops_sustained",
+            "traffic": traffic, "seconds": round(t, 4), "bf16_flops": bf16_flops,
+            "useful_fp64_equiv_flops": useful}
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import paper_2205_03406_gb300 as hm
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    w = workload(args.n)
+    prec = hm.HM_MIXED_BF16X6 if args.precision == "mixed" else hm.HM_FP64
+    s = hm.Settings(d=3, leaf_size=w.leaf_size, r=w.r, oversample=w.oversample, tol=w.tol, precision=prec,
+                    seed=w.seed + rank)
+    stream = torch.cuda.current_stream()
+    comp = hm.Compressor(s, stream)
+    op = hm.kernel_op(w.kernel)
+    pts = torch.from_numpy(w.points).cuda()
+    x = torch.from_numpy(np.random.default_rng(rank).standard_normal(w.n)).cuda()
+
+    def step():
+        comp.tree_build(pts)
+        comp.compress(op)
+        return comp.apply(x)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    barrier()
+    launches0 = comp.info().launches_total
+    clocks = Clocks(local)
+    clocks.start()
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    evs[0].record(stream)
+    infos = []
+    for k in range(args.steps):
+        step()
+        evs[k + 1].record(stream)
+        infos.append(comp.info())
+    torch.cuda.synchronize()
+    elapsed_host = time.perf_counter() - t0
+    barrier()
+    clk = clocks.stop()
+    launches = comp.info().launches_total - launches0
+    per_step = [evs[k].elapsed_time(evs[k + 1]) / 1e3 for k in range(args.steps)]
+    elapsed = evs[0].elapsed_time(evs[-1]) / 1e3
+    tmax = elapsed
+    if dist is not None:
+        tt = torch.tensor([elapsed], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        tmax = float(tt.item())
+    info = infos[-1]
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        hp = torch.from_numpy(w.points).pin_memory()
+        hx = torch.from_numpy(np.random.default_rng(rank).standard_normal(w.n)).pin_memory()
+        hy = torch.empty(w.n, dtype=torch.float64).pin_memory()
+        dp = torch.empty_like(hp, device="cuda")
+        dx = torch.empty_like(hx, device="cuda")
+        torch.cuda.synchronize()
+        barrier()
+        t1 = time.perf_counter()
+        for _ in range(args.steps):
+            dp.copy_(hp, non_blocking=True)
+            comp.tree_build(dp)
+            comp.compress(op)
+            dx.copy_(hx, non_blocking=True)
+            y = comp.apply(dx)
+            hy.copy_(y, non_blocking=True)
+            torch.cuda.synchronize()
+        te = time.perf_counter() - t1
+        if dist is not None:
+            tt = torch.tensor([te], device="cuda", dtype=torch.float64)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            te = float(tt.item())
+        e2e = {"value": round(world * args.steps / te, 4), "unit": "jobs/s",
+               "h2d_bytes_per_step": int(hp.numel() * 8 + hx.numel() * 8),
+               "d2h_bytes_per_step": int(hy.numel() * 8), "time_to_compress_s": round(te / args.steps, 4)}
+
+    relerr = None
+    if not args.no_relerr and rank == 0:
+        relerr = comp.relerr(hm.kernel_op(w.kernel), args.relerr_iters)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(w, rows_per_level=100)
+
+    if rank != 0:
+        comp.close()
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+    per_step.sort()
+    p50 = per_step[len(per_step) // 2]
+    p99 = per_step[min(len(per_step) - 1, int(math.ceil(0.99 * len(per_step))) - 1)]
+    phases = {n: round(info.seconds_phase[i], 4) for i, n in enumerate(hm.PHASES)}
+    out = {
+        "metric": METRIC, "value": round(world * args.steps / tmax, 4), "unit": "jobs/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * tmax / args.steps, 2),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16x6-f32acc+f64" if args.precision == "mixed" else "f64",
+        "data": "synthetic (seeded torus point cloud)",
+        "config": dict(config_of(args, w), parallelism=f"replicas x{world}"),
+        "time_to_compress_s": round(tmax / args.steps, 4),
+        "p50_s": round(p50, 4), "p99_s": round(p99, 4),
+        "rel_error": relerr, "rel_error_iters": None if relerr is None else args.relerr_iters,
+        "matvec_cols": int(info.matvec_cols), "floats_per_dof": round(info.factor_floats / w.n, 1),
+        "colors": [int(info.colors[l]) for l in range(2, info.L + 2)], "max_rank": int(info.max_rank),
+        "phases_s": phases, "host_elapsed_s": round(elapsed_host, 3),
+        "roofline": roofline_tc(info, w.r),
+        "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
+    }
+    print(json.dumps(out), flush=True)
+    comp.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle: bounded sample of the same workload
+# ---------------------------------------------------------------------------
+
+class OracleSample:
+    """The CPU oracle on a bounded sample of the 200k-point job.
+
+    Setup times the oracle's full cluster tree and every colouring once.  A
+    sample then times the oracle's black-box product A(rows, :) Omega_l and
+    A(rows, :) Psi_l (same shape and zero pattern as Omega_l, so Omega_l stands
+    for both) for `rows_per_level` random rows of every level and
+    extrapolates to all rows.  Peel, QR, cores and leaf extraction are not
+    timed, so the estimate is a lower bound on the oracle's time-to-compress."""
+
+    def __init__(self, w):
+        from oracle import graph as og
+        from oracle import h1 as oh1
+        from oracle import tree as ot
+        self.w = w
+        t0 = time.perf_counter()
+        self.t = ot.build_tree(w.points, w.leaf_size)
+        self.cols = {l: og.color_level(self.t, l) for l in range(2, self.t.L + 1)}
+        og.color_leaf(self.t)
+        self.t_struct = time.perf_counter() - t0
+        self.op = oh1.KernelOp(w.points[self.t.perm], w.kernel)
+        # Omega_l of every level; Psi_l has the same shape and zero pattern, so
+        # the product with Omega_l is timed twice to stand for both sides
+        self.mats = {}
+        for l, col in self.cols.items():
+            if col.n_vertices == 0:
+                continue
+            GO = oh1.gaussians(self.t, l, 0, w.r, w.seed)
+            self.mats[l] = oh1.test_matrix(self.t, l, col, GO, w.r)
+
+    def sample(self, rows_per_level: int, seed: int = 0):
+        import numpy as np
+        rng = np.random.default_rng(seed)
+        n = self.w.n
+        t_bb = 0.0
+        for l, Om in self.mats.items():
+            for side in range(2):
+                rows = np.sort(rng.choice(n, rows_per_level, replace=False))
+                t1 = time.perf_counter()
+                self.op.rows(rows, Om)
+                t_bb += (time.perf_counter() - t1) * (n / rows_per_level)
+        est = self.t_struct + t_bb
+        cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+        return {"value": round(1.0 / est, 6), "unit": "jobs/s", "cores": cores, "kind": "oracle",
+                "sample": f"oracle tree + all colourings timed in full ({self.t_struct:.1f} s); black-box "
+                          f"product for {rows_per_level} random rows of each level ({len(self.mats)} levels), "
+                          f"extrapolated to all {n} rows ({t_bb:.1f} s); peel/QR/cores/leaf not timed, so "
+                          f"{est:.1f} s is a lower bound on the oracle's time-to-compress",
+                "seconds_estimate": round(est, 2)}
+
+
+def cpu_baseline(w, rows_per_level: int = 100):
+    return OracleSample(w).sample(rows_per_level)
+
+
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    w = workload(args.n)
+    orc = OracleSample(w)
+    for k in range(args.warmup):
+        orc.sample(40, seed=k)
+    ests = []
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        ests.append(orc.sample(40, seed=100 + k))
+    wall = time.perf_counter() - t0
+    est = sum(e["seconds_estimate"] for e in ests) / len(ests)
+    value = round(1.0 / est, 6)
+    out = {"metric": METRIC, "value": value, "unit": "jobs/s", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": round(1e3 * est, 1), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded torus point cloud)",
+           "impl": "reference", "config": dict(config_of(args, w), parallelism="cpu oracle"),
+           "cpu_baseline": {"value": value, "unit": "jobs/s", "cores": ests[-1]["cores"], "kind": "oracle",
+                            "sample": ests[-1]["sample"]},
+           "e2e": {"value": value, "unit": "jobs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+           "host_wall_s": round(wall, 2)}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

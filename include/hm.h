@@ -122,7 +122,12 @@ typedef struct {
     double seconds_phase[8];  /* device time per phase of hm_compress (CUDA events):
                                  0 colouring, 1 test matrices, 2 black box (admissible
                                  levels), 3 peel, 4 bases and cores, 5 leaf black box,
-                                 6 leaf peel and extraction, 7 unused */
+                                 6 leaf peel and extraction, 7 the tensor-core
+                                 contraction kernels alone (inside 2) */
+    int64_t act_rows[32];     /* per cut level: sum over colours of the active rows
+                                 (rows of Omega that are not zero); index L+1 = leaf */
+    int64_t kernel_launches;  /* kernels this library launched during hm_compress */
+    int64_t launches_total;   /* kernels this library launched since it was loaded */
 } hm_info;
 
 /* Create a context.  cfg is copied.  stream: a cudaStream_t or NULL. */

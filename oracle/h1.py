@@ -93,7 +93,11 @@ class KernelOp:
     def rows(self, idx: np.ndarray, X: np.ndarray) -> np.ndarray:
         """(A X)(idx, :) only: used for sampled checks at full size."""
         nz = np.flatnonzero(np.any(X != 0.0, axis=1))
-        return kernel_eval(self.kind, self.x[idx], self.x[nz]) @ X[nz]
+        out = np.zeros((len(idx), X.shape[1]))
+        step = max(1, self.chunk // max(nz.size, 1))
+        for s in range(0, len(idx), step):
+            out[s:s + step] = kernel_eval(self.kind, self.x[idx[s:s + step]], self.x[nz]) @ X[nz]
+        return out
 
     def dense(self) -> np.ndarray:
         return kernel_eval(self.kind, self.x, self.x)

@@ -23,7 +23,7 @@ __global__ void k_permute(const double *in, double *out, const int *perm, int64_
 }
 
 Err permute_rows(hm_ctx *c, const double *in, double *out, int nrhs, bool to_sorted) {
-    k_permute<<<ceil_div(c->n * nrhs, 256), 256, 0, c->st>>>(in, out, c->perm.as<int>(), c->n, nrhs, to_sorted);
+    k_permute<<<ceil_div(c->n * nrhs, 256), 256, 0, c->st>>>(in, out, c->perm.as<int>(), c->n, nrhs, to_sorted); ::hm::count_launch();
     HM_LAUNCH("permute");
     return ok();
 }
@@ -129,7 +129,7 @@ Err apply_sorted(hm_ctx *c, const double *x, double *y, int nrhs, int trans) {
         HM_TRY(alloc(sz, (np + 1) * sizeof(int64_t)));
         HM_TRY(alloc(toff[l], (np + 1) * sizeof(int64_t)));
         k_toff_sizes<<<ceil_div(np, 256), 256, 0, st>>>(f.kU.as<int>(), f.kV.as<int>(), np, nrhs, trans,
-                                                        sz.as<int64_t>());
+                                                        sz.as<int64_t>()); ::hm::count_launch();
         HM_TRY(scan_exclusive(sz.as<int64_t>(), toff[l].as<int64_t>(), np, st));
         int64_t tot = 0;
         HM_TRY(read_scalar(tot, toff[l].as<int64_t>() + np, st));
@@ -141,7 +141,7 @@ Err apply_sorted(hm_ctx *c, const double *x, double *y, int nrhs, int trans) {
                                                    f.kU.as<int>(), f.kV.as<int>(), f.offU.as<int64_t>(),
                                                    f.offV.as<int64_t>(), f.offB.as<int64_t>(), f.U.as<double>(),
                                                    f.V.as<double>(), f.B.as<double>(), x, nrhs, trans,
-                                                   toff[l].as<int64_t>(), tq[l].as<double>());
+                                                   toff[l].as<int64_t>(), tq[l].as<double>()); ::hm::count_launch();
         HM_LAUNCH("apply_stage1");
         ApplyLevel a;
         a.pt2ent = cu.pt2ent.as<int>();
@@ -167,7 +167,7 @@ Err apply_sorted(hm_ctx *c, const double *x, double *y, int nrhs, int trans) {
     const Coloring &gl = c->colorings[c->L + 1];
     k_apply_stage2<<<cl.nc, 128, 0, st>>>(cl.ent.as<int>(), cl.nc, lvd.as<ApplyLevel>(), (int)lv.size(),
                                           cl.near_ptr.as<int>(), cl.near_idx.as<int>(), gl.pair_T.as<int>(),
-                                          c->leaf.offD.as<int64_t>(), c->leaf.D.as<double>(), x, nrhs, trans, y);
+                                          c->leaf.offD.as<int64_t>(), c->leaf.D.as<double>(), x, nrhs, trans, y); ::hm::count_launch();
     HM_LAUNCH("apply_stage2");
     HM_CUDA(cudaStreamSynchronize(st));
     return ok();

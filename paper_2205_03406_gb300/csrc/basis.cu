@@ -358,7 +358,7 @@ Err bases_and_cores(hm_ctx *c, int level) {
     // M = G_alpha^T P for every pair (tile p is read only by pair p)
     HM_TRY(ensure(c->scratch_a, (size_t)np * r * r * sizeof(double)));
     k_core_M<<<(int)np, 256, 0, st>>>(g.pair_alpha.as<int>(), g.pair_color.as<int>(), cu.ent.as<int>(), n, r,
-                                      c->cur.Y.as<double>(), c->GP.as<double>(), c->scratch_a.as<double>());
+                                      c->cur.Y.as<double>(), c->GP.as<double>(), c->scratch_a.as<double>()); ::hm::count_launch();
     HM_LAUNCH("core_M");
     // QR of every Y tile and every Z tile
     DBuf kY, kZ;
@@ -367,10 +367,10 @@ Err bases_and_cores(hm_ctx *c, int level) {
     const int cap = c->cfg.rank > 0 ? r : r - c->cfg.oversample;
     k_qr_tiles<<<(int)np, 256, 0, st>>>(g.pair_alpha.as<int>(), cu.int_idx.as<int>(), g.pair_color.as<int>(),
                                         cu.ent.as<int>(), n, r, cap, c->cfg.rank, c->cfg.tol, c->cur.Y.as<double>(),
-                                        kY.as<int>());
+                                        kY.as<int>()); ::hm::count_launch();
     k_qr_tiles<<<(int)np, 256, 0, st>>>(g.pair_alpha.as<int>(), cu.int_idx.as<int>(), g.pair_color.as<int>(),
                                         cu.ent.as<int>(), n, r, cap, c->cfg.rank, c->cfg.tol, c->cur.Z.as<double>(),
-                                        kZ.as<int>());
+                                        kZ.as<int>()); ::hm::count_launch();
     HM_LAUNCH("qr_tiles");
     HM_TRY(alloc(f.kU, np * sizeof(int)));
     HM_TRY(alloc(f.kV, np * sizeof(int)));
@@ -379,7 +379,7 @@ Err bases_and_cores(hm_ctx *c, int level) {
     int64_t *sU = sz.as<int64_t>(), *sV = sU + (np + 1), *sB = sV + (np + 1);
     k_factor_sizes<<<ceil_div(np, 256), 256, 0, st>>>(g.pair_alpha.as<int>(), cu.int_idx.as<int>(),
                                                       g.pair_T.as<int>(), kY.as<int>(), kZ.as<int>(), cu.ent.as<int>(),
-                                                      np, f.kU.as<int>(), f.kV.as<int>(), sU, sV, sB);
+                                                      np, f.kU.as<int>(), f.kV.as<int>(), sU, sV, sB); ::hm::count_launch();
     HM_LAUNCH("factor_sizes");
     HM_TRY(alloc(f.offU, (np + 1) * sizeof(int64_t)));
     HM_TRY(alloc(f.offV, (np + 1) * sizeof(int64_t)));
@@ -396,14 +396,14 @@ Err bases_and_cores(hm_ctx *c, int level) {
     k_pack<<<(int)np, 128, 0, st>>>(g.pair_alpha.as<int>(), cu.int_idx.as<int>(), g.pair_color.as<int>(),
                                     g.pair_T.as<int>(), cu.ent.as<int>(), n, r, f.kU.as<int>(), f.kV.as<int>(),
                                     f.offU.as<int64_t>(), f.offV.as<int64_t>(), c->cur.Y.as<double>(),
-                                    c->cur.Z.as<double>(), f.U.as<double>(), f.V.as<double>());
+                                    c->cur.Z.as<double>(), f.U.as<double>(), f.V.as<double>()); ::hm::count_launch();
     HM_LAUNCH("pack");
     const size_t smem = (4 * (size_t)r * r + r) * sizeof(double);
     HM_CUDA(cudaFuncSetAttribute(k_core, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     k_core<<<(int)np, 32, smem, st>>>(g.pair_alpha.as<int>(), cu.int_idx.as<int>(), cu.ent.as<int>(), r,
                                       f.kU.as<int>(), f.kV.as<int>(), f.offU.as<int64_t>(), f.offV.as<int64_t>(),
                                       f.offB.as<int64_t>(), f.U.as<double>(), f.V.as<double>(), c->GO.as<double>(),
-                                      c->GP.as<double>(), c->scratch_a.as<double>(), f.B.as<double>());
+                                      c->GP.as<double>(), c->scratch_a.as<double>(), f.B.as<double>()); ::hm::count_launch();
     HM_LAUNCH("core");
     std::vector<int> hk;
     HM_TRY(to_host(hk, f.kU.p, np, st));
@@ -448,14 +448,14 @@ Err extract_leaf(hm_ctx *c) {
     HM_TRY(alloc(sz, (np + 1) * sizeof(int64_t)));
     HM_TRY(alloc(lf.offD, (np + 1) * sizeof(int64_t)));
     k_leaf_sizes<<<ceil_div(np, 256), 256, 0, st>>>(g.pair_alpha.as<int>(), cu.near_idx.as<int>(), cu.ent.as<int>(), np,
-                                                    sz.as<int64_t>());
+                                                    sz.as<int64_t>()); ::hm::count_launch();
     HM_LAUNCH("leaf_sizes");
     HM_TRY(scan_exclusive(sz.as<int64_t>(), lf.offD.as<int64_t>(), np, st));
     HM_TRY(read_scalar(lf.nD, lf.offD.as<int64_t>() + np, st));
     HM_TRY(alloc(lf.D, std::max<int64_t>(lf.nD, 1) * sizeof(double)));
     k_leaf_extract<<<(int)np, 128, 0, st>>>(g.pair_alpha.as<int>(), cu.near_idx.as<int>(), g.pair_color.as<int>(),
                                             cu.ent.as<int>(), c->n, g.m_cols, lf.offD.as<int64_t>(),
-                                            c->cur.Y.as<double>(), lf.D.as<double>());
+                                            c->cur.Y.as<double>(), lf.D.as<double>()); ::hm::count_launch();
     HM_LAUNCH("leaf_extract");
     lf.done = true;
     return ok();

@@ -357,9 +357,9 @@ Err color_cut(hm_ctx *c, int level, bool leaf) {
     HM_TRY(alloc(first, (np + 1) * sizeof(int64_t)));
     HM_TRY(alloc(fscan, (np + 1) * sizeof(int64_t)));
     HM_TRY(alloc(rep, np * sizeof(int)));
-    k_pair_alpha<<<ceil_div(nc, 128), 128, 0, st>>>(g.pair_ptr, nc, g.pair_alpha.as<int>());
+    k_pair_alpha<<<ceil_div(nc, 128), 128, 0, st>>>(g.pair_ptr, nc, g.pair_alpha.as<int>()); ::hm::count_launch();
     k_pair_keys<<<ceil_div(np, 128), 128, 0, st>>>(g.pair_ptr, g.pair_col, g.pair_alpha.as<int>(), np, sptr, sidx,
-                                                   g.pair_T.as<int>(), first.as<int64_t>(), rep.as<int>());
+                                                   g.pair_T.as<int>(), first.as<int64_t>(), rep.as<int>()); ::hm::count_launch();
     HM_LAUNCH("pair_keys");
     HM_TRY(scan_exclusive(first.as<int64_t>(), fscan.as<int64_t>(), np, st));
     HM_TRY(read_scalar(g.n_vertices, fscan.as<int64_t>() + np, st));
@@ -371,7 +371,7 @@ Err color_cut(hm_ctx *c, int level, bool leaf) {
     HM_TRY(alloc(g.vertex_degree, nv * sizeof(int)));
     k_vertex_ids<<<ceil_div(np, 256), 256, 0, st>>>(first.as<int64_t>(), fscan.as<int64_t>(), rep.as<int>(),
                                                     g.pair_col, np, g.pair_vertex.as<int>(),
-                                                    g.vertex_pair.as<int>(), g.vertex_beta.as<int>());
+                                                    g.vertex_pair.as<int>(), g.vertex_beta.as<int>()); ::hm::count_launch();
     HM_LAUNCH("vertex_ids");
 
     // vertices by beta
@@ -380,11 +380,11 @@ Err color_cut(hm_ctx *c, int level, bool leaf) {
     HM_TRY(alloc(vptr64, (nc + 1) * sizeof(int64_t)));
     HM_TRY(alloc(vidx, nv * sizeof(int)));
     k_vby_beta<<<ceil_div(nc, 128), 128, 0, st>>>(g.pair_ptr, g.pair_T.as<int>(), first.as<int64_t>(),
-                                                  g.pair_vertex.as<int>(), nc, 0, vcnt.as<int>(), nullptr, nullptr);
+                                                  g.pair_vertex.as<int>(), nc, 0, vcnt.as<int>(), nullptr, nullptr); ::hm::count_launch();
     HM_TRY(scan_counts_i32(vcnt.as<int>(), vptr64.as<int64_t>(), nc, st, c->scan_tmp));
     k_vby_beta<<<ceil_div(nc, 128), 128, 0, st>>>(g.pair_ptr, g.pair_T.as<int>(), first.as<int64_t>(),
                                                   g.pair_vertex.as<int>(), nc, 1, nullptr, vptr64.as<int64_t>(),
-                                                  vidx.as<int>());
+                                                  vidx.as<int>()); ::hm::count_launch();
     HM_LAUNCH("vby_beta");
     {
         std::vector<int64_t> h;
@@ -402,7 +402,7 @@ Err color_cut(hm_ctx *c, int level, bool leaf) {
     k_edges<<<(int)nv, 256, bm_bytes, st>>>(nv, g.vertex_pair.as<int>(), g.vertex_beta.as<int>(),
                                             g.pair_alpha.as<int>(), g.pair_ptr, g.pair_vertex.as<int>(), sptr, sidx,
                                             vptr.as<int>(), vidx.as<int>(), 0, g.vertex_degree.as<int>(), nullptr,
-                                            nullptr);
+                                            nullptr); ::hm::count_launch();
     HM_LAUNCH("edges count");
     HM_TRY(scan_counts_i32(g.vertex_degree.as<int>(), adj_ptr.as<int64_t>(), nv, st, c->scan_tmp));
     int64_t n_adj = 0;
@@ -412,7 +412,7 @@ Err color_cut(hm_ctx *c, int level, bool leaf) {
     k_edges<<<(int)nv, 256, bm_bytes, st>>>(nv, g.vertex_pair.as<int>(), g.vertex_beta.as<int>(),
                                             g.pair_alpha.as<int>(), g.pair_ptr, g.pair_vertex.as<int>(), sptr, sidx,
                                             vptr.as<int>(), vidx.as<int>(), 1, nullptr, adj_ptr.as<int64_t>(),
-                                            adj.as<int>());
+                                            adj.as<int>()); ::hm::count_launch();
     HM_LAUNCH("edges fill");
 
     // DSatur
@@ -422,9 +422,9 @@ Err color_cut(hm_ctx *c, int level, bool leaf) {
     HM_TRY(alloc(status, 2 * sizeof(int)));
     HM_CUDA(cudaMemsetAsync(status.p, 0, 2 * sizeof(int), st));
     k_dsatur_init<<<ceil_div(nv, 256), 256, 0, st>>>(nv, g.vertex_degree.as<int>(), key.as<unsigned long long>(),
-                                                      forb.as<unsigned int>());
+                                                      forb.as<unsigned int>()); ::hm::count_launch();
     k_dsatur<<<1, 1024, 0, st>>>(nv, adj_ptr.as<int64_t>(), adj.as<int>(), key.as<unsigned long long>(),
-                                 forb.as<unsigned int>(), g.vertex_color.as<int>(), status.as<int>());
+                                 forb.as<unsigned int>(), g.vertex_color.as<int>(), status.as<int>()); ::hm::count_launch();
     HM_LAUNCH("dsatur");
     int hs[2];
     HM_CUDA(cudaMemcpyAsync(hs, status.p, sizeof(hs), cudaMemcpyDeviceToHost, st));
@@ -433,7 +433,7 @@ Err color_cut(hm_ctx *c, int level, bool leaf) {
     g.n_colors = hs[0];
     const int chi = g.n_colors;
     k_pair_color<<<ceil_div(np, 256), 256, 0, st>>>(g.pair_vertex.as<int>(), g.vertex_color.as<int>(), np,
-                                                    g.pair_color.as<int>());
+                                                    g.pair_color.as<int>()); ::hm::count_launch();
     HM_LAUNCH("pair_color");
 
     // active tables
@@ -441,31 +441,31 @@ Err color_cut(hm_ctx *c, int level, bool leaf) {
     HM_TRY(alloc(act, (size_t)chi * nc));
     HM_CUDA(cudaMemsetAsync(act.p, 0, (size_t)chi * nc, st));
     k_act_mark<<<ceil_div(nv, 256), 256, 0, st>>>(g.vertex_beta.as<int>(), g.vertex_color.as<int>(), nv, nc,
-                                                   act.as<unsigned char>());
+                                                   act.as<unsigned char>()); ::hm::count_launch();
     HM_TRY(alloc(cnt, std::max(chi, nc) * sizeof(int)));
     HM_TRY(alloc(off64, (std::max(chi, nc) + 1) * sizeof(int64_t)));
-    k_act_by_color<<<chi, 1024, 0, st>>>(act.as<unsigned char>(), nc, 0, cnt.as<int>(), nullptr, nullptr);
+    k_act_by_color<<<chi, 1024, 0, st>>>(act.as<unsigned char>(), nc, 0, cnt.as<int>(), nullptr, nullptr); ::hm::count_launch();
     HM_TRY(scan_counts_i32(cnt.as<int>(), off64.as<int64_t>(), chi, st, c->scan_tmp));
     std::vector<int64_t> hoff;
     HM_TRY(to_host(hoff, off64.p, chi + 1, st));
     const int64_t na = hoff[chi];
     HM_TRY(alloc(g.act_box, na * sizeof(int)));
     k_act_by_color<<<chi, 1024, 0, st>>>(act.as<unsigned char>(), nc, 1, nullptr, off64.as<int64_t>(),
-                                         g.act_box.as<int>());
+                                         g.act_box.as<int>()); ::hm::count_launch();
     HM_LAUNCH("act_by_color");
     {
         std::vector<int> h32(hoff.begin(), hoff.end());
         HM_TRY(to_dev(g.act_ptr, h32, st));
     }
     k_act_by_entry<<<ceil_div(nc, 128), 128, 0, st>>>(act.as<unsigned char>(), nc, chi, 0, cnt.as<int>(), nullptr,
-                                                      nullptr);
+                                                      nullptr); ::hm::count_launch();
     HM_TRY(scan_counts_i32(cnt.as<int>(), off64.as<int64_t>(), nc, st, c->scan_tmp));
     {
         std::vector<int64_t> h;
         HM_TRY(to_host(h, off64.p, nc + 1, st));
         HM_TRY(alloc(g.ent_col, std::max<int64_t>(h[nc], 1) * sizeof(int)));
         k_act_by_entry<<<ceil_div(nc, 128), 128, 0, st>>>(act.as<unsigned char>(), nc, chi, 1, nullptr,
-                                                          off64.as<int64_t>(), g.ent_col.as<int>());
+                                                          off64.as<int64_t>(), g.ent_col.as<int>()); ::hm::count_launch();
         HM_LAUNCH("act_by_entry");
         std::vector<int> h32(h.begin(), h.end());
         HM_TRY(to_dev(g.ent_cptr, h32, st));
@@ -475,14 +475,14 @@ Err color_cut(hm_ctx *c, int level, bool leaf) {
         DBuf sz, rowoff;
         HM_TRY(alloc(sz, std::max<int64_t>(na, 1) * sizeof(int)));
         HM_TRY(alloc(rowoff, (na + 1) * sizeof(int64_t)));
-        k_act_sizes<<<ceil_div(na, 256), 256, 0, st>>>(g.act_box.as<int>(), na, cu.ent.as<int>(), sz.as<int>());
+        k_act_sizes<<<ceil_div(na, 256), 256, 0, st>>>(g.act_box.as<int>(), na, cu.ent.as<int>(), sz.as<int>()); ::hm::count_launch();
         HM_TRY(scan_counts_i32(sz.as<int>(), rowoff.as<int64_t>(), na, st, c->scan_tmp));
         std::vector<int64_t> hro;
         HM_TRY(to_host(hro, rowoff.p, na + 1, st));
         g.n_act_rows = hro[na];
         HM_TRY(alloc(g.act_rows, std::max<int64_t>(g.n_act_rows, 1) * sizeof(int)));
         k_act_rows<<<ceil_div(na * 32, 256), 256, 0, st>>>(g.act_box.as<int>(), na, cu.ent.as<int>(),
-                                                           rowoff.as<int64_t>(), g.act_rows.as<int>());
+                                                           rowoff.as<int64_t>(), g.act_rows.as<int>()); ::hm::count_launch();
         HM_LAUNCH("act_rows");
         std::vector<int64_t> crp(chi + 1);
         for (int k = 0; k <= chi; ++k) crp[k] = hro[hoff[k]];

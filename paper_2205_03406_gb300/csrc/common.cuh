@@ -46,6 +46,10 @@ inline Err fail(hm_status c, const std::string &m) { Err e; e.code = c; e.msg = 
 // Stream on which the current API call allocates and frees (set on entry).
 extern thread_local cudaStream_t g_alloc_stream;
 
+// Kernel launches made by this library (every launch site calls this once).
+void count_launch();
+long long launches_so_far();
+
 // A device allocation: move-only, freed (stream-ordered) when it goes out of
 // scope, so temporaries of a call never outlive it and never force a device
 // synchronisation.

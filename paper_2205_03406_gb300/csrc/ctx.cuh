@@ -122,6 +122,7 @@ struct hm_ctx {
 
     hm_info info;
     double t_sample = 0.0;
+    double t_tc = 0.0;        // device time of the tensor-core contraction kernels
 };
 
 namespace hm {

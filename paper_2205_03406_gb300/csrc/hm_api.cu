@@ -7,8 +7,13 @@
 #include <cmath>
 #include <cstring>
 
+#include <atomic>
+
 namespace hm {
 thread_local cudaStream_t g_alloc_stream = nullptr;
+static std::atomic<long long> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+long long launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
 }
 
 using namespace hm;
@@ -211,6 +216,8 @@ static Err keep_current(hm_ctx *c, int idx, bool leaf) {
 
 static Err compress_all(hm_ctx *c, const hm_op *op) {
     const auto t0 = std::chrono::steady_clock::now();
+    const long long launches0 = launches_so_far();
+    c->t_tc = 0.0;
     // (phase, start event, end event) triples, read once at the end
     std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev;
     int cur_phase = -1;
@@ -284,12 +291,15 @@ static Err compress_all(hm_ctx *c, const hm_op *op) {
     c->t_sample = ts;
     hm_info &in = c->info;
     std::memset(&in, 0, sizeof(in));
-    for (int k = 0; k < 8; ++k) in.seconds_phase[k] = phase[k];
+    for (int k = 0; k < 7; ++k) in.seconds_phase[k] = phase[k];
+    in.seconds_phase[7] = c->t_tc;
     in.n = c->n;
     in.L = c->L;
     for (auto &lv : c->levels) in.n_boxes += lv.nb;
     int64_t floats = 0;
+    in.kernel_launches = launches_so_far() - launches0;
     for (int l = 2; l <= c->L && l < 31; ++l) {
+        in.act_rows[l] = c->colorings[l].n_act_rows;
         in.colors[l] = c->colorings[l].n_colors;
         in.pairs[l] = c->colorings[l].n_pairs;
         in.vertices[l] = c->colorings[l].n_vertices;
@@ -298,6 +308,7 @@ static Err compress_all(hm_ctx *c, const hm_op *op) {
         in.max_rank = std::max(in.max_rank, f.max_k);
     }
     if (c->L + 1 < 32) {
+        in.act_rows[c->L + 1] = c->colorings[c->L + 1].n_act_rows;
         in.colors[c->L + 1] = c->colorings[c->L + 1].n_colors;
         in.pairs[c->L + 1] = c->colorings[c->L + 1].n_pairs;
         in.vertices[c->L + 1] = c->colorings[c->L + 1].n_vertices;
@@ -359,36 +370,36 @@ hm_status hm_relerr(hm_ctx *c, const hm_op *op, int iters, double *err) {
         HM_TRY(alloc(w, n * 2 * sizeof(double)));
         HM_TRY(alloc(sq, 2 * sizeof(double)));
         const int g = ceil_div(n, 256);
-        k_start_vector<<<g, 256, 0, c->st>>>(n, (unsigned long long)c->cfg.seed + 1ull, x.as<double>());
+        k_start_vector<<<g, 256, 0, c->st>>>(n, (unsigned long long)c->cfg.seed + 1ull, x.as<double>()); ::hm::count_launch();
         HM_LAUNCH("start_vector");
         double lam[2] = {0, 0};
         {  // normalise the start vector
             HM_CUDA(cudaMemsetAsync(sq.p, 0, 2 * sizeof(double), c->st));
-            k_colsq<<<64, 256, 0, c->st>>>(x.as<double>(), n, 2, sq.as<double>());
+            k_colsq<<<64, 256, 0, c->st>>>(x.as<double>(), n, 2, sq.as<double>()); ::hm::count_launch();
             double h[2];
             HM_CUDA(cudaMemcpyAsync(h, sq.p, sizeof(h), cudaMemcpyDeviceToHost, c->st));
             HM_CUDA(cudaStreamSynchronize(c->st));
-            k_scale2<<<g, 256, 0, c->st>>>(x.as<double>(), n, 1.0 / sqrt(h[0]), 1.0 / sqrt(h[1]));
+            k_scale2<<<g, 256, 0, c->st>>>(x.as<double>(), n, 1.0 / sqrt(h[0]), 1.0 / sqrt(h[1])); ::hm::count_launch();
         }
         for (int it = 0; it < iters; ++it) {
             // w = M x: col 0 (A~ - A) x0, col 1 A x1
             HM_TRY(op_apply_vectors(c, op, x.as<double>(), ax.as<double>(), 0, t1, t2));
             HM_TRY(apply_sorted(c, x.as<double>(), hx.as<double>(), 2, 0));
-            k_axpby2<<<g, 256, 0, c->st>>>(hx.as<double>(), ax.as<double>(), n, w.as<double>());
+            k_axpby2<<<g, 256, 0, c->st>>>(hx.as<double>(), ax.as<double>(), n, w.as<double>()); ::hm::count_launch();
             // x = M^* w
             HM_TRY(op_apply_vectors(c, op, w.as<double>(), ax.as<double>(), 1, t1, t2));
             HM_TRY(apply_sorted(c, w.as<double>(), hx.as<double>(), 2, 1));
-            k_axpby2<<<g, 256, 0, c->st>>>(hx.as<double>(), ax.as<double>(), n, x.as<double>());
+            k_axpby2<<<g, 256, 0, c->st>>>(hx.as<double>(), ax.as<double>(), n, x.as<double>()); ::hm::count_launch();
             HM_LAUNCH("power step");
             HM_CUDA(cudaMemsetAsync(sq.p, 0, 2 * sizeof(double), c->st));
-            k_colsq<<<64, 256, 0, c->st>>>(x.as<double>(), n, 2, sq.as<double>());
+            k_colsq<<<64, 256, 0, c->st>>>(x.as<double>(), n, 2, sq.as<double>()); ::hm::count_launch();
             double h[2];
             HM_CUDA(cudaMemcpyAsync(h, sq.p, sizeof(h), cudaMemcpyDeviceToHost, c->st));
             HM_CUDA(cudaStreamSynchronize(c->st));
             lam[0] = sqrt(h[0]);
             lam[1] = sqrt(h[1]);
             k_scale2<<<g, 256, 0, c->st>>>(x.as<double>(), n, lam[0] > 0 ? 1.0 / lam[0] : 0.0,
-                                           lam[1] > 0 ? 1.0 / lam[1] : 0.0);
+                                           lam[1] > 0 ? 1.0 / lam[1] : 0.0); ::hm::count_launch();
         }
         *err = lam[1] > 0.0 ? sqrt(lam[0]) / sqrt(lam[1]) : 0.0;
         return ok();
@@ -400,6 +411,7 @@ hm_status hm_relerr(hm_ctx *c, const hm_op *op, int iters, double *err) {
 hm_status hm_get_info(hm_ctx *c, hm_info *out) {
     if (!c || !out) return HM_EINVAL;
     *out = c->info;
+    out->launches_total = launches_so_far();
     if (c->stage >= 1) {
         out->n = c->n;
         out->L = c->L;

@@ -188,7 +188,7 @@ Err peel_level(hm_ctx *c, int level, bool leaf) {
             k_desc_count<<<ceil_div(np, 256), 256, 0, st>>>(gj.pair_alpha.as<int>(), cj.int_idx.as<int>(), np,
                                                             cj.ent.as<int>(), cl.pt2ent.as<int>(),
                                                             side ? f.kU.as<int>() : f.kV.as<int>(), cols, side,
-                                                            xsz);
+                                                            xsz); ::hm::count_launch();
             HM_LAUNCH("desc_count");
             HM_TRY(scan_exclusive(xsz, xoff, np, st));
             int64_t xtot = 0;
@@ -200,7 +200,7 @@ Err peel_level(hm_ctx *c, int level, bool leaf) {
                                               side ? f.kU.as<int>() : f.kV.as<int>(),
                                               side ? f.offU.as<int64_t>() : f.offV.as<int64_t>(),
                                               side ? f.U.as<double>() : f.V.as<double>(), G, cols, leaf ? 1 : 0,
-                                              side, xoff, c->scratch_d.as<double>());
+                                              side, xoff, c->scratch_d.as<double>()); ::hm::count_launch();
             HM_LAUNCH("peel_x");
             PeelLevel P;
             P.entl = cl.ent.as<int>();
@@ -228,7 +228,7 @@ Err peel_level(hm_ctx *c, int level, bool leaf) {
             P.V = f.V.as<double>();
             P.B = f.B.as<double>();
             double *OUT = side ? c->cur.Z.as<double>() : c->cur.Y.as<double>();
-            k_peel_update<<<(int)g.n_pairs, 128, smem, st>>>(P, side, xoff, c->scratch_d.as<double>(), OUT);
+            k_peel_update<<<(int)g.n_pairs, 128, smem, st>>>(P, side, xoff, c->scratch_d.as<double>(), OUT); ::hm::count_launch();
             HM_LAUNCH("peel_update");
         }
     }

@@ -71,7 +71,7 @@ Err make_gaussians(hm_ctx *c, int level) {
     const Cut &cu = c->cuts[level];
     k_gauss<<<ceil_div(n * r, 256), 256, 0, c->st>>>(n, r, cu.pt2ent.as<int>(), cu.ent.as<int>(), level,
                                                      (unsigned long long)c->cfg.seed, c->GO.as<double>(),
-                                                     c->GP.as<double>());
+                                                     c->GP.as<double>()); ::hm::count_launch();
     HM_LAUNCH("gauss");
     c->gauss_level = level;
     return ok();
@@ -207,7 +207,7 @@ template <int MAXQ>
 static void launch_sample64(const OpDev &o, int trans, const int64_t *rp, const int *rows, const double *G, int NC,
                             double *o0, double *o1, int split, int chi, cudaStream_t st) {
     dim3 grid(ceil_div(o.n, TR), chi);
-    k_sample64<MAXQ><<<grid, 256, 0, st>>>(o, trans, rp, rows, G, NC, o0, o1, split);
+    k_sample64<MAXQ><<<grid, 256, 0, st>>>(o, trans, rp, rows, G, NC, o0, o1, split); ::hm::count_launch();
 }
 
 static Err run_sample64(const OpDev &o, int trans, const int64_t *rp, const int *rows, const double *G, int NC,
@@ -265,13 +265,13 @@ static Err sample_callback(hm_ctx *c, const hm_op *op, const Coloring &g, bool l
         k_build_omega<<<ceil_div(n, 256), 256, 0, c->st>>>(n, chi, cols, cu.pt2ent.as<int>(), g.ent_cptr.as<int>(),
                                                            g.ent_col.as<int>(),
                                                            side ? c->GP.as<double>() : c->GO.as<double>(), leaf,
-                                                           cu.ent.as<int>(), c->perm.as<int>(), Om);
+                                                           cu.ent.as<int>(), c->perm.as<int>(), Om); ::hm::count_launch();
         HM_LAUNCH("build_omega");
         const int rc = op->apply(op->user, side, Om, Yd, s, (void *)c->st);
         if (rc != 0) return fail(HM_EOP, "black-box operator returned " + std::to_string(rc));
         HM_LAUNCH("user operator");
         k_gather_samples<<<ceil_div(n * s, 256), 256, 0, c->st>>>(n, (int)s, c->perm.as<int>(), Yd, side ? Z : Y,
-                                                                  cols);
+                                                                  cols); ::hm::count_launch();
         HM_LAUNCH("gather_samples");
     }
     return ok();
@@ -310,7 +310,7 @@ Err sample_level(hm_ctx *c, const hm_op *op, int level, bool leaf) {
     if (leaf) {
         dim3 grid(ceil_div(n, 64), chi, ceil_div(cols, 64));
         k_sample_leaf64<<<grid, 256, 0, c->st>>>(o, g.act_ptr.as<int>(), g.act_box.as<int>(), cu.ent.as<int>(), cols,
-                                                 S.Y.as<double>());
+                                                 S.Y.as<double>()); ::hm::count_launch();
         HM_LAUNCH("sample_leaf64");
         return ok();
     }
@@ -322,7 +322,7 @@ Err sample_level(hm_ctx *c, const hm_op *op, int level, bool leaf) {
         // symmetric kernel: one sweep for [Y | Z]
         HM_TRY(ensure(c->scratch_c, (size_t)n * 2 * cols * sizeof(double)));
         k_interleave<<<ceil_div(n * cols, 256), 256, 0, c->st>>>(c->GO.as<double>(), c->GP.as<double>(), n, cols,
-                                                                 c->scratch_c.as<double>());
+                                                                 c->scratch_c.as<double>()); ::hm::count_launch();
         HM_LAUNCH("interleave");
         return run_sample64(o, 0, rp, rows, c->scratch_c.as<double>(), 2 * cols, S.Y.as<double>(), S.Z.as<double>(),
                             cols, chi, c->st);

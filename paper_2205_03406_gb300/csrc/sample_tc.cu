@@ -498,7 +498,7 @@ __global__ void k_make_xdf(const double *xs, int64_t n, float4 *xdf) {
 static Err make_xdf(hm_ctx *c) {
     if (c->xdf.p) return ok();
     HM_TRY(alloc(c->xdf, (size_t)c->n * 2 * sizeof(float4)));
-    tc::k_make_xdf<<<ceil_div(c->n, 256), 256, 0, c->st>>>(c->xs.as<double>(), c->n, c->xdf.as<float4>());
+    tc::k_make_xdf<<<ceil_div(c->n, 256), 256, 0, c->st>>>(c->xs.as<double>(), c->n, c->xdf.as<float4>()); ::hm::count_launch();
     HM_LAUNCH("make_xdf");
     return ok();
 }
@@ -529,11 +529,11 @@ Err sample_tc(hm_ctx *c, int level, int kernel) {
     if (total > 0) {
         k_pack_b<<<ceil_div(total * 2 * r * 8, 256), 256, 0, st>>>(
             cfd.as<int64_t>(), chi, g.act_rows_ptr.as<int64_t>(), g.act_rows.as<int>(), c->GO.as<double>(),
-            c->GP.as<double>(), r, total, c->scratch_b.as<unsigned char>());
+            c->GP.as<double>(), r, total, c->scratch_b.as<unsigned char>()); ::hm::count_launch();
         k_pack_coords<<<ceil_div(total * KC, 256), 256, 0, st>>>(cfd.as<int64_t>(), chi,
                                                                   g.act_rows_ptr.as<int64_t>(), g.act_rows.as<int>(),
                                                                   c->xdf.as<float4>(), r, total,
-                                                                  c->scratch_b.as<unsigned char>());
+                                                                  c->scratch_b.as<unsigned char>()); ::hm::count_launch();
         HM_LAUNCH("pack");
     }
     Params P;
@@ -548,11 +548,15 @@ Err sample_tc(hm_ctx *c, int level, int kernel) {
     P.status = c->scratch_c.as<int>();
     const int smem = 2 * stage_bytes(r) + 1024;
     dim3 grid(ceil_div(n, TM), chi);
+    cudaEvent_t e0, e1;
+    HM_CUDA(cudaEventCreate(&e0));
+    HM_CUDA(cudaEventCreate(&e1));
+    HM_CUDA(cudaEventRecord(e0, st));
     switch (kernel) {
 #define LAUNCH(K)                                                                                   \
     case K:                                                                                         \
         HM_CUDA(cudaFuncSetAttribute(k_sample_tc<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)); \
-        k_sample_tc<K><<<grid, NTHREADS, smem, st>>>(P);                                            \
+        k_sample_tc<K><<<grid, NTHREADS, smem, st>>>(P); ::hm::count_launch();                                            \
         break;
         LAUNCH(HM_K_LOG)
         LAUNCH(HM_K_LAPLACE3D)
@@ -562,8 +566,13 @@ Err sample_tc(hm_ctx *c, int level, int kernel) {
     default: return fail(HM_EINVAL, "sample_tc: unknown kernel");
     }
     HM_LAUNCH("sample_tc");
+    HM_CUDA(cudaEventRecord(e1, st));
     int status = 0;
     HM_TRY(read_scalar(status, c->scratch_c.p, st));
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess) c->t_tc += ms * 1e-3;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
     if (status) return fail(HM_ETIMEOUT, "sample_tc: a pipeline wait expired");
     return ok();
 }
@@ -580,7 +589,7 @@ Err sample_leaf_mixed(hm_ctx *c, int kernel) {
 #define LAUNCH(K)                                                                                       \
     case K:                                                                                             \
         k_sample_leaf32<K><<<grid, 256, 0, c->st>>>(c->xdf.as<float4>(), n, g.act_ptr.as<int>(),          \
-                                                     g.act_box.as<int>(), cu.ent.as<int>(), m, c->cur.Y.as<double>()); \
+                                                     g.act_box.as<int>(), cu.ent.as<int>(), m, c->cur.Y.as<double>()); ::hm::count_launch(); \
         break;
         LAUNCH(HM_K_LOG)
         LAUNCH(HM_K_LAPLACE3D)

@@ -48,7 +48,7 @@ __global__ void k_scan_exclusive_i64(const int64_t *in, int64_t *out, int64_t n)
 }
 
 Err scan_exclusive(const int64_t *in_dev, int64_t *out_dev, int64_t n, cudaStream_t st) {
-    k_scan_exclusive_i64<<<1, 1024, 0, st>>>(in_dev, out_dev, n);
+    k_scan_exclusive_i64<<<1, 1024, 0, st>>>(in_dev, out_dev, n); ::hm::count_launch();
     HM_LAUNCH("scan_exclusive");
     return ok();
 }
@@ -61,7 +61,7 @@ __global__ void k_i32_to_i64(const int *in, int64_t *out, int64_t n) {
 Err scan_counts_i32(const int *counts_dev, int64_t *out_dev, int64_t n, cudaStream_t st, DBuf &tmp) {
     HM_TRY(ensure(tmp, (size_t)(n + 1) * sizeof(int64_t)));
     if (n > 0) {
-        k_i32_to_i64<<<ceil_div(n, 256), 256, 0, st>>>(counts_dev, tmp.as<int64_t>(), n);
+        k_i32_to_i64<<<ceil_div(n, 256), 256, 0, st>>>(counts_dev, tmp.as<int64_t>(), n); ::hm::count_launch();
         HM_LAUNCH("i32_to_i64");
     }
     return scan_exclusive(tmp.as<int64_t>(), out_dev, n, st);
@@ -170,12 +170,12 @@ static Err bitonic_sort(ulonglong2 *a, int64_t npad, cudaStream_t st) {
     for (int64_t k = 2; k <= npad; k <<= 1) {
         int64_t j = k >> 1;
         for (; j >= 2048; j >>= 1) {
-            k_bitonic_step<<<nb, 256, 0, st>>>(a, npad, j, k);
+            k_bitonic_step<<<nb, 256, 0, st>>>(a, npad, j, k); ::hm::count_launch();
         }
         if (npad >= 2048) {
-            k_bitonic_shared<<<(int)(npad / 2048), 1024, 0, st>>>(a, npad, k, j);
+            k_bitonic_shared<<<(int)(npad / 2048), 1024, 0, st>>>(a, npad, k, j); ::hm::count_launch();
         } else {
-            for (; j > 0; j >>= 1) k_bitonic_step<<<nb, 256, 0, st>>>(a, npad, j, k);
+            for (; j > 0; j >>= 1) k_bitonic_step<<<nb, 256, 0, st>>>(a, npad, j, k); ::hm::count_launch();
         }
     }
     HM_LAUNCH("bitonic");
@@ -374,7 +374,7 @@ Err build_tree(hm_ctx *c, const double *points_dev, int64_t n) {
         const int nb = 64;
         DBuf mm;
         HM_TRY(alloc(mm, nb * 6 * sizeof(double)));
-        k_minmax<<<nb, 256, 0, st>>>(points_dev, n, d, mm.as<double>());
+        k_minmax<<<nb, 256, 0, st>>>(points_dev, n, d, mm.as<double>()); ::hm::count_launch();
         HM_LAUNCH("minmax");
         std::vector<double> h;
         HM_TRY(to_host(h, mm.p, nb * 6, st));
@@ -406,7 +406,7 @@ Err build_tree(hm_ctx *c, const double *points_dev, int64_t n) {
     HM_TRY(alloc(q, n * 3 * sizeof(int)));
     HM_TRY(alloc(ksorted, n * sizeof(unsigned long long)));
     k_quantize<<<ceil_div(npad, 256), 256, 0, st>>>(points_dev, n, d, c->lo[0], c->lo[1], c->lo[2], c->side,
-                                                    q.as<int>(), keys.as<ulonglong2>(), npad);
+                                                    q.as<int>(), keys.as<ulonglong2>(), npad); ::hm::count_launch();
     HM_LAUNCH("quantize");
     HM_TRY(bitonic_sort(keys.as<ulonglong2>(), npad, st));
     HM_TRY(alloc(c->perm, n * sizeof(int)));
@@ -414,7 +414,7 @@ Err build_tree(hm_ctx *c, const double *points_dev, int64_t n) {
     HM_TRY(alloc(c->qs, n * 3 * sizeof(int)));
     k_gather_sorted<<<ceil_div(n, 256), 256, 0, st>>>(keys.as<ulonglong2>(), points_dev, q.as<int>(), n, d,
                                                       c->perm.as<int>(), c->xs.as<double>(), c->qs.as<int>(),
-                                                      ksorted.as<unsigned long long>());
+                                                      ksorted.as<unsigned long long>()); ::hm::count_launch();
     HM_LAUNCH("gather_sorted");
     keys.release();
     q.release();
@@ -439,18 +439,18 @@ Err build_tree(hm_ctx *c, const double *points_dev, int64_t n) {
         HM_TRY(alloc(bo, n * sizeof(int)));
         HM_CUDA(cudaMemsetAsync(bo.p, 0, n * sizeof(int), st));
         box_of.push_back(std::move(bo));
-        k_level_leaf<<<1, 32, 0, st>>>(c->levels[0].box.as<int>(), 1, 0, c->cfg.leaf_size, c->cfg.uniform_depth);
+        k_level_leaf<<<1, 32, 0, st>>>(c->levels[0].box.as<int>(), 1, 0, c->cfg.leaf_size, c->cfg.uniform_depth); ::hm::count_launch();
         HM_LAUNCH("level_leaf");
     }
     int gid = 1;
     const int nbk = ceil_div(n, 256);
     for (int l = 0; l < QBITS; ++l) {
         k_leafgid_update<<<nbk, 256, 0, st>>>(box_of[l].as<int>(), c->levels[l].box.as<int>(), n,
-                                              leafgid.as<int>());
+                                              leafgid.as<int>()); ::hm::count_launch();
         const int shift = d * (QBITS - l - 1);
         k_level_heads<<<nbk, 256, 0, st>>>(ksorted.as<unsigned long long>(), box_of[l].as<int>(),
                                            c->levels[l].box.as<int>(), n, shift, head.as<int64_t>(),
-                                           active.as<int>());
+                                           active.as<int>()); ::hm::count_launch();
         HM_LAUNCH("level_heads");
         HM_TRY(scan_exclusive(head.as<int64_t>(), head_scan.as<int64_t>(), n, st));
         int64_t nb_next = 0;
@@ -463,10 +463,10 @@ Err build_tree(hm_ctx *c, const double *points_dev, int64_t n) {
         HM_TRY(alloc(bo, n * sizeof(int)));
         k_level_fill<<<nbk, 256, 0, st>>>(head_scan.as<int64_t>(), head.as<int64_t>(), active.as<int>(),
                                           box_of[l].as<int>(), c->qs.as<int>(), n, l + 1, gid, nx.box.as<int>(),
-                                          bo.as<int>());
+                                          bo.as<int>()); ::hm::count_launch();
         HM_LAUNCH("level_fill");
         k_level_leaf<<<ceil_div(nb_next, 256), 256, 0, st>>>(nx.box.as<int>(), (int)nb_next, l + 1,
-                                                              c->cfg.leaf_size, c->cfg.uniform_depth);
+                                                              c->cfg.leaf_size, c->cfg.uniform_depth); ::hm::count_launch();
         HM_LAUNCH("level_leaf");
         c->level_off.push_back(gid);
         gid += (int)nb_next;
@@ -474,7 +474,7 @@ Err build_tree(hm_ctx *c, const double *points_dev, int64_t n) {
         box_of.push_back(std::move(bo));
     }
     k_leafgid_update<<<nbk, 256, 0, st>>>(box_of.back().as<int>(), c->levels.back().box.as<int>(), n,
-                                          leafgid.as<int>());
+                                          leafgid.as<int>()); ::hm::count_launch();
     c->L = (int)c->levels.size() - 1;
     const int L = c->L;
 
@@ -499,7 +499,7 @@ Err build_tree(hm_ctx *c, const double *points_dev, int64_t n) {
     for (int l = 0; l <= L; ++l) {
         Cut &cu = c->cuts[l];
         k_cut_heads<<<nbk, 256, 0, st>>>(box_of[l].as<int>(), leafgid.as<int>(), c->level_off[l], n,
-                                         entgid.as<int>(), head.as<int64_t>());
+                                         entgid.as<int>(), head.as<int64_t>()); ::hm::count_launch();
         HM_LAUNCH("cut_heads");
         HM_TRY(scan_exclusive(head.as<int64_t>(), head_scan.as<int64_t>(), n, st));
         int64_t nc = 0;
@@ -510,20 +510,20 @@ Err build_tree(hm_ctx *c, const double *points_dev, int64_t n) {
         HM_TRY(alloc(cu.pt2ent, n * sizeof(int)));
         k_cut_fill<<<nbk, 256, 0, st>>>(head_scan.as<int64_t>(), head.as<int64_t>(), entgid.as<int>(), n,
                                         gid_level.as<int>(), gid_index.as<int>(), c->qs.as<int>(),
-                                        cu.ent.as<int>(), cu.pt2ent.as<int>());
+                                        cu.ent.as<int>(), cu.pt2ent.as<int>()); ::hm::count_launch();
         HM_LAUNCH("cut_fill");
         HM_TRY(alloc(cu.parent, nc * sizeof(int)));
         if (l == 0) {
             HM_CUDA(cudaMemsetAsync(cu.parent.p, 0, nc * sizeof(int), st));
         } else {
             k_cut_links<<<ceil_div(nc, 256), 256, 0, st>>>(cu.ent.as<int>(), cu.nc, c->cuts[l - 1].pt2ent.as<int>(),
-                                                           cu.parent.as<int>());
+                                                           cu.parent.as<int>()); ::hm::count_launch();
             HM_LAUNCH("cut_links");
             Cut &pv = c->cuts[l - 1];
             HM_TRY(alloc(pv.kid_begin, pv.nc * sizeof(int)));
             HM_TRY(alloc(pv.kid_end, pv.nc * sizeof(int)));
             k_cut_kids<<<ceil_div(pv.nc, 256), 256, 0, st>>>(pv.ent.as<int>(), pv.nc, cu.pt2ent.as<int>(),
-                                                             pv.kid_begin.as<int>(), pv.kid_end.as<int>());
+                                                             pv.kid_begin.as<int>(), pv.kid_end.as<int>()); ::hm::count_launch();
             HM_LAUNCH("cut_kids");
         }
     }
@@ -563,7 +563,7 @@ Err build_tree(hm_ctx *c, const double *points_dev, int64_t n) {
         const int g = ceil_div(cu.nc, 128);
         k_lists<<<g, 128, 0, st>>>(cu.ent.as<int>(), cu.nc, l, d, cu.parent.as<int>(), pv.near_ptr.as<int>(),
                                    pv.near_idx.as<int>(), pv.kid_begin.as<int>(), pv.kid_end.as<int>(), 0,
-                                   cn.as<int>(), ci.as<int>(), nullptr, nullptr, nullptr, nullptr, nullptr);
+                                   cn.as<int>(), ci.as<int>(), nullptr, nullptr, nullptr, nullptr, nullptr); ::hm::count_launch();
         HM_LAUNCH("lists count");
         HM_TRY(scan_counts_i32(cn.as<int>(), pn64.as<int64_t>(), cu.nc, st, c->scan_tmp));
         HM_TRY(scan_counts_i32(ci.as<int>(), pi64.as<int64_t>(), cu.nc, st, c->scan_tmp));
@@ -575,13 +575,13 @@ Err build_tree(hm_ctx *c, const double *points_dev, int64_t n) {
         k_lists<<<g, 128, 0, st>>>(cu.ent.as<int>(), cu.nc, l, d, cu.parent.as<int>(), pv.near_ptr.as<int>(),
                                    pv.near_idx.as<int>(), pv.kid_begin.as<int>(), pv.kid_end.as<int>(), 1,
                                    nullptr, nullptr, pn64.as<int64_t>(), pi64.as<int64_t>(), cu.near_idx.as<int>(),
-                                   cu.int_idx.as<int>(), cu.s_idx.as<int>());
+                                   cu.int_idx.as<int>(), cu.s_idx.as<int>()); ::hm::count_launch();
         HM_LAUNCH("lists fill");
         HM_TRY(alloc(cu.near_ptr, (cu.nc + 1) * sizeof(int)));
         HM_TRY(alloc(cu.int_ptr, (cu.nc + 1) * sizeof(int)));
         HM_TRY(alloc(cu.s_ptr, (cu.nc + 1) * sizeof(int)));
-        k_i64_to_i32<<<ceil_div(cu.nc + 1, 256), 256, 0, st>>>(pn64.as<int64_t>(), cu.near_ptr.as<int>(), cu.nc + 1);
-        k_i64_to_i32<<<ceil_div(cu.nc + 1, 256), 256, 0, st>>>(pi64.as<int64_t>(), cu.int_ptr.as<int>(), cu.nc + 1);
+        k_i64_to_i32<<<ceil_div(cu.nc + 1, 256), 256, 0, st>>>(pn64.as<int64_t>(), cu.near_ptr.as<int>(), cu.nc + 1); ::hm::count_launch();
+        k_i64_to_i32<<<ceil_div(cu.nc + 1, 256), 256, 0, st>>>(pi64.as<int64_t>(), cu.int_ptr.as<int>(), cu.nc + 1); ::hm::count_launch();
         HM_LAUNCH("ptr convert");
         // S pointers: near_ptr + int_ptr
         std::vector<int64_t> hn, hi;
