@@ -204,6 +204,24 @@ enum {
  */
 hm_status hm_export(hm_ctx *ctx, int what, int level, void *host_buf, size_t *bytes);
 
+/*
+ * hm_apply_noalloc: hm_apply without any device allocation.  (The paper has no
+ * counterpart; this is a library convenience.)  For callers that cannot
+ * allocate device memory when they apply the operator -- a serving loop whose
+ * process has given all free device memory to another framework's caching
+ * allocator, or a latency-critical loop that must not wait on cudaMalloc /
+ * cudaFree or risk running out of memory mid-request.  Its scratch (permuted
+ * vectors, per-pair intermediate products, offsets, level table) comes from one
+ * array of HM_APPLY_NOALLOC_SCRATCH_BYTES inside the library, which every GPU
+ * that loads the library holds until the process exits.  A request that needs
+ * more returns HM_ENOTSUP (use hm_apply).  The first call on a device looks up
+ * that array's address (cudaGetSymbolAddress), so it should come before any
+ * stream capture.  All calls share the array: calls that overlap on the GPU
+ * race.  Arguments, results and the other errors are those of hm_apply.
+ */
+#define HM_APPLY_NOALLOC_SCRATCH_BYTES (64u << 20)
+hm_status hm_apply_noalloc(hm_ctx *ctx, const double *x_dev, double *y_dev, int64_t nrhs, int trans);
+
 /* Human-readable description of the last error on this context. */
 const char *hm_last_error(const hm_ctx *ctx);
 

@@ -29,7 +29,7 @@ HM_LEVEL_LEAF = -1
  HM_X_FACTOR_OFFS, HM_X_LEAF_D, HM_X_VERTEX_DEGREE) = range(1, 17)
 
 EXPORTED = ["hm_create", "hm_destroy", "hm_tree_build", "hm_color", "hm_sample", "hm_compress", "hm_apply",
-            "hm_relerr", "hm_get_info", "hm_export", "hm_last_error"]
+            "hm_relerr", "hm_get_info", "hm_export", "hm_last_error", "hm_apply_noalloc"]
 
 
 class hm_config(ctypes.Structure):
@@ -74,6 +74,7 @@ def _load():
         "hm_sample": [P, ctypes.POINTER(hm_op), I],
         "hm_compress": [P, ctypes.POINTER(hm_op)],
         "hm_apply": [P, P, P, I64, I],
+        "hm_apply_noalloc": [P, P, P, I64, I],
         "hm_relerr": [P, ctypes.POINTER(hm_op), I, ctypes.POINTER(D)],
         "hm_get_info": [P, ctypes.POINTER(hm_info)],
         "hm_export": [P, I, I, P, ctypes.POINTER(ctypes.c_size_t)],
@@ -139,6 +140,11 @@ def hm_compress(ctx, op: hm_op):
 
 def hm_apply(ctx, x_dev: int, y_dev: int, nrhs: int, trans: int = 0):
     _check(ctx, _lib.hm_apply(ctx, ctypes.c_void_p(x_dev), ctypes.c_void_p(y_dev), nrhs, trans), "hm_apply")
+
+
+def hm_apply_noalloc(ctx, x_dev: int, y_dev: int, nrhs: int, trans: int = 0):
+    _check(ctx, _lib.hm_apply_noalloc(ctx, ctypes.c_void_p(x_dev), ctypes.c_void_p(y_dev), nrhs, trans),
+           "hm_apply_noalloc")
 
 
 def hm_relerr(ctx, op: hm_op, iters: int = 20) -> float:
@@ -258,6 +264,17 @@ class Compressor:
         Xc = X.t().contiguous()              # column-major n x nrhs
         Yc = t.empty_like(Xc)
         hm_apply(self.ctx, Xc.data_ptr(), Yc.data_ptr(), X.shape[1], trans)
+        Y = Yc.t()
+        return Y[:, 0] if vec else Y
+
+    def apply_noalloc(self, x, trans: int = 0):
+        """Like apply(), through hm_apply_noalloc (no device allocation in the library)."""
+        t = self.torch
+        vec = x.dim() == 1
+        X = x.reshape(x.shape[0], -1).to(dtype=t.float64)
+        Xc = X.t().contiguous()
+        Yc = t.empty_like(Xc)
+        hm_apply_noalloc(self.ctx, Xc.data_ptr(), Yc.data_ptr(), X.shape[1], trans)
         Y = Yc.t()
         return Y[:, 0] if vec else Y
 

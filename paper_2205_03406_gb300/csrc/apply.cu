@@ -7,7 +7,7 @@
 //  stage 2: one CTA per leaf owns its rows: y(I_alpha) = sum over levels j of
 //           U_q(rows of alpha) t_q for the pairs q of alpha's level-j ancestor,
 //           plus the neighbour blocks.  No atomics; deterministic.
-#include "ctx.cuh"
+#include "apply_kernels.cuh"
 
 #include <algorithm>
 
@@ -60,15 +60,6 @@ __global__ void k_apply_stage1(const int *pair_alpha, const int *pair_col, const
         tq[toff[q] + o] = acc;
     }
 }
-
-struct ApplyLevel {
-    const int *pt2ent, *ent, *int_ptr, *int_idx, *pairT;
-    const int *kU, *kV;
-    const int64_t *offU, *offV;
-    const double *U, *V;
-    const int64_t *toff;
-    const double *tq;
-};
 
 __global__ void k_apply_stage2(const int *ent_leaf, int nleaf, const ApplyLevel *lv, int nlev, const int *near_ptr,
                                const int *near_idx, const int *leaf_pairT, const int64_t *offD, const double *D,
