@@ -35,10 +35,12 @@ sys.path.insert(0, ROOT)
 METRIC = "time-to-compress (s) and jobs/s at stated rel. error; p50/p99 latency"
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
 
-# dram bytes (read + write) per launch of the tensor-core contraction kernel,
-# from the ncu capture summarised in profiles/k_sample_tc_torus.md, valid for
-# the source whose sha256 prefix is recorded beside it
-TRAFFIC = {"file": "paper_2205_03406_gb300/csrc/sample_tc.cu", "sha256": None, "bytes_per_row": None}
+# dram bytes (read + write) of the tensor-core contraction kernel per output
+# element, from the ncu capture summarised in profiles/k_sample_tc_torus50k.md
+# (scaled by the outputs of a step: the traffic is the FP64 outputs written once
+# plus the L2-resident packed chunks); valid only for the source whose sha256
+# prefix is recorded here
+TRAFFIC = {"file": "paper_2205_03406_gb300/csrc/sample_tc.cu", "sha256": "07ae0e57438406aa", "bytes_per_output": 7.92}
 
 
 def parse():
@@ -148,9 +150,9 @@ def roofline_tc(info, r: int):
     try:
         src_path = os.path.join(ROOT, TRAFFIC["file"])
         sha = hashlib.sha256(open(src_path, "rb").read()).hexdigest()[:16]
-        if TRAFFIC["sha256"] == sha and TRAFFIC["bytes_per_row"]:
-            rows = sum(info.act_rows[l] for l in range(2, info.L + 1))
-            traffic = TRAFFIC["bytes_per_row"] * rows
+        if TRAFFIC["sha256"] == sha and TRAFFIC["bytes_per_output"]:
+            outputs = sum(2.0 * info.n * r * info.colors[l] for l in range(2, info.L + 1))
+            traffic = round(TRAFFIC["bytes_per_output"] * outputs)
     except OSError:
         pass
     return {"kernel": "k_sample_tc (split-BF16 kernel-matrix x Omega contraction)", "bound": "tensor",
