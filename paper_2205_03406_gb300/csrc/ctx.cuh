@@ -67,6 +67,7 @@ struct Factors {
     DBuf kU, kV;              // int32
     DBuf offU, offV, offB;    // int64 element offsets
     DBuf U, V, B;
+    DBuf U32, V32, B32;       // FP32 copies for the mixed-precision peel (made on first use)
     int64_t nU = 0, nV = 0, nB = 0;
     int max_k = 0;
 };
@@ -140,8 +141,9 @@ Err op_apply_dense_vectors(hm_ctx *c, const hm_op *op, const double *x_sorted, d
 Err sample_tc(hm_ctx *c, int level, int kernel);
 Err sample_leaf_mixed(hm_ctx *c, int kernel);
 bool tc_supported(const hm_ctx *c);
-// peel.cu
+// peel.cu, peel_mixed.cu
 Err peel_level(hm_ctx *c, int level, bool leaf);
+Err peel_level_mixed(hm_ctx *c, int level, bool leaf);
 // basis.cu
 Err bases_and_cores(hm_ctx *c, int level);
 Err extract_leaf(hm_ctx *c);

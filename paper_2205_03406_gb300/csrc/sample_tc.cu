@@ -176,15 +176,6 @@ __host__ __device__ constexpr double kscale(int kind) {
     return kind == HM_K_LAPLACE3D ? 0.079577471545947667884 : (kind == HM_K_LOG ? 0.34657359027997265471 : 1.0);
 }
 
-// split v into three BF16 pieces (h + m + l = v to 24 bits)
-__device__ __forceinline__ void split3(float v, __nv_bfloat16 &h, __nv_bfloat16 &m, __nv_bfloat16 &l) {
-    h = __float2bfloat16_rn(v);
-    const float r1 = v - __bfloat162float(h);
-    m = __float2bfloat16_rn(r1);
-    const float r2 = r1 - __bfloat162float(m);
-    l = __float2bfloat16_rn(r2);
-}
-
 struct Params {
     const float4 *xdf;         // sorted points, double-float: [n][2] = (hi xyz, lo xyz)
     int64_t n;
@@ -196,10 +187,32 @@ struct Params {
     int *status;
 };
 
+constexpr int SEG = 2;      // chunks accumulated in tensor memory before promotion
+constexpr int MAXR = 40;    // largest r (columns per thread in the promotion: r)
+
+// exact FP32 -> FP64 with integer operations (normal numbers; zero and
+// subnormals map to a signed zero), keeping the conversion off the FP64 pipe
+__device__ __forceinline__ double f2d(float f) {
+    const uint32_t u = __float_as_uint(f);
+    const uint32_t e = (u >> 23) & 0xFFu;
+    const uint64_t sgn = (uint64_t)(u & 0x80000000u) << 32;
+    if (e == 0) return __longlong_as_double((long long)sgn);
+    return __longlong_as_double((long long)(sgn | ((uint64_t)(e + 896u) << 52) | ((uint64_t)(u & 0x7FFFFFu) << 29)));
+}
+
+// hi + lo += v, error-free (Knuth two-sum on the high part)
+__device__ __forceinline__ void dfadd(float &hi, float &lo, float v) {
+    const float s = hi + v;
+    const float bb = s - hi;
+    const float err = (hi - (s - bb)) + (v - bb);
+    hi = s;
+    lo += err;
+}
+
 template <int KIND>
 __global__ void __launch_bounds__(NTHREADS, 1) k_sample_tc(Params P) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    __shared__ uint64_t full_a[2], full_b[2], empty[2], accum;
+    __shared__ uint64_t full_a[2], full_b[2], empty[2], seg_done[2], set_free[2], accum;
     __shared__ uint32_t tmem_slot;
     unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const int r = P.r;
@@ -210,6 +223,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_sample_tc(Params P) {
     const int64_t i0 = (int64_t)blockIdx.x * TM;
     const int64_t nrows = P.rows_ptr[c + 1] - P.rows_ptr[c];
     const int nchunks = (int)((nrows + KC - 1) / KC);
+    const int nseg = (nchunks + SEG - 1) / SEG;
     const unsigned char *gpack = P.pack + (size_t)P.chunk_off[c] * CB;
     volatile int *status = P.status;
 
@@ -218,6 +232,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_sample_tc(Params P) {
             mbar_init(&full_a[s], NPROD);
             mbar_init(&full_b[s], 1);
             mbar_init(&empty[s], 1);
+            mbar_init(&seg_done[s], 1);
+            mbar_init(&set_free[s], NPROD);
         }
         mbar_init(&accum, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -251,6 +267,40 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_sample_tc(Params P) {
             rx[u][0] = h.x; rx[u][1] = h.y; rx[u][2] = h.z;
             rx[u][3] = l.x; rx[u][4] = l.y; rx[u][5] = l.z;
         }
+        // promotion: this thread owns TMEM lane quarter (warp & 3), columns
+        // [side r, side r + r) of the 2r outputs (side 0: Y, side 1: Z)
+        const int quarter = warp & 3, side = warp >> 2;
+        const uint32_t trow = tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(side * r);
+        const float scale = (float)kscale(KIND);
+        float acc_hi[MAXR], acc_lo[MAXR];
+#pragma unroll
+        for (int k = 0; k < MAXR; ++k) acc_hi[k] = acc_lo[k] = 0.0f;
+        int promoted = 0;
+        auto promote = [&](int sg) -> bool {
+            const int set = sg & 1;
+            // tcgen05.ld is warp-collective: the whole warp goes on or stops together
+            const bool done = mbar_wait(&seg_done[set], (uint32_t)(sg >> 1) & 1, status, false);
+            if (!__all_sync(0xffffffffu, done)) return false;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t base = trow + (uint32_t)(set * 6 * r);
+#pragma unroll
+            for (int g = 0; g < MAXR / 8; ++g) {
+                if (8 * g >= r) break;
+                float hh[8], x1[8], x2[8];
+                tmem_ld8(base + 8 * g, hh);
+                tmem_ld8(base + 2 * r + 8 * g, x1);
+                tmem_ld8(base + 4 * r + 8 * g, x2);
+                tmem_wait_ld();
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    dfadd(acc_hi[8 * g + k], acc_lo[8 * g + k], hh[k] * scale);
+                    acc_lo[8 * g + k] += (x1[k] + x2[k]) * scale;
+                }
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            mbar_arrive(&set_free[set]);
+            return true;
+        };
         int b_issued = 0, b_waited = 0;  // thread 0: bulk copies issued / consumed
         if (tid == 0 && nchunks > 0) {
             mbar_expect_tx(&full_b[0], CB);
@@ -271,6 +321,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_sample_tc(Params P) {
             }
             if (q >= 2 && ok) ok = mbar_wait(&empty[s], (u - 1) & 1, status);
             if (ok) ok = mbar_wait(&full_b[s], u & 1, status);
+            ok = __all_sync(0xffffffffu, ok);
             if (!ok) break;
             b_waited = q + 1;
             unsigned char *st = smem + s * SB;
@@ -292,83 +343,85 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_sample_tc(Params P) {
             for (int uu = 0; uu < 4; ++uu) {
                 const int m = mrow[uu];
                 const int off = (m >> 3) * 1024 + (m & 7) * 128 + ((ck ^ (m & 7)) << 4);
-                __align__(16) __nv_bfloat16 ph[8], pm[8], pl[8];
+                uint32_t ph[4], pm[4], pl[4];
 #pragma unroll
-                for (int e = 0; e < 8; ++e) split3(kv[uu][e], ph[e], pm[e], pl[e]);
-                *reinterpret_cast<uint4 *>(st + off) = *reinterpret_cast<const uint4 *>(ph);
-                *reinterpret_cast<uint4 *>(st + A_PIECE + off) = *reinterpret_cast<const uint4 *>(pm);
-                *reinterpret_cast<uint4 *>(st + 2 * A_PIECE + off) = *reinterpret_cast<const uint4 *>(pl);
+                for (int e2 = 0; e2 < 4; ++e2) {
+                    const float v0 = kv[uu][2 * e2], v1 = kv[uu][2 * e2 + 1];
+                    const __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
+                    const float2 hf = __bfloat1622float2(h);
+                    const float r0 = v0 - hf.x, r1 = v1 - hf.y;
+                    const __nv_bfloat162 mm = __floats2bfloat162_rn(r0, r1);
+                    const float2 mf = __bfloat1622float2(mm);
+                    const __nv_bfloat162 ll = __floats2bfloat162_rn(r0 - mf.x, r1 - mf.y);
+                    ph[e2] = *reinterpret_cast<const uint32_t *>(&h);
+                    pm[e2] = *reinterpret_cast<const uint32_t *>(&mm);
+                    pl[e2] = *reinterpret_cast<const uint32_t *>(&ll);
+                }
+                *reinterpret_cast<uint4 *>(st + off) = make_uint4(ph[0], ph[1], ph[2], ph[3]);
+                *reinterpret_cast<uint4 *>(st + A_PIECE + off) = make_uint4(pm[0], pm[1], pm[2], pm[3]);
+                *reinterpret_cast<uint4 *>(st + 2 * A_PIECE + off) = make_uint4(pl[0], pl[1], pl[2], pl[3]);
             }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             mbar_arrive(&full_a[s]);
+            // promote the previous segment once the next one has started
+            if (q % SEG == 0 && q > 0) {
+                ok = promote(promoted);
+                ++promoted;
+            }
         }
         // never leave a bulk copy in flight: wait for the ones not consumed
         if (tid == 0)
             for (int k = b_waited; k < b_issued; ++k) mbar_wait(&full_b[k & 1], (uint32_t)(k >> 1) & 1, status, false);
+        if (ok)
+            while (promoted < nseg && ok) {
+                ok = promote(promoted);
+                ++promoted;
+            }
+        // epilogue: row 32 quarter + lane, columns [side r, side r + r)
+        const int64_t i = i0 + 32 * quarter + lane;
+        if (ok && *status == 0 && i < P.n) {
+            double *dst = (side ? P.Z : P.Y) + ((int64_t)c * P.n + i) * r;
+#pragma unroll
+            for (int k = 0; k < MAXR; k += 2) {
+                if (k >= r) break;
+                *reinterpret_cast<double2 *>(dst + k) =
+                    make_double2(f2d(acc_hi[k]) + f2d(acc_lo[k]), f2d(acc_hi[k + 1]) + f2d(acc_lo[k + 1]));
+            }
+        }
     } else if (lane == 0) {
         // ------------------------------------------------------------ MMA issuer
         const uint32_t id1 = idesc_bf16(6 * r), id2 = idesc_bf16(4 * r), id3 = idesc_bf16(2 * r);
-        int issued = 0;
         for (int q = 0; q < nchunks && ok; ++q) {
             const int s = q & 1;
             const uint32_t u = (uint32_t)(q >> 1);
-            ok = mbar_wait(&full_a[s], u & 1, status) && mbar_wait(&full_b[s], u & 1, status);
+            const int sg = q / SEG, set = sg & 1;
+            const bool first = (q % SEG) == 0;
+            // the accumulator set is free once the producers promoted segment sg - 2
+            if (first && sg >= 2) ok = mbar_wait(&set_free[set], (uint32_t)((sg >> 1) - 1) & 1, status);
+            if (ok) ok = mbar_wait(&full_a[s], u & 1, status) && mbar_wait(&full_b[s], u & 1, status);
             if (!ok) break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint32_t sa = smem_u32(smem + s * SB);
             const uint64_t ah = sw128_desc(sa), am = sw128_desc(sa + A_PIECE), al = sw128_desc(sa + 2 * A_PIECE);
             const uint64_t bd = sw128_desc(sa + 3 * A_PIECE);
+            const uint32_t d = tmem + (uint32_t)(set * 6 * r);
 #pragma unroll
             for (int kk = 0; kk < 4; ++kk) {
-                const uint32_t acc = (q > 0 || kk > 0) ? 1u : 0u;
                 const uint64_t adv = (uint64_t)(kk * 2);  // 32 bytes per K step, in 16-byte units
-                mma_bf16(tmem + 0, ah + adv, bd + adv, id1, acc);
-                mma_bf16(tmem + 6 * r, am + adv, bd + adv, id2, acc);
-                mma_bf16(tmem + 10 * r, al + adv, bd + adv, id3, acc);
+                // A_h x [B_h B_m B_l] -> hh | hm | hl ; A_m x [B_h B_m] adds mh, mm onto hm, hl ;
+                // A_l x B_h adds lh onto hl.  The first product of a segment starts the set.
+                mma_bf16(d, ah + adv, bd + adv, id1, (first && kk == 0) ? 0u : 1u);
+                mma_bf16(d + 2 * r, am + adv, bd + adv, id2, 1u);
+                mma_bf16(d + 4 * r, al + adv, bd + adv, id3, 1u);
             }
             mma_commit(&empty[s]);
-            issued = q + 1;
+            if ((q % SEG) == SEG - 1 || q == nchunks - 1) mma_commit(&seg_done[set]);
         }
-        if (issued > 0) mma_commit(&accum);
-        else mbar_arrive(&accum);
+        // every MMA of this CTA has completed before tensor memory is freed
+        mma_commit(&accum);
+        mbar_wait(&accum, 0, status, false);
     }
     __syncwarp();
-
-    // ---------------------------------------------------------------- epilogue
-    if (warp < 8) {
-        // the MMAs of this CTA must have finished before tensor memory is read or freed
-        const bool good = mbar_wait(&accum, 0, status, false) && *status == 0;
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const int quarter = warp & 3, side = warp >> 2;
-        const int m = 32 * quarter + lane;
-        const int64_t i = i0 + m;
-        const uint32_t trow = tmem + ((uint32_t)(32 * quarter) << 16);
-        double *out = side ? P.Z : P.Y;
-        const float scale = (float)kscale(KIND);
-        for (int h = 0; h < r / 8; ++h) {  // 8 output columns per step
-            const int n = side * r + 8 * h;
-            float hh[8], hm[8], hl[8], mh[8], mm[8], lh[8];
-            tmem_ld8(trow + n, hh);
-            tmem_ld8(trow + 2 * r + n, hm);
-            tmem_ld8(trow + 4 * r + n, hl);
-            tmem_ld8(trow + 6 * r + n, mh);
-            tmem_ld8(trow + 8 * r + n, mm);
-            tmem_ld8(trow + 10 * r + n, lh);
-            tmem_wait_ld();
-            if (good && i < P.n) {
-                double *dst = out + ((int64_t)c * P.n + i) * r + 8 * h;
-#pragma unroll
-                for (int k = 0; k < 8; k += 2) {
-                    float a0 = 0.f, a1 = 0.f;
-                    if (nchunks > 0) {
-                        a0 = (((hl[k] + mm[k]) + lh[k]) + (hm[k] + mh[k]) + hh[k]) * scale;
-                        a1 = (((hl[k + 1] + mm[k + 1]) + lh[k + 1]) + (hm[k + 1] + mh[k + 1]) + hh[k + 1]) * scale;
-                    }
-                    *reinterpret_cast<double2 *>(dst + k) = make_double2((double)a0, (double)a1);
-                }
-            }
-        }
-    }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 8) {
