@@ -57,6 +57,8 @@ __global__ void __launch_bounds__(256) k_core_M(const int *tile_alpha, const int
     }
 }
 
+constexpr int QR_WARP_ROWS_DECL = 256;
+
 // Column-pivoted Householder QR of one tile (m x r, row-major), in place;
 // on exit the first k columns hold Q_k with R_jj >= 0.
 __global__ void __launch_bounds__(256) k_qr_tiles(const int *tile_alpha, const int *tile_beta, const int *tile_color,
@@ -69,6 +71,7 @@ __global__ void __launch_bounds__(256) k_qr_tiles(const int *tile_alpha, const i
     const int64_t p = blockIdx.x;
     const int *e = ent + (int64_t)tile_alpha[p] * ENT_FIELDS;
     const int m = e[4] - e[3];
+    if (m <= QR_WARP_ROWS_DECL) return;  // the warp kernel factors this tile
     double *A = Ybase + ((int64_t)tile_color[p] * n + e[3]) * r;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int *eb = ent + (int64_t)tile_beta[p] * ENT_FIELDS;
@@ -201,6 +204,110 @@ __global__ void __launch_bounds__(256) k_qr_tiles(const int *tile_alpha, const i
     if (threadIdx.x == 0) kout[p] = k;
 }
 
+// The same pivoted QR for tiles of at most QR_WARP_ROWS rows: one warp per
+// tile, lane j owns columns j and j + 32; for a fixed row the lanes touch
+// consecutive columns (coalesced), and the Householder vector's entry is a
+// broadcast load.  No block barriers.
+constexpr int QR_WARP_ROWS = QR_WARP_ROWS_DECL;
+
+__global__ void __launch_bounds__(128) k_qr_warp(const int *tile_alpha, const int *tile_beta, const int *tile_color,
+                                                 const int *ent, int64_t n, int r, int cap, int rank, double tol,
+                                                 double *Ybase, int *kout, int64_t ntiles) {
+    __shared__ double s_tau[4][64], s_beta[4][64];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t p = (int64_t)blockIdx.x * 4 + warp;
+    if (p >= ntiles) return;
+    const int *e = ent + (int64_t)tile_alpha[p] * ENT_FIELDS;
+    const int m = e[4] - e[3];
+    if (m > QR_WARP_ROWS) return;  // the block kernel factors this tile
+    double *A = Ybase + ((int64_t)tile_color[p] * n + e[3]) * r;
+    const int *eb = ent + (int64_t)tile_beta[p] * ENT_FIELDS;
+    const int kmax = min(min(m, eb[4] - eb[3]), min(r, cap));
+    double *tau = s_tau[warp], *beta = s_beta[warp];
+    const int c0 = lane, c1 = lane + 32;
+    double n0 = 0.0;
+    int k = 0;
+    for (int s = 0; s < kmax; ++s) {
+        double a0 = 0.0, a1 = 0.0;
+        for (int i = s; i < m; ++i) {
+            if (c0 < r) a0 = fma(A[(int64_t)i * r + c0], A[(int64_t)i * r + c0], a0);
+            if (c1 < r) a1 = fma(A[(int64_t)i * r + c1], A[(int64_t)i * r + c1], a1);
+        }
+        double best = -1.0;
+        int bj = 1 << 30;
+        if (c0 < r && c0 >= s) { best = a0; bj = c0; }
+        if (c1 < r && c1 >= s && (a1 > best || bj == (1 << 30))) { best = a1; bj = c1; }
+        for (int o = 16; o > 0; o >>= 1) {  // largest norm, lowest column on ties
+            const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+            const int oj = __shfl_xor_sync(0xffffffffu, bj, o);
+            if (ob > best || (ob == best && oj < bj)) { best = ob; bj = oj; }
+        }
+        const double nv = sqrt(best);
+        if (s == 0) n0 = nv;
+        const bool stop = rank > 0 ? (s >= rank) : (!(n0 > 0.0) || !(nv > tol * n0));
+        if (stop) break;
+        const int piv = bj;
+        if (piv != s)
+            for (int i = lane; i < m; i += 32) {
+                const double t = A[(int64_t)i * r + s];
+                A[(int64_t)i * r + s] = A[(int64_t)i * r + piv];
+                A[(int64_t)i * r + piv] = t;
+            }
+        __syncwarp();
+        const double x0 = A[(int64_t)s * r + s];
+        double t = 0.0, b = 0.0, sc = 0.0;
+        if (nv > 0.0) {
+            b = -copysign(nv, x0);
+            t = (b - x0) / b;
+            sc = 1.0 / (x0 - b);
+        }
+        for (int i = s + 1 + lane; i < m; i += 32) A[(int64_t)i * r + s] *= sc;
+        __syncwarp();
+        if (lane == 0) {
+            tau[s] = t;
+            beta[s] = b;
+            if (nv > 0.0) A[(int64_t)s * r + s] = b;
+        }
+        for (int h = 0; h < 2; ++h) {
+            const int j = h ? c1 : c0;
+            if (j <= s || j >= r) continue;
+            double w = A[(int64_t)s * r + j];
+            for (int i = s + 1; i < m; ++i) w = fma(A[(int64_t)i * r + s], A[(int64_t)i * r + j], w);
+            A[(int64_t)s * r + j] -= t * w;
+            for (int i = s + 1; i < m; ++i) A[(int64_t)i * r + j] -= t * A[(int64_t)i * r + s] * w;
+        }
+        __syncwarp();
+        k = s + 1;
+    }
+    // explicit Q_k, backward accumulation of the reflectors
+    for (int j = k - 1; j >= 0; --j) {
+        const double tj = tau[j];
+        for (int h = 0; h < 2; ++h) {
+            const int c = h ? c1 : c0;
+            if (c <= j || c >= k) continue;
+            double w = A[(int64_t)j * r + c];
+            for (int i = j + 1; i < m; ++i) w = fma(A[(int64_t)i * r + j], A[(int64_t)i * r + c], w);
+            A[(int64_t)j * r + c] -= tj * w;
+            for (int i = j + 1; i < m; ++i) A[(int64_t)i * r + c] -= tj * A[(int64_t)i * r + j] * w;
+        }
+        __syncwarp();
+        for (int i = lane; i < m; i += 32) {
+            double v;
+            if (i < j) v = 0.0;
+            else if (i == j) v = 1.0 - tj;
+            else v = -tj * A[(int64_t)i * r + j];
+            A[(int64_t)i * r + j] = v;
+        }
+        __syncwarp();
+    }
+    for (int h = 0; h < 2; ++h) {  // R_jj >= 0
+        const int c = h ? c1 : c0;
+        if (c < k && beta[c] < 0.0)
+            for (int i = 0; i < m; ++i) A[(int64_t)i * r + c] = -A[(int64_t)i * r + c];
+    }
+    if (lane == 0) kout[p] = k;
+}
+
 __global__ void k_factor_sizes(const int *pair_alpha, const int *pair_col, const int *pairT, const int *kY,
                                const int *kZ, const int *ent, int64_t np, int *kU, int *kV, int64_t *sU, int64_t *sV,
                                int64_t *sB) {
@@ -288,55 +395,60 @@ __device__ void warp_back_solve(const double *A, int k, int lda, double *X, int 
     __syncwarp();
 }
 
-// one warp per pair: B = (GP_a^T U)^+ M (GO_b^T V)^{+T}
-__global__ void __launch_bounds__(32) k_core(const int *pair_alpha, const int *pair_col, const int *ent, int r,
-                                             const int *kU, const int *kV, const int64_t *offU, const int64_t *offV,
-                                             const int64_t *offB, const double *U, const double *V, const double *GO,
-                                             const double *GP, const double *M, double *B) {
+// one warp per pair, four pairs per CTA: B = (GP_a^T U)^+ M (GO_b^T V)^{+T};
+// M (r x r, FP64) is worked on in place in its scratch; S1, S2 and X^T live in
+// shared memory with leading dimension kc (the largest k)
+constexpr int CORE_WARPS = 4;
+
+__global__ void __launch_bounds__(128) k_core(const int *pair_alpha, const int *pair_col, const int *ent,
+                                                          int r, int kc, int64_t np, const int *kU, const int *kV,
+                                                          const int64_t *offU, const int64_t *offV,
+                                                          const int64_t *offB, const double *U, const double *V,
+                                                          const double *GO, const double *GP, double *M, double *B) {
     extern __shared__ double sm[];
-    const int64_t p = blockIdx.x;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+    const int64_t p = (int64_t)blockIdx.x * nwarps + warp;
+    if (p >= np) return;
     const int ku = kU[p], kv = kV[p];
     if (ku == 0 || kv == 0) return;
-    const int lane = threadIdx.x;
-    double *S1 = sm;              // r x ku  (ld r)
-    double *S2 = S1 + r * r;      // r x kv
-    double *Mx = S2 + r * r;      // r x r, then X^T
-    double *X = Mx + r * r;       // ku x r, then Bt
-    double *tau = X + r * r;      // r
+    double *S1 = sm + (size_t)warp * (3 * r * kc + r);  // r x ku  (ld kc)
+    double *S2 = S1 + r * kc;                            // r x kv
+    double *X = S2 + r * kc;                             // r x ku: X^T
+    double *tau = X + r * kc;                            // r
+    double *Mx = M + p * r * r;                          // r x r (ld r), in place
     const int *ea = ent + (int64_t)pair_alpha[p] * ENT_FIELDS, *eb = ent + (int64_t)pair_col[p] * ENT_FIELDS;
     const int sa = ea[3], ma = ea[4] - ea[3], sb = eb[3], mb = eb[4] - eb[3];
     const double *Up = U + offU[p], *Vp = V + offV[p];
     for (int o = lane; o < r * ku; o += 32) {
         const int a = o / ku, u = o % ku;
-        double s = 0.0;
-        for (int i = 0; i < ma; ++i) s = fma(GP[(int64_t)(sa + i) * r + a], Up[(int64_t)i * ku + u], s);
-        S1[a * r + u] = s;
+        double sacc = 0.0;
+        for (int i = 0; i < ma; ++i) sacc = fma(GP[(int64_t)(sa + i) * r + a], Up[(int64_t)i * ku + u], sacc);
+        S1[a * kc + u] = sacc;
     }
     for (int o = lane; o < r * kv; o += 32) {
         const int a = o / kv, v = o % kv;
-        double s = 0.0;
-        for (int i = 0; i < mb; ++i) s = fma(GO[(int64_t)(sb + i) * r + a], Vp[(int64_t)i * kv + v], s);
-        S2[a * r + v] = s;
+        double sacc = 0.0;
+        for (int i = 0; i < mb; ++i) sacc = fma(GO[(int64_t)(sb + i) * r + a], Vp[(int64_t)i * kv + v], sacc);
+        S2[a * kc + v] = sacc;
     }
-    for (int o = lane; o < r * r; o += 32) Mx[o] = M[p * r * r + o];
     __syncwarp();
     // X = R1^{-1} (Q1^T M)(0:ku, :)
-    warp_house_qr(S1, r, ku, r, tau);
-    warp_apply_qt(S1, r, ku, r, tau, Mx, r, r);
-    warp_back_solve(S1, ku, r, Mx, r, r);
-    // Bt = R2^{-1} (Q2^T X^T)(0:kv, :) with X^T (r x ku) stored in X
+    warp_house_qr(S1, r, ku, kc, tau);
+    warp_apply_qt(S1, r, ku, kc, tau, Mx, r, r);
+    warp_back_solve(S1, ku, kc, Mx, r, r);
+    // B^T = R2^{-1} (Q2^T X^T)(0:kv, :)
     for (int o = lane; o < r * ku; o += 32) {
         const int a = o / ku, u = o % ku;
-        X[a * r + u] = Mx[u * r + a];
+        X[a * kc + u] = Mx[u * r + a];
     }
     __syncwarp();
-    warp_house_qr(S2, r, kv, r, tau);
-    warp_apply_qt(S2, r, kv, r, tau, X, ku, r);
-    warp_back_solve(S2, kv, r, X, ku, r);
+    warp_house_qr(S2, r, kv, kc, tau);
+    warp_apply_qt(S2, r, kv, kc, tau, X, ku, kc);
+    warp_back_solve(S2, kv, kc, X, ku, kc);
     double *Bp = B + offB[p];
     for (int o = lane; o < ku * kv; o += 32) {
         const int u = o / kv, v = o % kv;
-        Bp[o] = X[v * r + u];
+        Bp[o] = X[v * kc + u];
     }
 }
 
@@ -368,9 +480,15 @@ Err bases_and_cores(hm_ctx *c, int level) {
     k_qr_tiles<<<(int)np, 256, 0, st>>>(g.pair_alpha.as<int>(), cu.int_idx.as<int>(), g.pair_color.as<int>(),
                                         cu.ent.as<int>(), n, r, cap, c->cfg.rank, c->cfg.tol, c->cur.Y.as<double>(),
                                         kY.as<int>()); ::hm::count_launch();
+    k_qr_warp<<<ceil_div(np, 4), 128, 0, st>>>(g.pair_alpha.as<int>(), cu.int_idx.as<int>(), g.pair_color.as<int>(),
+                                               cu.ent.as<int>(), n, r, cap, c->cfg.rank, c->cfg.tol,
+                                               c->cur.Y.as<double>(), kY.as<int>(), np); ::hm::count_launch();
     k_qr_tiles<<<(int)np, 256, 0, st>>>(g.pair_alpha.as<int>(), cu.int_idx.as<int>(), g.pair_color.as<int>(),
                                         cu.ent.as<int>(), n, r, cap, c->cfg.rank, c->cfg.tol, c->cur.Z.as<double>(),
                                         kZ.as<int>()); ::hm::count_launch();
+    k_qr_warp<<<ceil_div(np, 4), 128, 0, st>>>(g.pair_alpha.as<int>(), cu.int_idx.as<int>(), g.pair_color.as<int>(),
+                                               cu.ent.as<int>(), n, r, cap, c->cfg.rank, c->cfg.tol,
+                                               c->cur.Z.as<double>(), kZ.as<int>(), np); ::hm::count_launch();
     HM_LAUNCH("qr_tiles");
     HM_TRY(alloc(f.kU, np * sizeof(int)));
     HM_TRY(alloc(f.kV, np * sizeof(int)));
@@ -398,12 +516,16 @@ Err bases_and_cores(hm_ctx *c, int level) {
                                     f.offU.as<int64_t>(), f.offV.as<int64_t>(), c->cur.Y.as<double>(),
                                     c->cur.Z.as<double>(), f.U.as<double>(), f.V.as<double>()); ::hm::count_launch();
     HM_LAUNCH("pack");
-    const size_t smem = (4 * (size_t)r * r + r) * sizeof(double);
+    const int kc = std::max(1, c->cfg.rank > 0 ? std::min(r, c->cfg.rank) : std::min(r, cap));
+    const size_t per_warp = (3 * (size_t)r * kc + r) * sizeof(double);
+    const int core_warps = (int)std::min<size_t>(CORE_WARPS, (200 * 1024) / per_warp);
+    if (core_warps < 1) return fail(HM_ENOTSUP, "cores: r x k too large for shared memory");
+    const size_t smem = (size_t)core_warps * per_warp;
     HM_CUDA(cudaFuncSetAttribute(k_core, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_core<<<(int)np, 32, smem, st>>>(g.pair_alpha.as<int>(), cu.int_idx.as<int>(), cu.ent.as<int>(), r,
-                                      f.kU.as<int>(), f.kV.as<int>(), f.offU.as<int64_t>(), f.offV.as<int64_t>(),
-                                      f.offB.as<int64_t>(), f.U.as<double>(), f.V.as<double>(), c->GO.as<double>(),
-                                      c->GP.as<double>(), c->scratch_a.as<double>(), f.B.as<double>()); ::hm::count_launch();
+    k_core<<<ceil_div(np, core_warps), core_warps * 32, smem, st>>>(
+        g.pair_alpha.as<int>(), cu.int_idx.as<int>(), cu.ent.as<int>(), r, kc, np, f.kU.as<int>(), f.kV.as<int>(),
+        f.offU.as<int64_t>(), f.offV.as<int64_t>(), f.offB.as<int64_t>(), f.U.as<double>(), f.V.as<double>(),
+        c->GO.as<double>(), c->GP.as<double>(), c->scratch_a.as<double>(), f.B.as<double>()); ::hm::count_launch();
     HM_LAUNCH("core");
     std::vector<int> hk;
     HM_TRY(to_host(hk, f.kU.p, np, st));

@@ -174,73 +174,103 @@ __device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v)
 }
 
 // One CTA of 1024 threads; exactly nv steps, no waits on other blocks.
+// Per step: (1) every warp reduces the 1024 bucket maxima, so the chosen
+// vertex v is known after one barrier; (2) in parallel, warp 0 finds v's
+// smallest free colour, every thread fetches its share of v's neighbours
+// together with their keys and first four forbidden-colour words (colours
+// < 128), and warp 1 re-scans v's bucket without v; (3) neighbours take the
+// colour into their forbidden sets and raise their saturation.
+constexpr int DS_PREFETCH = 2;  // neighbours fetched ahead per thread
+
 __global__ void __launch_bounds__(1024) k_dsatur(int64_t nv, const int64_t *adj_ptr, const int *adj,
                                                  unsigned long long *key, unsigned int *forb, int *color,
                                                  int *status /* [0] = colours, [1] = error */) {
     __shared__ unsigned long long bmax[DS_BUCKETS];
     __shared__ unsigned long long red[32];
-    __shared__ int sel_v, sel_c, ncol;
+    __shared__ int sel_c, ncol;
     const int t = threadIdx.x, lane = t & 31, w = t >> 5;
-    unsigned long long m = 0;
-    for (int64_t v = t; v < nv; v += DS_BUCKETS) m = key[v] > m ? key[v] : m;
-    bmax[t] = m;
+    unsigned long long m0 = 0;
+    for (int64_t v = t; v < nv; v += DS_BUCKETS) m0 = key[v] > m0 ? key[v] : m0;
+    bmax[t] = m0;
     if (t == 0) ncol = 0;
     __syncthreads();
     for (int64_t step = 0; step < nv; ++step) {
         unsigned long long k = warp_max_u64(bmax[t]);
         if (lane == 0) red[w] = k;
         __syncthreads();
-        if (w == 0) {
-            k = warp_max_u64(red[lane]);
-            const int v = (int)(VID_MASK - (k & VID_MASK));
-            // smallest colour not forbidden for v
-            const unsigned int word = forb[(int64_t)v * FORB_WORDS + lane];
-            const unsigned int freebits = ~word;
-            const unsigned int has = __ballot_sync(0xffffffffu, freebits != 0u);
-            if (lane == 0) {
-                sel_v = v;
-                sel_c = -1;
+        k = warp_max_u64(red[lane]);
+        const int v = (int)(VID_MASK - (k & VID_MASK));
+        const int b = v & (DS_BUCKETS - 1);
+        const int64_t e0 = adj_ptr[v], e1 = adj_ptr[v + 1];
+        // neighbours, their keys and forbidden words 0..3, fetched before the colour is known
+        int nu[DS_PREFETCH];
+        unsigned long long nk[DS_PREFETCH];
+        uint4 nf[DS_PREFETCH];
+#pragma unroll
+        for (int h = 0; h < DS_PREFETCH; ++h) {
+            const int64_t e = e0 + t + (int64_t)h * blockDim.x;
+            nu[h] = -1;
+            if (e < e1) {
+                nu[h] = adj[e];
+                nk[h] = key[nu[h]];
+                nf[h] = *reinterpret_cast<const uint4 *>(&forb[(int64_t)nu[h] * FORB_WORDS]);
             }
+        }
+        if (w == 0) {
+            const unsigned int freebits = ~forb[(int64_t)v * FORB_WORDS + lane];
+            const unsigned int has = __ballot_sync(0xffffffffu, freebits != 0u);
+            if (lane == 0) sel_c = -1;
             __syncwarp();
             if (has) {
                 const int l0 = __ffs(has) - 1;
                 if (lane == l0) sel_c = l0 * 32 + __ffs(freebits) - 1;
             }
+        } else if (w == 1) {
+            unsigned long long mm = 0;
+            for (int64_t x = b + (int64_t)lane * DS_BUCKETS; x < nv; x += 32ll * DS_BUCKETS)
+                if (x != v) mm = key[x] > mm ? key[x] : mm;
+            mm = warp_max_u64(mm);
+            if (lane == 0) bmax[b] = mm;  // v leaves its bucket; raises follow by atomicMax
         }
         __syncthreads();
-        const int v = sel_v, c = sel_c;
+        const int c = sel_c;
         if (c < 0) {
             if (t == 0) status[1] = 1;
             return;  // uniform: every thread reads the same sel_c
         }
+        const int cw = c >> 5;
         const unsigned int bit = 1u << (c & 31);
-        for (int64_t e = adj_ptr[v] + t; e < adj_ptr[v + 1]; e += blockDim.x) {
+#pragma unroll
+        for (int h = 0; h < DS_PREFETCH; ++h) {
+            const int u = nu[h];
+            if (u < 0 || !(nk[h] & UNCOLORED)) continue;
+            unsigned int fw;
+            if (cw < 4) fw = cw == 0 ? nf[h].x : (cw == 1 ? nf[h].y : (cw == 2 ? nf[h].z : nf[h].w));
+            else fw = forb[(int64_t)u * FORB_WORDS + cw];
+            if (!(fw & bit)) {
+                forb[(int64_t)u * FORB_WORDS + cw] = fw | bit;
+                const unsigned long long ku = nk[h] + (1ull << SAT_SHIFT);
+                key[u] = ku;
+                atomicMax(&bmax[u & (DS_BUCKETS - 1)], ku);
+            }
+        }
+        // vertices of very large degree: the rest without prefetch
+        for (int64_t e = e0 + t + (int64_t)DS_PREFETCH * blockDim.x; e < e1; e += blockDim.x) {
             const int u = adj[e];
-            unsigned long long ku = key[u];
-            if (ku & UNCOLORED) {
-                unsigned int *f = &forb[(int64_t)u * FORB_WORDS + (c >> 5)];
-                const unsigned int fw = *f;
-                if (!(fw & bit)) {
-                    *f = fw | bit;
-                    ku += 1ull << SAT_SHIFT;
-                    key[u] = ku;
-                    atomicMax(&bmax[u & (DS_BUCKETS - 1)], ku);
-                }
+            const unsigned long long ku = key[u];
+            if (!(ku & UNCOLORED)) continue;
+            unsigned int *f = &forb[(int64_t)u * FORB_WORDS + cw];
+            const unsigned int fw = *f;
+            if (!(fw & bit)) {
+                *f = fw | bit;
+                key[u] = ku + (1ull << SAT_SHIFT);
+                atomicMax(&bmax[u & (DS_BUCKETS - 1)], ku + (1ull << SAT_SHIFT));
             }
         }
         if (t == 0) {
             key[v] = 0ull;
             color[v] = c;
             if (c + 1 > ncol) ncol = c + 1;
-        }
-        __syncthreads();
-        if (w == 0) {
-            const int b = v & (DS_BUCKETS - 1);
-            unsigned long long mm = 0;
-            for (int64_t x = b + (int64_t)lane * DS_BUCKETS; x < nv; x += 32ll * DS_BUCKETS)
-                mm = key[x] > mm ? key[x] : mm;
-            mm = warp_max_u64(mm);
-            if (lane == 0) bmax[b] = mm;
         }
         __syncthreads();
     }

@@ -36,7 +36,7 @@ namespace tc {
 constexpr int KC = 64;          // rows j per chunk (one 128-byte row of BF16)
 constexpr int TM = 128;         // rows i per tile (MMA M)
 constexpr int NPROD = 256;      // producer threads (8 warps)
-constexpr int NTHREADS = NPROD + 32;
+constexpr int NTHREADS = NPROD + 64;  // + MMA warp (8) + TMA warp (9)
 constexpr int A_PIECE = TM * 128;        // bytes of one A piece (16 KB)
 constexpr int COORD_BYTES = KC * 32;     // 64 entries x 8 floats
 constexpr unsigned long long WAIT_NS = 4000000000ull;  // 4 s per wait
@@ -214,6 +214,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_sample_tc(Params P) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     __shared__ uint64_t full_a[2], full_b[2], empty[2], seg_done[2], set_free[2], accum;
     __shared__ uint32_t tmem_slot;
+    __shared__ __align__(16) float4 cbuf[2][2 * KC];  // double-float coordinates of chunks q, q+1
     unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const int r = P.r;
     const int SB = stage_bytes(r);
@@ -301,77 +302,69 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_sample_tc(Params P) {
             mbar_arrive(&set_free[set]);
             return true;
         };
-        int b_issued = 0, b_waited = 0;  // thread 0: bulk copies issued / consumed
-        if (tid == 0 && nchunks > 0) {
-            mbar_expect_tx(&full_b[0], CB);
-            bulk_g2s(smem + 3 * A_PIECE, gpack, CB, &full_b[0]);
-            b_issued = 1;
-        }
-        for (int q = 0; q < nchunks && ok; ++q) {
+        // coordinates: 2 KB per chunk, 8 bytes per producer thread, prefetched
+        // one chunk ahead into cbuf (producers sync on named barrier 1)
+        const float2 *gcoord = reinterpret_cast<const float2 *>(gpack + b_bytes(r));
+        float2 cnext = make_float2(0.f, 0.f);
+        if (nchunks > 0) reinterpret_cast<float2 *>(cbuf[0])[tid] = gcoord[tid];
+        asm volatile("bar.sync 1, %0;" ::"n"(NPROD) : "memory");
+        // every producer runs every named barrier; after an error it only
+        // skips the work, so no warp can be left waiting at bar.sync
+        for (int q = 0; q < nchunks; ++q) {
             const int s = q & 1;
             const uint32_t u = (uint32_t)(q >> 1);
-            if (tid == 0 && q + 1 < nchunks) {
-                const int s1 = (q + 1) & 1;
-                if (q + 1 >= 2) ok = mbar_wait(&empty[s1], ((uint32_t)((q + 1) >> 1) - 1) & 1, status);
-                if (ok) {
-                    mbar_expect_tx(&full_b[s1], CB);
-                    bulk_g2s(smem + s1 * SB + 3 * A_PIECE, gpack + (size_t)(q + 1) * CB, CB, &full_b[s1]);
-                    b_issued = q + 2;
-                }
-            }
-            if (q >= 2 && ok) ok = mbar_wait(&empty[s], (u - 1) & 1, status);
-            if (ok) ok = mbar_wait(&full_b[s], u & 1, status);
+            if (q + 1 < nchunks) cnext = reinterpret_cast<const float2 *>(gpack + (size_t)(q + 1) * CB + b_bytes(r))[tid];
+            if (ok && q >= 2) ok = mbar_wait(&empty[s], (u - 1) & 1, status);
             ok = __all_sync(0xffffffffu, ok);
-            if (!ok) break;
-            b_waited = q + 1;
-            unsigned char *st = smem + s * SB;
-            const float4 *cd = reinterpret_cast<const float4 *>(st + 3 * A_PIECE + b_bytes(r));
-            float kv[4][8];
+            if (ok) {
+                unsigned char *st = smem + s * SB;
+                const float4 *cd = cbuf[q & 1];
+                float kv[4][8];
 #pragma unroll
-            for (int e = 0; e < 8; ++e) {
-                const float4 ch = cd[(8 * ck + e) * 2], cl = cd[(8 * ck + e) * 2 + 1];
+                for (int e = 0; e < 8; ++e) {
+                    const float4 ch = cd[(8 * ck + e) * 2], cl = cd[(8 * ck + e) * 2 + 1];
+#pragma unroll
+                    for (int uu = 0; uu < 4; ++uu) {
+                        const float dx = (rx[uu][0] - ch.x) + (rx[uu][3] - cl.x);
+                        const float dy = (rx[uu][1] - ch.y) + (rx[uu][4] - cl.y);
+                        const float dz = (rx[uu][2] - ch.z) + (rx[uu][5] - cl.z);
+                        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                        kv[uu][e] = kval<KIND>(r2);
+                    }
+                }
 #pragma unroll
                 for (int uu = 0; uu < 4; ++uu) {
-                    const float dx = (rx[uu][0] - ch.x) + (rx[uu][3] - cl.x);
-                    const float dy = (rx[uu][1] - ch.y) + (rx[uu][4] - cl.y);
-                    const float dz = (rx[uu][2] - ch.z) + (rx[uu][5] - cl.z);
-                    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                    kv[uu][e] = kval<KIND>(r2);
+                    const int m = mrow[uu];
+                    const int off = (m >> 3) * 1024 + (m & 7) * 128 + ((ck ^ (m & 7)) << 4);
+                    uint32_t ph[4], pm[4], pl[4];
+#pragma unroll
+                    for (int e2 = 0; e2 < 4; ++e2) {
+                        const float v0 = kv[uu][2 * e2], v1 = kv[uu][2 * e2 + 1];
+                        const __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
+                        const float2 hf = __bfloat1622float2(h);
+                        const float r0 = v0 - hf.x, r1 = v1 - hf.y;
+                        const __nv_bfloat162 mm = __floats2bfloat162_rn(r0, r1);
+                        const float2 mf = __bfloat1622float2(mm);
+                        const __nv_bfloat162 ll = __floats2bfloat162_rn(r0 - mf.x, r1 - mf.y);
+                        ph[e2] = *reinterpret_cast<const uint32_t *>(&h);
+                        pm[e2] = *reinterpret_cast<const uint32_t *>(&mm);
+                        pl[e2] = *reinterpret_cast<const uint32_t *>(&ll);
+                    }
+                    *reinterpret_cast<uint4 *>(st + off) = make_uint4(ph[0], ph[1], ph[2], ph[3]);
+                    *reinterpret_cast<uint4 *>(st + A_PIECE + off) = make_uint4(pm[0], pm[1], pm[2], pm[3]);
+                    *reinterpret_cast<uint4 *>(st + 2 * A_PIECE + off) = make_uint4(pl[0], pl[1], pl[2], pl[3]);
+                }
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                mbar_arrive(&full_a[s]);
+                // promote the previous segment once the next one has started
+                if (q % SEG == 0 && q > 0) {
+                    ok = promote(promoted);
+                    ++promoted;
                 }
             }
-#pragma unroll
-            for (int uu = 0; uu < 4; ++uu) {
-                const int m = mrow[uu];
-                const int off = (m >> 3) * 1024 + (m & 7) * 128 + ((ck ^ (m & 7)) << 4);
-                uint32_t ph[4], pm[4], pl[4];
-#pragma unroll
-                for (int e2 = 0; e2 < 4; ++e2) {
-                    const float v0 = kv[uu][2 * e2], v1 = kv[uu][2 * e2 + 1];
-                    const __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
-                    const float2 hf = __bfloat1622float2(h);
-                    const float r0 = v0 - hf.x, r1 = v1 - hf.y;
-                    const __nv_bfloat162 mm = __floats2bfloat162_rn(r0, r1);
-                    const float2 mf = __bfloat1622float2(mm);
-                    const __nv_bfloat162 ll = __floats2bfloat162_rn(r0 - mf.x, r1 - mf.y);
-                    ph[e2] = *reinterpret_cast<const uint32_t *>(&h);
-                    pm[e2] = *reinterpret_cast<const uint32_t *>(&mm);
-                    pl[e2] = *reinterpret_cast<const uint32_t *>(&ll);
-                }
-                *reinterpret_cast<uint4 *>(st + off) = make_uint4(ph[0], ph[1], ph[2], ph[3]);
-                *reinterpret_cast<uint4 *>(st + A_PIECE + off) = make_uint4(pm[0], pm[1], pm[2], pm[3]);
-                *reinterpret_cast<uint4 *>(st + 2 * A_PIECE + off) = make_uint4(pl[0], pl[1], pl[2], pl[3]);
-            }
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            mbar_arrive(&full_a[s]);
-            // promote the previous segment once the next one has started
-            if (q % SEG == 0 && q > 0) {
-                ok = promote(promoted);
-                ++promoted;
-            }
+            if (q + 1 < nchunks) reinterpret_cast<float2 *>(cbuf[(q + 1) & 1])[tid] = cnext;
+            asm volatile("bar.sync 1, %0;" ::"n"(NPROD) : "memory");
         }
-        // never leave a bulk copy in flight: wait for the ones not consumed
-        if (tid == 0)
-            for (int k = b_waited; k < b_issued; ++k) mbar_wait(&full_b[k & 1], (uint32_t)(k >> 1) & 1, status, false);
         if (ok)
             while (promoted < nseg && ok) {
                 ok = promote(promoted);
@@ -387,6 +380,22 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_sample_tc(Params P) {
                 *reinterpret_cast<double2 *>(dst + k) =
                     make_double2(f2d(acc_hi[k]) + f2d(acc_lo[k]), f2d(acc_hi[k + 1]) + f2d(acc_lo[k + 1]));
             }
+        }
+    } else if (warp == 9) {
+        // ------------------------------------------------------------ TMA issuer
+        if (lane == 0) {
+            int issued = 0;
+            for (int q = 0; q < nchunks && ok; ++q) {
+                const int s = q & 1;
+                if (q >= 2) ok = mbar_wait(&empty[s], ((uint32_t)(q >> 1) - 1) & 1, status);
+                if (!ok) break;
+                mbar_expect_tx(&full_b[s], b_bytes(r));
+                bulk_g2s(smem + s * SB + 3 * A_PIECE, gpack + (size_t)q * CB, b_bytes(r), &full_b[s]);
+                issued = q + 1;
+            }
+            // never leave a bulk copy in flight: wait for the last two issued
+            for (int k = (issued > 2 ? issued - 2 : 0); k < issued; ++k)
+                mbar_wait(&full_b[k & 1], (uint32_t)(k >> 1) & 1, status, false);
         }
     } else if (lane == 0) {
         // ------------------------------------------------------------ MMA issuer
