@@ -22,6 +22,9 @@
  *    cudaStream_t passed as void*; NULL = the legacy default stream).  Calls
  *    that return sizes to the host (hm_tree_build, hm_color, hm_compress,
  *    hm_get_info, hm_export) synchronise that stream; the others do not.
+ *    hm_compress also colours the levels on a second stream that the context
+ *    creates (non-blocking, highest priority), from a host thread of its own,
+ *    ahead of the level loop; both have finished when hm_compress returns.
  *  - The context owns every device buffer it allocates (tree, colourings,
  *    samples, factors); hm_destroy frees them.
  *  - Matrices at the boundary are column-major with leading dimension n and are
@@ -120,7 +123,8 @@ typedef struct {
     double seconds_sample;    /* time in the black box during hm_compress */
     double seconds_total;     /* wall time of hm_compress */
     double seconds_phase[8];  /* device time per phase of hm_compress (CUDA events):
-                                 0 colouring, 1 test matrices, 2 black box (admissible
+                                 0 colouring (host time the level loop waited for
+                                 the colourings that run ahead of it), 1 test matrices, 2 black box (admissible
                                  levels), 3 peel, 4 bases and cores, 5 leaf black box,
                                  6 leaf peel and extraction, 7 the tensor-core
                                  contraction kernels alone (inside 2) */

@@ -10,8 +10,9 @@
 //       (alpha, beta) is the Q of the Z tile of the pair (beta, alpha).
 //  K10  B = (G_alpha^T U)^+ (G_alpha^T Y(I_alpha, c)) (V^T G_beta)^+ with
 //       G_alpha the Psi-side block of alpha and G_beta the Omega-side block of
-//       beta, by Householder QR of the two r x k matrices and triangular solves
-//       (one warp per pair).
+//       beta: the three r x k products over the boxes' rows by row-split CTAs
+//       (k_gram), then Householder QR of the two r x k matrices and triangular
+//       solves in shared memory (one warp per pair).
 //  K11  D_{alpha,beta} = Y_leaf(I_alpha, c m_max + [0, |I_beta|)).
 #include "ctx.cuh"
 
@@ -19,41 +20,63 @@
 
 namespace hm {
 
-// M_p = G^Psi(I_alpha)^T P_p  (r x r), before the tile is factored in place
-__global__ void __launch_bounds__(256) k_core_M(const int *tile_alpha, const int *tile_color, const int *ent, int64_t n,
-                                                int r, const double *Y, const double *GP, double *M) {
-    __shared__ double gs[32][64], ps[32][64];
+// Row-split Gram products of the core solve, one CTA per (pair, chunk of
+// GRAM_CHUNK rows):  out[chunk][p] (r x r slot, row-major, first kf columns)
+//   = sum over the chunk's rows i of G(s0 + i, :)^T F_p(i, :),
+// G the level's Gaussians [n][r], s0 the first row of box[p], F_p the pair's
+// block: the peeled Y tile of colour color[p] (kdim == nullptr, kf = r) or the
+// packed factor at offF[p] with kf = kdim[p] columns.  A chunk beyond the box
+// writes zeros; the consumer adds the chunks in order.
+constexpr int GRAM_CHUNK = 1024;
+
+__global__ void __launch_bounds__(256) k_gram(const int *box, const int *ent, int64_t np, int r, const double *G,
+                                              const double *F, const int *color, int64_t n, const int64_t *offF,
+                                              const int *kdim, double *out) {
+    __shared__ double gs[32][64], fs[32][64];
     const int64_t p = blockIdx.x;
-    const int *e = ent + (int64_t)tile_alpha[p] * ENT_FIELDS;
+    const int *e = ent + (int64_t)box[p] * ENT_FIELDS;
     const int s0 = e[3], m = e[4] - e[3];
-    const double *P = Y + ((int64_t)tile_color[p] * n + s0) * r;
+    int kf;
+    const double *Fp;
+    if (kdim) {
+        kf = kdim[p];
+        Fp = F + offF[p];
+    } else {
+        kf = r;
+        Fp = F + ((int64_t)color[p] * n + s0) * r;
+    }
+    const int i_begin = blockIdx.y * GRAM_CHUNK, i_end = min(m, i_begin + GRAM_CHUNK);
     double acc[16];
 #pragma unroll
     for (int q = 0; q < 16; ++q) acc[q] = 0.0;
-    for (int i0 = 0; i0 < m; i0 += 32) {
-        const int mm = min(32, m - i0);
+    for (int i0 = i_begin; i0 < i_end; i0 += 32) {
+        const int mm = min(32, i_end - i0);
         for (int o = threadIdx.x; o < 32 * r; o += 256) {
             const int i = o / r, j = o % r;
-            gs[i][j] = (i < mm) ? GP[(int64_t)(s0 + i0 + i) * r + j] : 0.0;
-            ps[i][j] = (i < mm) ? P[(int64_t)(i0 + i) * r + j] : 0.0;
+            gs[i][j] = (i < mm) ? G[(int64_t)(s0 + i0 + i) * r + j] : 0.0;
+        }
+        for (int o = threadIdx.x; o < 32 * kf; o += 256) {
+            const int i = o / kf, j = o % kf;
+            fs[i][j] = (i < mm) ? Fp[(int64_t)(i0 + i) * kf + j] : 0.0;
         }
         __syncthreads();
 #pragma unroll
         for (int q = 0; q < 16; ++q) {
             const int o = threadIdx.x + q * 256;
-            if (o < r * r) {
-                const int a = o / r, b = o % r;
-                double s = acc[q];
-                for (int i = 0; i < mm; ++i) s = fma(gs[i][a], ps[i][b], s);
-                acc[q] = s;
+            if (o < r * kf) {
+                const int a = o / kf, b = o % kf;
+                double sacc = acc[q];
+                for (int i = 0; i < mm; ++i) sacc = fma(gs[i][a], fs[i][b], sacc);
+                acc[q] = sacc;
             }
         }
         __syncthreads();
     }
+    double *o_ = out + ((int64_t)blockIdx.y * np + p) * r * r;
 #pragma unroll
     for (int q = 0; q < 16; ++q) {
         const int o = threadIdx.x + q * 256;
-        if (o < r * r) M[p * r * r + o] = acc[q];
+        if (o < r * kf) o_[(o / kf) * r + o % kf] = acc[q];
     }
 }
 
@@ -395,42 +418,36 @@ __device__ void warp_back_solve(const double *A, int k, int lda, double *X, int 
     __syncwarp();
 }
 
-// one warp per pair, four pairs per CTA: B = (GP_a^T U)^+ M (GO_b^T V)^{+T};
-// M (r x r, FP64) is worked on in place in its scratch; S1, S2 and X^T live in
-// shared memory with leading dimension kc (the largest k)
+// one warp per pair, up to four pairs per CTA: B = (GP_a^T U)^+ M (GO_b^T V)^{+T}.
+// M = GP_a^T P, S1 = GP_a^T U and S2 = GO_b^T V arrive as nsplit row-chunk
+// partial products (k_gram); the warp adds them in chunk order into shared
+// memory, where S1, S2 and X^T have leading dimension kc (the largest k) and
+// M leading dimension r.
 constexpr int CORE_WARPS = 4;
 
-__global__ void __launch_bounds__(128) k_core(const int *pair_alpha, const int *pair_col, const int *ent,
-                                                          int r, int kc, int64_t np, const int *kU, const int *kV,
-                                                          const int64_t *offU, const int64_t *offV,
-                                                          const int64_t *offB, const double *U, const double *V,
-                                                          const double *GO, const double *GP, double *M, double *B) {
+__device__ __forceinline__ double sum_chunks(const double *part, int nsplit, int64_t np, int64_t p, int r, int idx) {
+    double s = 0.0;
+    for (int c = 0; c < nsplit; ++c) s += part[((int64_t)c * np + p) * r * r + idx];
+    return s;
+}
+
+__global__ void __launch_bounds__(128) k_core(int r, int kc, int64_t np, int nsplit, const int *kU, const int *kV,
+                                              const int64_t *offB, const double *Mpart, const double *S1part,
+                                              const double *S2part, double *B) {
     extern __shared__ double sm[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
     const int64_t p = (int64_t)blockIdx.x * nwarps + warp;
     if (p >= np) return;
     const int ku = kU[p], kv = kV[p];
     if (ku == 0 || kv == 0) return;
-    double *S1 = sm + (size_t)warp * (3 * r * kc + r);  // r x ku  (ld kc)
-    double *S2 = S1 + r * kc;                            // r x kv
-    double *X = S2 + r * kc;                             // r x ku: X^T
-    double *tau = X + r * kc;                            // r
-    double *Mx = M + p * r * r;                          // r x r (ld r), in place
-    const int *ea = ent + (int64_t)pair_alpha[p] * ENT_FIELDS, *eb = ent + (int64_t)pair_col[p] * ENT_FIELDS;
-    const int sa = ea[3], ma = ea[4] - ea[3], sb = eb[3], mb = eb[4] - eb[3];
-    const double *Up = U + offU[p], *Vp = V + offV[p];
-    for (int o = lane; o < r * ku; o += 32) {
-        const int a = o / ku, u = o % ku;
-        double sacc = 0.0;
-        for (int i = 0; i < ma; ++i) sacc = fma(GP[(int64_t)(sa + i) * r + a], Up[(int64_t)i * ku + u], sacc);
-        S1[a * kc + u] = sacc;
-    }
-    for (int o = lane; o < r * kv; o += 32) {
-        const int a = o / kv, v = o % kv;
-        double sacc = 0.0;
-        for (int i = 0; i < mb; ++i) sacc = fma(GO[(int64_t)(sb + i) * r + a], Vp[(int64_t)i * kv + v], sacc);
-        S2[a * kc + v] = sacc;
-    }
+    double *S1 = sm + (size_t)warp * (3 * r * kc + r + r * r);  // r x ku  (ld kc)
+    double *S2 = S1 + r * kc;                                    // r x kv
+    double *X = S2 + r * kc;                                     // r x ku: X^T
+    double *tau = X + r * kc;                                    // r
+    double *Mx = tau + r;                                        // r x r (ld r)
+    for (int o = lane; o < r * ku; o += 32) S1[(o / ku) * kc + o % ku] = sum_chunks(S1part, nsplit, np, p, r, (o / ku) * r + o % ku);
+    for (int o = lane; o < r * kv; o += 32) S2[(o / kv) * kc + o % kv] = sum_chunks(S2part, nsplit, np, p, r, (o / kv) * r + o % kv);
+    for (int o = lane; o < r * r; o += 32) Mx[o] = sum_chunks(Mpart, nsplit, np, p, r, o);
     __syncwarp();
     // X = R1^{-1} (Q1^T M)(0:ku, :)
     warp_house_qr(S1, r, ku, kc, tau);
@@ -467,11 +484,17 @@ Err bases_and_cores(hm_ctx *c, int level) {
         f.done = true;
         return ok();
     }
-    // M = G_alpha^T P for every pair (tile p is read only by pair p)
-    HM_TRY(ensure(c->scratch_a, (size_t)np * r * r * sizeof(double)));
-    k_core_M<<<(int)np, 256, 0, st>>>(g.pair_alpha.as<int>(), g.pair_color.as<int>(), cu.ent.as<int>(), n, r,
-                                      c->cur.Y.as<double>(), c->GP.as<double>(), c->scratch_a.as<double>()); ::hm::count_launch();
-    HM_LAUNCH("core_M");
+    // M = G_alpha^T P for every pair (tile p is read only by pair p), before the
+    // tiles are factored in place
+    if (r > 64) return fail(HM_ENOTSUP, "cores: r > 64");
+    const int nsplit = std::max(1, ceil_div(cu.max_rows, GRAM_CHUNK));
+    const size_t part_bytes = (size_t)nsplit * np * r * r * sizeof(double);
+    HM_TRY(ensure(c->scratch_a, part_bytes));
+    k_gram<<<dim3((unsigned)np, nsplit), 256, 0, st>>>(g.pair_alpha.as<int>(), cu.ent.as<int>(), np, r,
+                                                       c->GP.as<double>(), c->cur.Y.as<double>(),
+                                                       g.pair_color.as<int>(), n, nullptr, nullptr,
+                                                       c->scratch_a.as<double>()); ::hm::count_launch();
+    HM_LAUNCH("gram M");
     // QR of every Y tile and every Z tile
     DBuf kY, kZ;
     HM_TRY(alloc(kY, np * sizeof(int)));
@@ -517,15 +540,25 @@ Err bases_and_cores(hm_ctx *c, int level) {
                                     c->cur.Z.as<double>(), f.U.as<double>(), f.V.as<double>()); ::hm::count_launch();
     HM_LAUNCH("pack");
     const int kc = std::max(1, c->cfg.rank > 0 ? std::min(r, c->cfg.rank) : std::min(r, cap));
-    const size_t per_warp = (3 * (size_t)r * kc + r) * sizeof(double);
+    // S1 = G_alpha^T U (Psi side) and S2 = G_beta^T V (Omega side)
+    DBuf spart;
+    HM_TRY(alloc(spart, 2 * part_bytes));
+    double *S1part = spart.as<double>(), *S2part = S1part + (size_t)nsplit * np * r * r;
+    k_gram<<<dim3((unsigned)np, nsplit), 256, 0, st>>>(g.pair_alpha.as<int>(), cu.ent.as<int>(), np, r,
+                                                       c->GP.as<double>(), f.U.as<double>(), nullptr, n,
+                                                       f.offU.as<int64_t>(), f.kU.as<int>(), S1part); ::hm::count_launch();
+    k_gram<<<dim3((unsigned)np, nsplit), 256, 0, st>>>(cu.int_idx.as<int>(), cu.ent.as<int>(), np, r,
+                                                       c->GO.as<double>(), f.V.as<double>(), nullptr, n,
+                                                       f.offV.as<int64_t>(), f.kV.as<int>(), S2part); ::hm::count_launch();
+    HM_LAUNCH("gram S");
+    const size_t per_warp = (3 * (size_t)r * kc + r + (size_t)r * r) * sizeof(double);
     const int core_warps = (int)std::min<size_t>(CORE_WARPS, (200 * 1024) / per_warp);
     if (core_warps < 1) return fail(HM_ENOTSUP, "cores: r x k too large for shared memory");
     const size_t smem = (size_t)core_warps * per_warp;
     HM_CUDA(cudaFuncSetAttribute(k_core, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_core<<<ceil_div(np, core_warps), core_warps * 32, smem, st>>>(
-        g.pair_alpha.as<int>(), cu.int_idx.as<int>(), cu.ent.as<int>(), r, kc, np, f.kU.as<int>(), f.kV.as<int>(),
-        f.offU.as<int64_t>(), f.offV.as<int64_t>(), f.offB.as<int64_t>(), f.U.as<double>(), f.V.as<double>(),
-        c->GO.as<double>(), c->GP.as<double>(), c->scratch_a.as<double>(), f.B.as<double>()); ::hm::count_launch();
+    k_core<<<ceil_div(np, core_warps), core_warps * 32, smem, st>>>(r, kc, np, nsplit, f.kU.as<int>(), f.kV.as<int>(),
+                                                                    f.offB.as<int64_t>(), c->scratch_a.as<double>(),
+                                                                    S1part, S2part, f.B.as<double>()); ::hm::count_launch();
     HM_LAUNCH("core");
     std::vector<int> hk;
     HM_TRY(to_host(hk, f.kU.p, np, st));

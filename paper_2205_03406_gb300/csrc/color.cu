@@ -347,13 +347,18 @@ __global__ void k_act_rows(const int *act_box, int64_t na, const int *ent, const
     for (int r = e[3] + lane; r < e[4]; r += 32) rows[rowoff[i] + (r - e[3])] = r;
 }
 
-Err color_cut(hm_ctx *c, int level, bool leaf) {
-    cudaStream_t st = c->st;
+Err color_cut(hm_ctx *c, int level, bool leaf) { return color_cut(c, level, leaf, c->st, c->scan_tmp); }
+
+// Everything runs on `st`, with `scan_tmp` as the scan scratch, and the call
+// returns after `st` has drained: a colouring reads and writes only its own
+// cut's entry of c->colorings, so colourings of different levels may run on
+// different host threads and streams.
+Err color_cut(hm_ctx *c, int level, bool leaf, cudaStream_t st, DBuf &scan_tmp) {
     const int l = leaf ? c->L : level;
     if (l < 0 || l > c->L) return fail(HM_EINVAL, "colour: level out of range");
     Cut &cu = c->cuts[l];
     const int idx = leaf ? c->L + 1 : level;
-    if ((int)c->colorings.size() < c->L + 2) c->colorings.resize(c->L + 2);
+    if ((int)c->colorings.size() < c->L + 2) return fail(HM_ESTATE, "colour: build the tree first");
     Coloring &g = c->colorings[idx];
     g = Coloring();
     g.leaf = leaf;
@@ -411,7 +416,7 @@ Err color_cut(hm_ctx *c, int level, bool leaf) {
     HM_TRY(alloc(vidx, nv * sizeof(int)));
     k_vby_beta<<<ceil_div(nc, 128), 128, 0, st>>>(g.pair_ptr, g.pair_T.as<int>(), first.as<int64_t>(),
                                                   g.pair_vertex.as<int>(), nc, 0, vcnt.as<int>(), nullptr, nullptr); ::hm::count_launch();
-    HM_TRY(scan_counts_i32(vcnt.as<int>(), vptr64.as<int64_t>(), nc, st, c->scan_tmp));
+    HM_TRY(scan_counts_i32(vcnt.as<int>(), vptr64.as<int64_t>(), nc, st, scan_tmp));
     k_vby_beta<<<ceil_div(nc, 128), 128, 0, st>>>(g.pair_ptr, g.pair_T.as<int>(), first.as<int64_t>(),
                                                   g.pair_vertex.as<int>(), nc, 1, nullptr, vptr64.as<int64_t>(),
                                                   vidx.as<int>()); ::hm::count_launch();
@@ -434,7 +439,7 @@ Err color_cut(hm_ctx *c, int level, bool leaf) {
                                             vptr.as<int>(), vidx.as<int>(), 0, g.vertex_degree.as<int>(), nullptr,
                                             nullptr); ::hm::count_launch();
     HM_LAUNCH("edges count");
-    HM_TRY(scan_counts_i32(g.vertex_degree.as<int>(), adj_ptr.as<int64_t>(), nv, st, c->scan_tmp));
+    HM_TRY(scan_counts_i32(g.vertex_degree.as<int>(), adj_ptr.as<int64_t>(), nv, st, scan_tmp));
     int64_t n_adj = 0;
     HM_TRY(read_scalar(n_adj, adj_ptr.as<int64_t>() + nv, st));
     g.n_edges = n_adj / 2;
@@ -457,6 +462,7 @@ Err color_cut(hm_ctx *c, int level, bool leaf) {
                                  forb.as<unsigned int>(), g.vertex_color.as<int>(), status.as<int>()); ::hm::count_launch();
     HM_LAUNCH("dsatur");
     int hs[2];
+    HM_CUDA(cudaStreamSynchronize(st));  // DSatur first, then the pageable copy (see to_host)
     HM_CUDA(cudaMemcpyAsync(hs, status.p, sizeof(hs), cudaMemcpyDeviceToHost, st));
     HM_CUDA(cudaStreamSynchronize(st));
     if (hs[1]) return fail(HM_ENOTSUP, "colour: more than 1024 colours");
@@ -475,7 +481,7 @@ Err color_cut(hm_ctx *c, int level, bool leaf) {
     HM_TRY(alloc(cnt, std::max(chi, nc) * sizeof(int)));
     HM_TRY(alloc(off64, (std::max(chi, nc) + 1) * sizeof(int64_t)));
     k_act_by_color<<<chi, 1024, 0, st>>>(act.as<unsigned char>(), nc, 0, cnt.as<int>(), nullptr, nullptr); ::hm::count_launch();
-    HM_TRY(scan_counts_i32(cnt.as<int>(), off64.as<int64_t>(), chi, st, c->scan_tmp));
+    HM_TRY(scan_counts_i32(cnt.as<int>(), off64.as<int64_t>(), chi, st, scan_tmp));
     std::vector<int64_t> hoff;
     HM_TRY(to_host(hoff, off64.p, chi + 1, st));
     const int64_t na = hoff[chi];
@@ -489,7 +495,7 @@ Err color_cut(hm_ctx *c, int level, bool leaf) {
     }
     k_act_by_entry<<<ceil_div(nc, 128), 128, 0, st>>>(act.as<unsigned char>(), nc, chi, 0, cnt.as<int>(), nullptr,
                                                       nullptr); ::hm::count_launch();
-    HM_TRY(scan_counts_i32(cnt.as<int>(), off64.as<int64_t>(), nc, st, c->scan_tmp));
+    HM_TRY(scan_counts_i32(cnt.as<int>(), off64.as<int64_t>(), nc, st, scan_tmp));
     {
         std::vector<int64_t> h;
         HM_TRY(to_host(h, off64.p, nc + 1, st));
@@ -506,7 +512,7 @@ Err color_cut(hm_ctx *c, int level, bool leaf) {
         HM_TRY(alloc(sz, std::max<int64_t>(na, 1) * sizeof(int)));
         HM_TRY(alloc(rowoff, (na + 1) * sizeof(int64_t)));
         k_act_sizes<<<ceil_div(na, 256), 256, 0, st>>>(g.act_box.as<int>(), na, cu.ent.as<int>(), sz.as<int>()); ::hm::count_launch();
-        HM_TRY(scan_counts_i32(sz.as<int>(), rowoff.as<int64_t>(), na, st, c->scan_tmp));
+        HM_TRY(scan_counts_i32(sz.as<int>(), rowoff.as<int64_t>(), na, st, scan_tmp));
         std::vector<int64_t> hro;
         HM_TRY(to_host(hro, rowoff.p, na + 1, st));
         g.n_act_rows = hro[na];

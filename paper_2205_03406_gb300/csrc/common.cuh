@@ -138,12 +138,18 @@ Err scan_exclusive(const int64_t *in_dev, int64_t *out_dev, int64_t n, cudaStrea
 Err scan_counts_i32(const int *counts_dev, int64_t *out_dev, int64_t n, cudaStream_t st,
                     DBuf &tmp);
 
+// Device-to-host reads into pageable memory drain the stream FIRST and copy
+// after: a pageable copy queued behind a long kernel blocks inside the driver
+// until that kernel ends, and holds up the pageable copies of every other host
+// thread meanwhile (the colouring thread runs its kernels concurrently with
+// the level loop).
 template <class T> Err to_host(std::vector<T> &h, const void *d, size_t count, cudaStream_t st) {
     h.resize(count);
+    HM_CUDA(cudaStreamSynchronize(st));
     if (count) {
         HM_CUDA(cudaMemcpyAsync(h.data(), d, count * sizeof(T), cudaMemcpyDeviceToHost, st));
+        HM_CUDA(cudaStreamSynchronize(st));
     }
-    HM_CUDA(cudaStreamSynchronize(st));
     return ok();
 }
 
@@ -156,6 +162,7 @@ template <class T> Err to_dev(DBuf &b, const std::vector<T> &h, cudaStream_t st)
 }
 
 template <class T> Err read_scalar(T &v, const void *d, cudaStream_t st) {
+    HM_CUDA(cudaStreamSynchronize(st));
     HM_CUDA(cudaMemcpyAsync(&v, d, sizeof(T), cudaMemcpyDeviceToHost, st));
     HM_CUDA(cudaStreamSynchronize(st));
     return ok();

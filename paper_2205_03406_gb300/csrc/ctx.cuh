@@ -121,6 +121,11 @@ struct hm_ctx {
     // scratch
     hm::DBuf scratch_a, scratch_b, scratch_c, scratch_d, scan_tmp;
 
+    // second stream on which a host thread colours the levels ahead of the
+    // level loop (created on first use, destroyed with the context)
+    cudaStream_t color_st = nullptr;
+    hm::DBuf color_scan_tmp;
+
     hm_info info;
     double t_sample = 0.0;
     double t_tc = 0.0;        // device time of the tensor-core contraction kernels
@@ -131,7 +136,8 @@ namespace hm {
 // tree.cu
 Err build_tree(hm_ctx *c, const double *points_dev, int64_t n);
 // color.cu
-Err color_cut(hm_ctx *c, int level, bool leaf);
+Err color_cut(hm_ctx *c, int level, bool leaf);  // on c->st
+Err color_cut(hm_ctx *c, int level, bool leaf, cudaStream_t st, DBuf &scan_tmp);
 // sample.cu
 Err make_gaussians(hm_ctx *c, int level);
 Err sample_level(hm_ctx *c, const hm_op *op, int level, bool leaf);

@@ -8,6 +8,9 @@
 #include <cstring>
 
 #include <atomic>
+#include <condition_variable>
+#include <mutex>
+#include <thread>
 
 namespace hm {
 thread_local cudaStream_t g_alloc_stream = nullptr;
@@ -138,9 +141,10 @@ hm_status hm_destroy(hm_ctx *c) {
     if (!c) return HM_OK;
     {
         StreamScope ss(c->st);
-        cudaStream_t st = c->st;
+        cudaStream_t st = c->st, cst = c->color_st;
         delete c;
         cudaStreamSynchronize(st);
+        if (cst) cudaStreamDestroy(cst);
     }
     cudaGetLastError();
     return HM_OK;
@@ -214,6 +218,74 @@ static Err keep_current(hm_ctx *c, int idx, bool leaf) {
     return ok();
 }
 
+// The colourings (Section 4.1.1) depend on the tree alone, so a host thread
+// computes them for levels 2..L and the leaf level, in that order, on a second
+// stream of the highest priority (its one-CTA DSatur launches get the next
+// free SM) while the calling thread samples, peels and compresses the levels
+// already coloured.  wait(idx) returns once colouring idx is complete on the
+// device; its Coloring is then only read.
+class ColorAhead {
+public:
+    explicit ColorAhead(hm_ctx *c) : c_(c), state_(c->L + 2, 0), errs_(c->L + 2) {}
+    ~ColorAhead() {
+        stop_ = true;
+        if (th_.joinable()) th_.join();
+    }
+    Err start() {
+        int dev = 0;
+        HM_CUDA(cudaGetDevice(&dev));
+        if (!c_->color_st) {
+            int least = 0, greatest = 0;
+            HM_CUDA(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+            HM_CUDA(cudaStreamCreateWithPriority(&c_->color_st, cudaStreamNonBlocking, greatest));
+        }
+        try {
+            th_ = std::thread([this, dev] { run(dev); });
+        } catch (const std::exception &e) {
+            return fail(HM_ENOMEM, std::string("colour: cannot start the colouring thread: ") + e.what());
+        }
+        return ok();
+    }
+    // blocks until colouring idx is done; adds the blocked host time to *secs
+    Err wait(int idx, double *secs) {
+        const auto t0 = std::chrono::steady_clock::now();
+        std::unique_lock<std::mutex> lk(m_);
+        cv_.wait(lk, [&] { return state_[idx] != 0; });
+        *secs += std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        return state_[idx] == 2 ? errs_[idx] : ok();
+    }
+
+private:
+    void run(int dev) {
+        Err e;
+        if (cudaSetDevice(dev) != cudaSuccess) e = fail(HM_ECUDA, "colour: cudaSetDevice failed");
+        StreamScope ss(c_->color_st);
+        // levels 2..L, then the leaf level at index L + 1 (which is below 2 when L < 1)
+        std::vector<int> order;
+        for (int l = 2; l <= c_->L; ++l) order.push_back(l);
+        order.push_back(c_->L + 1);
+        for (int idx : order) {
+            const bool leaf = idx == c_->L + 1;
+            if (!e && stop_) e = fail(HM_ECUDA, "colour: cancelled");
+            if (!e && !c_->colorings[idx].done)
+                e = color_cut(c_, leaf ? 0 : idx, leaf, c_->color_st, c_->color_scan_tmp);
+            {
+                std::lock_guard<std::mutex> lk(m_);
+                state_[idx] = e ? 2 : 1;
+                errs_[idx] = e;  // after a failure every later level reports it too
+            }
+            cv_.notify_all();
+        }
+    }
+    hm_ctx *c_;
+    std::thread th_;
+    std::mutex m_;
+    std::condition_variable cv_;
+    std::vector<int> state_;  // 0 pending, 1 done, 2 failed
+    std::vector<Err> errs_;
+    std::atomic<bool> stop_{false};
+};
+
 static Err compress_all(hm_ctx *c, const hm_op *op) {
     const auto t0 = std::chrono::steady_clock::now();
     const long long launches0 = launches_so_far();
@@ -244,9 +316,11 @@ static Err compress_all(hm_ctx *c, const hm_op *op) {
     } while (0)
     Err err;
     int64_t cols_total = 0;
+    double color_wait = 0.0;
+    ColorAhead ahead(c);
+    err = ahead.start();
     for (int l = 2; l <= c->L && !err; ++l) {
-        PHASE(0, color_cut(c, l, false));
-        if (err) break;
+        if ((err = ahead.wait(l, &color_wait))) break;
         const Coloring &g = c->colorings[l];
         if (g.n_pairs == 0 || g.n_colors == 0) {
             c->factors[l] = Factors();
@@ -263,7 +337,7 @@ static Err compress_all(hm_ctx *c, const hm_op *op) {
         if ((err = keep_current(c, l, false))) break;
         PHASE(4, bases_and_cores(c, l));
     }
-    if (!err) PHASE(0, color_cut(c, 0, true));
+    if (!err) err = ahead.wait(c->L + 1, &color_wait);
     if (!err) {
         const Coloring &g = c->colorings[c->L + 1];
         PHASE(5, sample_level(c, op, HM_LEVEL_LEAF, true));
@@ -278,7 +352,7 @@ static Err compress_all(hm_ctx *c, const hm_op *op) {
     if (cur_start) cudaEventDestroy(cur_start);
     cudaError_t ce = cudaStreamSynchronize(c->st);
     if (!err && ce != cudaSuccess) err = fail(HM_ECUDA, std::string("compress: ") + cudaGetErrorString(ce));
-    double phase[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    double phase[8] = {color_wait, 0, 0, 0, 0, 0, 0, 0};
     for (auto &e : ev) {
         float ms = 0.f;
         if (cudaEventElapsedTime(&ms, e.second.first, e.second.second) == cudaSuccess) phase[e.first] += ms * 1e-3;

@@ -37,7 +37,7 @@ __global__ void k_xsize(const int *pair_alpha, const int *pair_col, int64_t np, 
 }
 
 // X_{q,gamma} (k x cols, FP32): F_q(I_gamma)^T G(I_gamma), or the identity
-// block's F rows at the leaf step
+// block's F rows at the leaf step; CTA (q, y) takes the gammas y, y + gridDim.y, ...
 __global__ void k_peel_x32(const int *pair_alpha, const int *pair_col, const int *entj, const int *entl,
                            const int *pt2ent_l, const int *kdim, const int64_t *offF, const float *F, const float *G,
                            int cols, int identity, int side, const int64_t *xoff, float *X) {
@@ -50,7 +50,7 @@ __global__ void k_peel_x32(const int *pair_alpha, const int *pair_col, const int
     const int kb = pt2ent_l[e[3]], ke = pt2ent_l[e[4] - 1] + 1;
     const float *Fq = F + offF[q];
     float *Xq = X + xoff[q];
-    for (int g = kb; g < ke; ++g) {
+    for (int g = kb + blockIdx.y; g < ke; g += gridDim.y) {
         const int *eg = entl + (int64_t)g * ENT_FIELDS;
         const int s0 = eg[3], len = eg[4] - eg[3];
         float *xg = Xq + (int64_t)(g - kb) * k * cols;
@@ -263,7 +263,9 @@ Err peel_level_mixed(hm_ctx *c, int level, bool leaf) {
             int64_t xtot = 0;
             HM_TRY(read_scalar(xtot, xo.as<int64_t>() + np, st));
             HM_TRY(alloc(X, std::max<int64_t>(xtot, 1) * sizeof(float)));
-            pm::k_peel_x32<<<(int)np, 128, 0, st>>>(gj.pair_alpha.as<int>(), cj.int_idx.as<int>(), cj.ent.as<int>(),
+            // CTAs per coarse pair: about one per level-l box inside the largest coarse box
+            const int gy = std::min(256, std::max(1, cj.max_rows / std::max(1, std::min(cl.max_rows, 64))));
+            pm::k_peel_x32<<<dim3((unsigned)np, gy), 128, 0, st>>>(gj.pair_alpha.as<int>(), cj.int_idx.as<int>(), cj.ent.as<int>(),
                                                      cl.ent.as<int>(), cl.pt2ent.as<int>(), kdim,
                                                      side ? f.offU.as<int64_t>() : f.offV.as<int64_t>(),
                                                      side ? f.U32.as<float>() : f.V32.as<float>(),
