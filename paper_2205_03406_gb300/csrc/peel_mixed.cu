@@ -5,14 +5,15 @@
 // the FP64 samples is FP64.  The FP32 products carry the same ~1e-7 relative
 // rounding as the mixed-precision black-box samples they are subtracted from.
 //
-// One warp owns one (tile, chunk of 32 rows), lane = row, and walks every
-// coarse level and pair with warp-level synchronisation only:
-//   * the level-l boxes gamma inside the coarse pair's other box that are
-//     active in the tile's colour c form a contiguous run of that colour's
-//     sorted active-box list, found by two binary searches;
-//   * W = sum of the precomputed X_{q,gamma} = F_q(I_gamma)^T G(I_gamma) over
-//     them, T = B_q W (or B_q^T W), and acc(row) += F_q'(row, :) T;
-//   * at the end the FP64 tile -= acc.
+// For every coarse level j the subtraction splits into two products:
+//   T_{q,c} = B_q W_{q,c},  W_{q,c} = sum over the level-l boxes gamma inside the
+//   pair's other box that are active in colour c of X_{q,gamma} = F_q(I_gamma)^T G(I_gamma),
+// computed ONCE per (coarse pair q, colour c) that some tile needs (k_peel_T),
+// and the update of every tile (alpha, c) by sum over q of F'_q(I_alpha) T_{q,c},
+// a register-tiled FP32 product over 64-row chunks (k_peel_gemm).  The (q, c)
+// combinations a level needs are found through the (ancestor box A at level
+// j, colour c) combinations of the tiles: the slots of T for (A, c) are
+// contiguous, one per entry of A's interaction list, in list order.
 #include "ctx.cuh"
 
 namespace hm {
@@ -75,6 +76,9 @@ struct Coarse {
     const float *U, *V, *B;
     const int64_t *xoff;
     const float *X;
+    const int64_t *base;        // [nc_j * chi + 1]: first T slot of (A, c)
+    float *T;                   // [slots][kcap][cols]
+    unsigned char *live;        // [slots]: T holds a nonzero product
 };
 
 __device__ __forceinline__ int lower_bound(const int *a, int lo, int hi, int key) {
@@ -86,11 +90,72 @@ __device__ __forceinline__ int lower_bound(const int *a, int lo, int hi, int key
     return lo;
 }
 
+// weight of (A, c): the length of A's interaction list if some tile (alpha, c)
+// lies inside A (idempotent writes), else 0 from the memset
+__global__ void k_anc_mark(const int *tile_alpha, const int *tile_color, int64_t ntiles, const int *entl,
+                           const int *pt2ent_j, const int *int_ptr_j, int chi, int64_t *w) {
+    const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (p >= ntiles) return;
+    const int A = pt2ent_j[entl[(int64_t)tile_alpha[p] * ENT_FIELDS + 3]];
+    w[(int64_t)A * chi + tile_color[p]] = int_ptr_j[A + 1] - int_ptr_j[A];
+}
+
+// One warp per (A, c) combination of level j; for every entry t of A's
+// interaction list: W = sum of X_{q,gamma} over the gammas of colour c in the
+// other box, T[slot] = B W (Y side, B is kout x kin) or B^T W (Z side).
+__global__ void __launch_bounds__(WARPS * 32) k_peel_T(Coarse C, int64_t ncomb, int chi, int side, int cols,
+                                                     int kcap, const int *pt2ent_l, const int *act_ptr,
+                                                     const int *act_box) {
+    extern __shared__ float sm[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t e = (int64_t)blockIdx.x * WARPS + warp;
+    if (e >= ncomb) return;
+    const int64_t s0 = C.base[e];
+    if (C.base[e + 1] == s0) return;  // no tile needs (A, c)
+    const int A = (int)(e / chi), c = (int)(e % chi);
+    float *W = sm + (size_t)warp * kcap * cols;
+    const int a0 = act_ptr[c], a1 = act_ptr[c + 1];
+    const int t0 = C.int_ptr[A];
+    for (int t = t0; t < C.int_ptr[A + 1]; ++t) {
+        const int64_t slot = s0 + (t - t0);
+        const int q = side ? C.pairT[t] : t;
+        const int kin = side ? C.kU[q] : C.kV[q];
+        const int kout = side ? C.kV[q] : C.kU[q];
+        int lo = 0, hi = 0;
+        if (kin > 0 && kout > 0) {
+            const int *eo = C.ent + (int64_t)C.int_idx[t] * ENT_FIELDS;
+            const int kb = pt2ent_l[eo[3]], ke = pt2ent_l[eo[4] - 1] + 1;
+            lo = lower_bound(act_box, a0, a1, kb);
+            hi = lower_bound(act_box, lo, a1, ke);
+            if (lo < hi) {
+                const float *Xq = C.X + C.xoff[q];
+                for (int o = lane; o < kin * cols; o += 32) {
+                    float sacc = 0.0f;
+                    for (int g = lo; g < hi; ++g) sacc += Xq[(int64_t)(act_box[g] - kb) * kin * cols + o];
+                    W[o] = sacc;
+                }
+                __syncwarp();
+                const float *Bq = C.B + C.offB[q];
+                float *To = C.T + slot * kcap * cols;
+                for (int o = lane; o < kout * cols; o += 32) {
+                    const int u = o / cols, col = o % cols;
+                    float sacc = 0.0f;
+                    for (int v = 0; v < kin; ++v)
+                        sacc = fmaf(side ? Bq[v * kout + u] : Bq[u * kin + v], W[v * cols + col], sacc);
+                    To[o] = sacc;
+                }
+                __syncwarp();
+            }
+        }
+        if (lane == 0) C.live[slot] = (kin > 0 && kout > 0 && lo < hi) ? 1 : 0;
+    }
+}
+
 __global__ void k_item_count(const int *tile_alpha, const int *entl, int64_t ntiles, int64_t *cnt) {
     const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (p >= ntiles) return;
     const int *e = entl + (int64_t)tile_alpha[p] * ENT_FIELDS;
-    cnt[p] = (e[4] - e[3] + 31) / 32;
+    cnt[p] = (e[4] - e[3] + 63) / 64;
 }
 
 __global__ void k_item_fill(const int64_t *off, int64_t ntiles, int64_t *item_tile, int *item_row) {
@@ -98,89 +163,94 @@ __global__ void k_item_fill(const int64_t *off, int64_t ntiles, int64_t *item_ti
     if (p >= ntiles) return;
     for (int64_t k = off[p]; k < off[p + 1]; ++k) {
         item_tile[k] = p;
-        item_row[k] = (int)(k - off[p]) * 32;
+        item_row[k] = (int)(k - off[p]) * 64;
     }
 }
 
-// MAXC: compile-time bound on the columns per colour (32 or 64)
+// One CTA of 128 threads per 64-row chunk of a tile (alpha, c): for every
+// coarse level and every entry of the ancestor's interaction list with a live
+// T slot, acc += F'(rows, 0:kout) T (kout x cols), staged through shared
+// memory (F' transposed, leading dimension 68); thread (rg, cg) owns rows
+// 4rg..4rg+3 and columns cg*CW..cg*CW+CW-1 (CW = MAXC / 8).  At the end the
+// FP64 tile -= acc.  MAXC (32 or 64) bounds the columns, KMAX = 64 the ranks.
+constexpr int GEMM_ROWS = 64, GEMM_LDF = 68, KMAX = 64;
+
 template <int MAXC>
-__global__ void __launch_bounds__(WARPS * 32) k_peel_warp(const Coarse *cl, int ncl, int side, const int *tile_alpha,
-                                                         const int *tile_color, const int *entl,
-                                                         const int *pt2ent_l, const int *act_ptr,
-                                                         const int *act_box, const int64_t *item_tile,
-                                                         const int *item_row, int64_t nitems, int cols, int kcap,
-                                                         int64_t n, double *OUT) {
-    extern __shared__ float sm[];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t item = (int64_t)blockIdx.x * WARPS + warp;
-    if (item >= nitems) return;  // the whole warp leaves together
-    float *W = sm + (size_t)warp * 2 * kcap * MAXC;
-    float *T = W + (size_t)kcap * MAXC;
+__global__ void __launch_bounds__(128) k_peel_gemm(const Coarse *cl, int ncl, int side, int chi,
+                                                   const int *tile_alpha, const int *tile_color, const int *entl,
+                                                   const int64_t *item_tile, const int *item_row, int64_t nitems,
+                                                   int cols, int kcap, int64_t n, double *OUT) {
+    constexpr int CW = MAXC / 8;
+    __shared__ __align__(16) float Fs[KMAX * GEMM_LDF];
+    __shared__ __align__(16) float Ts[KMAX * MAXC];
+    const int64_t item = blockIdx.x;
+    if (item >= nitems) return;
+    const int tid = threadIdx.x, rg = tid >> 3, cg = tid & 7;
     const int64_t p = item_tile[item];
     const int alpha = tile_alpha[p], c = tile_color[p];
     const int *ea = entl + (int64_t)alpha * ENT_FIELDS;
     const int sa = ea[3] + item_row[item];
-    const int rows = min(32, ea[4] - sa);
-    const bool live = lane < rows;
-    float acc[MAXC];
+    const int rows = min(GEMM_ROWS, ea[4] - sa);
+    float acc[4][CW];
 #pragma unroll
-    for (int j = 0; j < MAXC; ++j) acc[j] = 0.0f;
-    const int a0 = act_ptr[c], a1 = act_ptr[c + 1];
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < CW; ++j) acc[i][j] = 0.0f;
     for (int lvl = 0; lvl < ncl; ++lvl) {
         const Coarse &C = cl[lvl];
-        const int anc = C.pt2ent[sa];
-        const int anc_start = C.ent[(int64_t)anc * ENT_FIELDS + 3];
-        for (int t = C.int_ptr[anc]; t < C.int_ptr[anc + 1]; ++t) {
+        const int A = C.pt2ent[sa];
+        const int anc_start = C.ent[(int64_t)A * ENT_FIELDS + 3];
+        const int t0 = C.int_ptr[A], t1 = C.int_ptr[A + 1];
+        const int64_t s0 = C.base[(int64_t)A * chi + c];
+        for (int t = t0; t < t1; ++t) {
+            const int64_t slot = s0 + (t - t0);
+            if (!C.live[slot]) continue;  // uniform over the CTA
             const int q = side ? C.pairT[t] : t;
-            const int kin = side ? C.kU[q] : C.kV[q];
             const int kout = side ? C.kV[q] : C.kU[q];
-            if (kin == 0 || kout == 0) continue;
-            const int *eo = C.ent + (int64_t)C.int_idx[t] * ENT_FIELDS;
-            const int kb = pt2ent_l[eo[3]], ke = pt2ent_l[eo[4] - 1] + 1;
-            const int lo = lower_bound(act_box, a0, a1, kb);
-            const int hi = lower_bound(act_box, lo, a1, ke);
-            if (lo == hi) continue;
-            // W = sum of X_{q,gamma} over the active gammas (kin x cols)
-            const float *Xq = C.X + C.xoff[q];
-            for (int o = lane; o < kin * cols; o += 32) {
-                float s = 0.0f;
-                for (int g = lo; g < hi; ++g) s += Xq[(int64_t)(act_box[g] - kb) * kin * cols + o];
-                W[(o / cols) * MAXC + o % cols] = s;
+            const float *F = (side ? C.V + C.offV[q] : C.U + C.offU[q]) + (int64_t)(sa - anc_start) * kout;
+            const float *Tq = C.T + slot * kcap * cols;
+            __syncthreads();  // the previous step's reads of Fs / Ts are done
+            for (int o = tid; o < GEMM_ROWS * kout; o += 128) {
+                const int row = o / kout, u = o % kout;
+                Fs[u * GEMM_LDF + row] = row < rows ? F[o] : 0.0f;
             }
-            __syncwarp();
-            // T = B W (Y side, B is kout x kin) or B^T W (Z side)
-            const float *Bq = C.B + C.offB[q];
-            for (int o = lane; o < kout * cols; o += 32) {
-                const int u = o / cols, col = o % cols;
-                float s = 0.0f;
-                for (int v = 0; v < kin; ++v)
-                    s = fmaf(side ? Bq[v * kout + u] : Bq[u * kin + v], W[v * MAXC + col], s);
-                T[u * MAXC + col] = s;
-            }
-            __syncwarp();
-            // acc(row) += F(row, :) T, F = U_q (Y side) or V_q (Z side), rows inside anc
-            const float *F = side ? C.V + C.offV[q] : C.U + C.offU[q];
-            const float *Fr = F + (int64_t)(sa - anc_start + lane) * kout;
+            for (int o = tid; o < kout * cols; o += 128) Ts[(o / cols) * MAXC + o % cols] = Tq[o];
+            if (cols < MAXC)
+                for (int o = tid; o < kout * (MAXC - cols); o += 128)
+                    Ts[(o / (MAXC - cols)) * MAXC + cols + o % (MAXC - cols)] = 0.0f;
+            __syncthreads();
             for (int u = 0; u < kout; ++u) {
-                const float f = live ? Fr[u] : 0.0f;
-                const float4 *tr = reinterpret_cast<const float4 *>(T + u * MAXC);
+                const float4 f = *reinterpret_cast<const float4 *>(&Fs[u * GEMM_LDF + rg * 4]);
+                float tv[CW];
 #pragma unroll
-                for (int j4 = 0; j4 < MAXC / 4; ++j4) {
-                    const float4 tv = tr[j4];
-                    acc[4 * j4] = fmaf(f, tv.x, acc[4 * j4]);
-                    acc[4 * j4 + 1] = fmaf(f, tv.y, acc[4 * j4 + 1]);
-                    acc[4 * j4 + 2] = fmaf(f, tv.z, acc[4 * j4 + 2]);
-                    acc[4 * j4 + 3] = fmaf(f, tv.w, acc[4 * j4 + 3]);
+                for (int j4 = 0; j4 < CW / 4; ++j4) {
+                    const float4 x = *reinterpret_cast<const float4 *>(&Ts[u * MAXC + cg * CW + 4 * j4]);
+                    tv[4 * j4] = x.x;
+                    tv[4 * j4 + 1] = x.y;
+                    tv[4 * j4 + 2] = x.z;
+                    tv[4 * j4 + 3] = x.w;
+                }
+#pragma unroll
+                for (int j = 0; j < CW; ++j) {
+                    acc[0][j] = fmaf(f.x, tv[j], acc[0][j]);
+                    acc[1][j] = fmaf(f.y, tv[j], acc[1][j]);
+                    acc[2][j] = fmaf(f.z, tv[j], acc[2][j]);
+                    acc[3][j] = fmaf(f.w, tv[j], acc[3][j]);
                 }
             }
-            __syncwarp();
         }
     }
-    if (!live) return;
-    double *out = OUT + ((int64_t)c * n + sa + lane) * cols;
 #pragma unroll
-    for (int j = 0; j < MAXC; ++j)
-        if (j < cols) out[j] -= (double)acc[j];
+    for (int i = 0; i < 4; ++i) {
+        const int row = rg * 4 + i;
+        if (row >= rows) continue;
+        double *out = OUT + ((int64_t)c * n + sa + row) * cols;
+#pragma unroll
+        for (int j = 0; j < CW; ++j) {
+            const int col = cg * CW + j;
+            if (col < cols) out[col] -= (double)acc[i][j];
+        }
+    }
 }
 
 }  // namespace pm
@@ -221,8 +291,9 @@ Err peel_level_mixed(hm_ctx *c, int level, bool leaf) {
         HM_TRY(f32_copy(G32[0], c->GO, n * r, st));
         HM_TRY(f32_copy(G32[1], c->GP, n * r, st));
     }
-    // work items: 32-row chunks of every tile
+    // work items: 64-row chunks of every tile
     const int64_t ntiles = g.n_pairs;
+    const int chi = g.n_colors;
     DBuf cnt, off, item_tile, item_row;
     HM_TRY(alloc(cnt, (ntiles + 1) * sizeof(int64_t)));
     HM_TRY(alloc(off, (ntiles + 1) * sizeof(int64_t)));
@@ -240,17 +311,41 @@ Err peel_level_mixed(hm_ctx *c, int level, bool leaf) {
     count_launch();
     HM_LAUNCH("item_fill");
 
+    // coarse levels with factors, and their (ancestor, colour) slot tables
+    // (the same for both sides)
+    std::vector<int> js;
+    for (int j = 2; j <= jmax; ++j)
+        if (j < (int)c->factors.size() && c->factors[j].done && c->factors[j].n_pairs > 0) js.push_back(j);
+    if (js.empty()) return ok();
+    std::vector<DBuf> bases(js.size());
+    std::vector<int64_t> nslots(js.size(), 0);
+    for (size_t i = 0; i < js.size(); ++i) {
+        const Cut &cj = c->cuts[js[i]];
+        const int64_t ncomb = (int64_t)cj.nc * chi;
+        DBuf w;
+        HM_TRY(alloc(w, (ncomb + 1) * sizeof(int64_t)));
+        HM_CUDA(cudaMemsetAsync(w.p, 0, (ncomb + 1) * sizeof(int64_t), st));
+        pm::k_anc_mark<<<ceil_div(ntiles, 256), 256, 0, st>>>(g.pair_alpha.as<int>(), g.pair_color.as<int>(), ntiles,
+                                                              cl.ent.as<int>(), cj.pt2ent.as<int>(),
+                                                              cj.int_ptr.as<int>(), chi, w.as<int64_t>());
+        count_launch();
+        HM_LAUNCH("anc_mark");
+        HM_TRY(alloc(bases[i], (ncomb + 1) * sizeof(int64_t)));
+        HM_TRY(scan_exclusive(w.as<int64_t>(), bases[i].as<int64_t>(), ncomb, st));
+        HM_TRY(read_scalar(nslots[i], bases[i].as<int64_t>() + ncomb, st));
+    }
+
     for (int side = 0; side < (leaf ? 1 : 2); ++side) {
         std::vector<pm::Coarse> tab;
-        std::vector<DBuf> xs, xoffs;
-        for (int j = 2; j <= jmax; ++j) {
-            if (j >= (int)c->factors.size() || !c->factors[j].done || c->factors[j].n_pairs == 0) continue;
+        std::vector<DBuf> keep;  // X, offsets, T and live flags of every coarse level
+        for (size_t i = 0; i < js.size(); ++i) {
+            const int j = js[i];
             Factors &f = c->factors[j];
             const Coloring &gj = c->colorings[j];
             const Cut &cj = c->cuts[j];
             const int64_t np = f.n_pairs;
             HM_TRY(factors_f32(f, st));
-            DBuf xsz, xo, X;
+            DBuf xsz, xo, X, T, live;
             HM_TRY(alloc(xsz, (np + 1) * sizeof(int64_t)));
             HM_TRY(alloc(xo, (np + 1) * sizeof(int64_t)));
             const int *kdim = side ? f.kU.as<int>() : f.kV.as<int>();
@@ -273,6 +368,8 @@ Err peel_level_mixed(hm_ctx *c, int level, bool leaf) {
                                                      xo.as<int64_t>(), X.as<float>());
             count_launch();
             HM_LAUNCH("peel_x32");
+            HM_TRY(alloc(T, std::max<int64_t>(nslots[i], 1) * r * cols * sizeof(float)));
+            HM_TRY(alloc(live, std::max<int64_t>(nslots[i], 1)));
             pm::Coarse co;
             co.ent = cj.ent.as<int>();
             co.pt2ent = cj.pt2ent.as<int>();
@@ -289,33 +386,40 @@ Err peel_level_mixed(hm_ctx *c, int level, bool leaf) {
             co.B = f.B32.as<float>();
             co.xoff = xo.as<int64_t>();
             co.X = X.as<float>();
+            co.base = bases[i].as<int64_t>();
+            co.T = T.as<float>();
+            co.live = live.as<unsigned char>();
+            if (nslots[i] > 0) {
+                const int64_t ncomb = (int64_t)cj.nc * chi;
+                const size_t smem = (size_t)pm::WARPS * r * cols * sizeof(float);
+                HM_CUDA(cudaFuncSetAttribute(pm::k_peel_T, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+                pm::k_peel_T<<<ceil_div(ncomb, pm::WARPS), pm::WARPS * 32, smem, st>>>(
+                    co, ncomb, chi, side, cols, r, cl.pt2ent.as<int>(), g.act_ptr.as<int>(), g.act_box.as<int>());
+                count_launch();
+                HM_LAUNCH("peel_T");
+            }
             tab.push_back(co);
-            xs.push_back(std::move(X));
-            xoffs.push_back(std::move(xo));
+            keep.push_back(std::move(X));
+            keep.push_back(std::move(xo));
+            keep.push_back(std::move(T));
+            keep.push_back(std::move(live));
         }
-        if (tab.empty()) continue;
         DBuf tabd;
         HM_TRY(alloc(tabd, tab.size() * sizeof(pm::Coarse)));
         HM_CUDA(cudaMemcpyAsync(tabd.p, tab.data(), tab.size() * sizeof(pm::Coarse), cudaMemcpyHostToDevice, st));
         double *OUT = side ? c->cur.Z.as<double>() : c->cur.Y.as<double>();
-        const int grid = ceil_div(nitems, pm::WARPS);
-        if (cols <= 32) {
-            const size_t smem = (size_t)pm::WARPS * 2 * r * 32 * sizeof(float);
-            HM_CUDA(cudaFuncSetAttribute(pm::k_peel_warp<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            pm::k_peel_warp<32><<<grid, pm::WARPS * 32, smem, st>>>(
-                tabd.as<pm::Coarse>(), (int)tab.size(), side, g.pair_alpha.as<int>(), g.pair_color.as<int>(),
-                cl.ent.as<int>(), cl.pt2ent.as<int>(), g.act_ptr.as<int>(), g.act_box.as<int>(), item_tile.as<int64_t>(),
-                item_row.as<int>(), nitems, cols, r, n, OUT);
-        } else {
-            const size_t smem = (size_t)pm::WARPS * 2 * r * 64 * sizeof(float);
-            HM_CUDA(cudaFuncSetAttribute(pm::k_peel_warp<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            pm::k_peel_warp<64><<<grid, pm::WARPS * 32, smem, st>>>(
-                tabd.as<pm::Coarse>(), (int)tab.size(), side, g.pair_alpha.as<int>(), g.pair_color.as<int>(),
-                cl.ent.as<int>(), cl.pt2ent.as<int>(), g.act_ptr.as<int>(), g.act_box.as<int>(), item_tile.as<int64_t>(),
-                item_row.as<int>(), nitems, cols, r, n, OUT);
+        if (nitems > 0) {
+            if (cols <= 32)
+                pm::k_peel_gemm<32><<<(unsigned)nitems, 128, 0, st>>>(
+                    tabd.as<pm::Coarse>(), (int)tab.size(), side, chi, g.pair_alpha.as<int>(), g.pair_color.as<int>(),
+                    cl.ent.as<int>(), item_tile.as<int64_t>(), item_row.as<int>(), nitems, cols, r, n, OUT);
+            else
+                pm::k_peel_gemm<64><<<(unsigned)nitems, 128, 0, st>>>(
+                    tabd.as<pm::Coarse>(), (int)tab.size(), side, chi, g.pair_alpha.as<int>(), g.pair_color.as<int>(),
+                    cl.ent.as<int>(), item_tile.as<int64_t>(), item_row.as<int>(), nitems, cols, r, n, OUT);
+            count_launch();
+            HM_LAUNCH("peel_gemm");
         }
-        count_launch();
-        HM_LAUNCH("peel_warp");
     }
     return ok();
 }
