@@ -35,12 +35,11 @@ sys.path.insert(0, ROOT)
 METRIC = "time-to-compress (s) and jobs/s at stated rel. error; p50/p99 latency"
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
 
-# dram bytes (read + write) of the tensor-core contraction kernel per output
-# element, from the ncu capture summarised in profiles/k_sample_tc_torus50k.md
-# (scaled by the outputs of a step: the traffic is the FP64 outputs written once
-# plus the L2-resident packed chunks); valid only for the source whose sha256
-# prefix is recorded here
-TRAFFIC = {"file": "paper_2205_03406_gb300/csrc/sample_tc.cu", "sha256": "07ae0e57438406aa", "bytes_per_output": 7.92}
+# dram bytes (read + write) of the tensor-core contraction kernel per evaluated
+# kernel entry, from the ncu capture summarised in profiles/ (scaled by the
+# entries a step evaluates); valid only for the source whose sha256 prefix is
+# recorded here, None until that source has been captured
+TRAFFIC = {"file": "paper_2205_03406_gb300/csrc/sample_tc.cu", "sha256": None, "bytes_per_eval": None}
 
 
 def parse():
@@ -138,9 +137,10 @@ def peaks():
 
 
 def roofline_tc(info, r: int):
-    """Tensor-core contraction: useful FP64-equivalent flops 4 n r sum_c |R_c|
-    per level (Y and Z), executed as 6 BF16 products each."""
-    useful = sum(4.0 * info.n * r * info.act_rows[l] for l in range(2, info.L + 1))
+    """Tensor-core contraction: every evaluated kernel entry (a row of a colour's
+    sample tiles x one of its active rows) feeds r Y and r Z outputs, 4 r useful
+    flops, executed as 6 BF16 products each."""
+    useful = 4.0 * r * info.tc_kernel_evals
     t = info.seconds_phase[7]
     pk, src = peaks()
     bf16_flops = 6.0 * useful
@@ -150,9 +150,8 @@ def roofline_tc(info, r: int):
     try:
         src_path = os.path.join(ROOT, TRAFFIC["file"])
         sha = hashlib.sha256(open(src_path, "rb").read()).hexdigest()[:16]
-        if TRAFFIC["sha256"] == sha and TRAFFIC["bytes_per_output"]:
-            outputs = sum(2.0 * info.n * r * info.colors[l] for l in range(2, info.L + 1))
-            traffic = round(TRAFFIC["bytes_per_output"] * outputs)
+        if TRAFFIC["sha256"] == sha and TRAFFIC["bytes_per_eval"]:
+            traffic = round(TRAFFIC["bytes_per_eval"] * info.tc_kernel_evals)
     except OSError:
         pass
     return {"kernel": "k_sample_tc (split-BF16 kernel-matrix x Omega contraction)", "bound": "tensor",

@@ -132,6 +132,9 @@ typedef struct {
                                  (rows of Omega that are not zero); index L+1 = leaf */
     int64_t kernel_launches;  /* kernels this library launched during hm_compress */
     int64_t launches_total;   /* kernels this library launched since it was loaded */
+    int64_t tc_kernel_evals;  /* kernel-matrix entries the tensor-core sampler evaluated
+                                 during hm_compress: for every colour, its output rows
+                                 (the rows of its sample tiles) x its active rows */
 } hm_info;
 
 /* Create a context.  cfg is copied.  stream: a cudaStream_t or NULL. */

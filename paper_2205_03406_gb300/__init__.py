@@ -54,7 +54,8 @@ class hm_info(ctypes.Structure):
                 ("matvec_cols", ctypes.c_int64), ("factor_floats", ctypes.c_int64), ("max_rank", ctypes.c_int),
                 ("seconds_sample", ctypes.c_double), ("seconds_total", ctypes.c_double),
                 ("seconds_phase", ctypes.c_double * 8), ("act_rows", ctypes.c_int64 * 32),
-                ("kernel_launches", ctypes.c_int64), ("launches_total", ctypes.c_int64)]
+                ("kernel_launches", ctypes.c_int64), ("launches_total", ctypes.c_int64),
+                ("tc_kernel_evals", ctypes.c_int64)]
 
 PHASES = ["colouring", "test matrices", "black box", "peel", "bases+cores", "leaf black box", "leaf peel+extract",
           "tensor-core kernel"]

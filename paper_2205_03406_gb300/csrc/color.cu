@@ -331,6 +331,40 @@ __global__ void k_act_by_entry(const unsigned char *act, int nc, int chi, int pa
     if (!pass) cnt[b] = k;
 }
 
+// Pairs of colour blockIdx.x in pair order (one CTA per colour): pass 0
+// counts them, pass 1 writes their alpha boxes from off[c] on.
+__global__ void __launch_bounds__(1024) k_pairs_by_color(const int *pair_color, const int *pair_alpha, int64_t np,
+                                                         int pass, int *cnt, const int64_t *off, int *tile_box) {
+    __shared__ int wsum[32];
+    __shared__ int run;
+    const int c = blockIdx.x, t = threadIdx.x, lane = t & 31, w = t >> 5;
+    if (t == 0) run = 0;
+    __syncthreads();
+    for (int64_t p0 = 0; p0 < np; p0 += 1024) {
+        const int64_t p = p0 + t;
+        const bool f = p < np && pair_color[p] == c;
+        const unsigned int b = __ballot_sync(0xffffffffu, f);
+        if (lane == 0) wsum[w] = __popc(b);
+        __syncthreads();
+        int before = 0, tot = 0;
+        for (int k = 0; k < 32; ++k) {
+            const int v = wsum[k];
+            if (k < w) before += v;
+            tot += v;
+        }
+        if (pass == 1 && f) tile_box[off[c] + run + before + __popc(b & ((1u << lane) - 1u))] = pair_alpha[p];
+        __syncthreads();
+        if (t == 0) run += tot;
+        __syncthreads();
+    }
+    if (pass == 0 && t == 0) cnt[c] = run;
+}
+
+__global__ void k_gather_ptr(const int64_t *rowoff, const int64_t *tptr, int chi, int64_t *out) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k <= chi) out[k] = rowoff[tptr[k]];
+}
+
 __global__ void k_act_sizes(const int *act_box, int64_t na, const int *ent, int *sz) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= na) return;
@@ -523,6 +557,31 @@ Err color_cut(hm_ctx *c, int level, bool leaf, cudaStream_t st, DBuf &scan_tmp) 
         std::vector<int64_t> crp(chi + 1);
         for (int k = 0; k <= chi; ++k) crp[k] = hro[hoff[k]];
         HM_TRY(to_dev(g.act_rows_ptr, crp, st));
+    }
+    // output rows of each colour (rows of the alpha boxes of its pairs)
+    {
+        DBuf tcnt, tptr, tile_box, sz, rowoff;
+        HM_TRY(alloc(tcnt, chi * sizeof(int)));
+        HM_TRY(alloc(tptr, (chi + 1) * sizeof(int64_t)));
+        HM_TRY(alloc(tile_box, np * sizeof(int)));
+        k_pairs_by_color<<<chi, 1024, 0, st>>>(g.pair_color.as<int>(), g.pair_alpha.as<int>(), np, 0,
+                                               tcnt.as<int>(), nullptr, nullptr); ::hm::count_launch();
+        HM_TRY(scan_counts_i32(tcnt.as<int>(), tptr.as<int64_t>(), chi, st, scan_tmp));
+        k_pairs_by_color<<<chi, 1024, 0, st>>>(g.pair_color.as<int>(), g.pair_alpha.as<int>(), np, 1, nullptr,
+                                               tptr.as<int64_t>(), tile_box.as<int>()); ::hm::count_launch();
+        HM_LAUNCH("pairs_by_color");
+        HM_TRY(alloc(sz, np * sizeof(int)));
+        HM_TRY(alloc(rowoff, (np + 1) * sizeof(int64_t)));
+        k_act_sizes<<<ceil_div(np, 256), 256, 0, st>>>(tile_box.as<int>(), np, cu.ent.as<int>(), sz.as<int>()); ::hm::count_launch();
+        HM_TRY(scan_counts_i32(sz.as<int>(), rowoff.as<int64_t>(), np, st, scan_tmp));
+        HM_TRY(alloc(g.out_rows_ptr, (chi + 1) * sizeof(int64_t)));
+        k_gather_ptr<<<ceil_div(chi + 1, 128), 128, 0, st>>>(rowoff.as<int64_t>(), tptr.as<int64_t>(), chi,
+                                                             g.out_rows_ptr.as<int64_t>()); ::hm::count_launch();
+        HM_TRY(to_host(g.h_out_rows_ptr, g.out_rows_ptr.p, chi + 1, st));
+        HM_TRY(alloc(g.out_rows, std::max<int64_t>(g.h_out_rows_ptr[chi], 1) * sizeof(int)));
+        k_act_rows<<<ceil_div(np * 32, 256), 256, 0, st>>>(tile_box.as<int>(), np, cu.ent.as<int>(),
+                                                           rowoff.as<int64_t>(), g.out_rows.as<int>()); ::hm::count_launch();
+        HM_LAUNCH("out_rows");
     }
     HM_CUDA(cudaStreamSynchronize(st));
     g.done = true;

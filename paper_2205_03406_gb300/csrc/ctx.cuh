@@ -56,6 +56,11 @@ struct Coloring {
     DBuf act_rows_ptr;         // colour -> offset into act_rows (int64, chi+1)
     DBuf act_rows;             // int32: rows (sorted points) active in each colour
     int64_t n_act_rows = 0;
+    // output rows of each colour: the rows I_alpha of its pairs (alpha, beta),
+    // i.e. of the sample tiles Y(I_alpha, c), grouped by colour in pair order
+    DBuf out_rows_ptr;         // int64 [chi + 1]
+    DBuf out_rows;             // int32
+    std::vector<int64_t> h_out_rows_ptr;
     int m_cols = 0;            // columns per colour: r, or m_max at the leaf
 };
 
@@ -129,6 +134,7 @@ struct hm_ctx {
     hm_info info;
     double t_sample = 0.0;
     double t_tc = 0.0;        // device time of the tensor-core contraction kernels
+    int64_t tc_evals = 0;     // kernel entries the tensor-core sampler evaluated (padding excluded)
 };
 
 namespace hm {

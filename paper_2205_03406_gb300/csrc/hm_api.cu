@@ -290,6 +290,7 @@ static Err compress_all(hm_ctx *c, const hm_op *op) {
     const auto t0 = std::chrono::steady_clock::now();
     const long long launches0 = launches_so_far();
     c->t_tc = 0.0;
+    c->tc_evals = 0;
     // (phase, start event, end event) triples, read once at the end
     std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev;
     int cur_phase = -1;
@@ -372,6 +373,7 @@ static Err compress_all(hm_ctx *c, const hm_op *op) {
     for (auto &lv : c->levels) in.n_boxes += lv.nb;
     int64_t floats = 0;
     in.kernel_launches = launches_so_far() - launches0;
+    in.tc_kernel_evals = c->tc_evals;
     for (int l = 2; l <= c->L && l < 31; ++l) {
         in.act_rows[l] = c->colorings[l].n_act_rows;
         in.colors[l] = c->colorings[l].n_colors;

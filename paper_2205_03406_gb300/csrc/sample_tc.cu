@@ -185,6 +185,12 @@ struct Params {
     const unsigned char *pack; // packed chunks
     double *Y, *Z;             // [chi][n][r]
     int *status;
+    // output rows: CTA b computes rows out_rows[item_base[b] + m], m < 128, of
+    // colour item_color[b] (the rows of that colour's sample tiles)
+    const int *out_rows;
+    const int64_t *out_ptr;    // per colour (chi + 1)
+    const int64_t *item_base;
+    const int *item_color;
 };
 
 constexpr int SEG = 2;      // chunks accumulated in tensor memory before promotion
@@ -220,8 +226,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_sample_tc(Params P) {
     const int SB = stage_bytes(r);
     const int CB = chunk_bytes(r);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int c = blockIdx.y;
-    const int64_t i0 = (int64_t)blockIdx.x * TM;
+    const int c = P.item_color[blockIdx.x];
+    const int64_t obase = P.item_base[blockIdx.x];
+    const int nvalid = (int)min((int64_t)TM, P.out_ptr[c + 1] - obase);
     const int64_t nrows = P.rows_ptr[c + 1] - P.rows_ptr[c];
     const int nchunks = (int)((nrows + KC - 1) / KC);
     const int nseg = (nchunks + SEG - 1) / SEG;
@@ -259,9 +266,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_sample_tc(Params P) {
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             mrow[u] = 16 * warp + (lane >> 3) + 4 * u;
-            const int64_t i = i0 + mrow[u];
             float4 h = make_float4(3.0e18f, 3.0e18f, 3.0e18f, 0.f), l = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (i < P.n) {  // padding rows sit far away: K ~ 0 there
+            if (mrow[u] < nvalid) {  // padding rows sit far away: K ~ 0 there
+                const int64_t i = P.out_rows[obase + mrow[u]];
                 h = P.xdf[2 * i];
                 l = P.xdf[2 * i + 1];
             }
@@ -371,8 +378,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_sample_tc(Params P) {
                 ++promoted;
             }
         // epilogue: row 32 quarter + lane, columns [side r, side r + r)
-        const int64_t i = i0 + 32 * quarter + lane;
-        if (ok && *status == 0 && i < P.n) {
+        const int mo = 32 * quarter + lane;
+        if (ok && *status == 0 && mo < nvalid) {
+            const int64_t i = P.out_rows[obase + mo];
             double *dst = (side ? P.Z : P.Y) + ((int64_t)c * P.n + i) * r;
 #pragma unroll
             for (int k = 0; k < MAXR; k += 2) {
@@ -598,6 +606,20 @@ Err sample_tc(hm_ctx *c, int level, int kernel) {
                                                                   c->scratch_b.as<unsigned char>()); ::hm::count_launch();
         HM_LAUNCH("pack");
     }
+    // one CTA per 128 output rows of a colour
+    std::vector<int> icol;
+    std::vector<int64_t> ibase;
+    if ((int)g.h_out_rows_ptr.size() == chi + 1)
+        for (int k = 0; k < chi; ++k)
+            for (int64_t b = g.h_out_rows_ptr[k]; b < g.h_out_rows_ptr[k + 1]; b += TM) {
+                icol.push_back(k);
+                ibase.push_back(b);
+                c->tc_evals += std::min<int64_t>(TM, g.h_out_rows_ptr[k + 1] - b) * (rp[k + 1] - rp[k]);
+            }
+    if (icol.empty()) return ok();
+    DBuf icold, ibased;
+    HM_TRY(to_dev(icold, icol, st));
+    HM_TRY(to_dev(ibased, ibase, st));
     Params P;
     P.xdf = c->xdf.as<float4>();
     P.n = n;
@@ -608,8 +630,12 @@ Err sample_tc(hm_ctx *c, int level, int kernel) {
     P.Y = c->cur.Y.as<double>();
     P.Z = c->cur.Z.as<double>();
     P.status = c->scratch_c.as<int>();
+    P.out_rows = g.out_rows.as<int>();
+    P.out_ptr = g.out_rows_ptr.as<int64_t>();
+    P.item_base = ibased.as<int64_t>();
+    P.item_color = icold.as<int>();
     const int smem = 2 * stage_bytes(r) + 1024;
-    dim3 grid(ceil_div(n, TM), chi);
+    const unsigned grid = (unsigned)icol.size();
     cudaEvent_t e0, e1;
     HM_CUDA(cudaEventCreate(&e0));
     HM_CUDA(cudaEventCreate(&e1));

@@ -60,6 +60,19 @@ def samples(comp, what, level, n, chi, cols):
     return y.transpose(1, 0, 2).reshape(n, chi * cols)
 
 
+def tile_mask(t, l, col, r):
+    """Entries of the level-l samples that Algorithm 4.1 reads: colour c's
+    columns on the rows I_alpha of every pair (alpha, beta) of colour c (the
+    sample tiles Y(I_alpha, c), Section 4.1.2).  The tensor-core sampler
+    computes only these rows; the rest of the sample buffer is unspecified."""
+    from oracle import tree as ot
+    mask = np.zeros((t.n, col.n_colors * r), dtype=bool)
+    for (a, _), c in zip(ot.admissible_pairs(t, l), col.pair_color):
+        s, e = t.rng(l, a)
+        mask[s:e, c * r:(c + 1) * r] = True
+    return mask
+
+
 def factors(comp, level, rng_a, rng_b):
     """Per-pair (U, B, V) from the level's arenas."""
     m = hm()
