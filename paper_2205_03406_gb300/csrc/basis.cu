@@ -8,6 +8,9 @@
 //       tol times the first; the explicit Q columns are signed so that
 //       R_jj >= 0.  The same kernel factors every Z tile; V of pair
 //       (alpha, beta) is the Q of the Z tile of the pair (beta, alpha).
+//       FP64 mode: one warp per tile up to 256 rows, one CTA per larger tile.
+//       Mixed precision: FP32 in shared memory, one CTA per tile up to
+//       QR32_MAX_ROWS rows (FP64 CTA kernel beyond).
 //  K10  B = (G_alpha^T U)^+ (G_alpha^T Y(I_alpha, c)) (V^T G_beta)^+ with
 //       G_alpha the Psi-side block of alpha and G_beta the Omega-side block of
 //       beta: the three r x k products over the boxes' rows by row-split CTAs
@@ -81,12 +84,13 @@ __global__ void __launch_bounds__(256) k_gram(const int *box, const int *ent, in
 }
 
 constexpr int QR_WARP_ROWS_DECL = 256;
+constexpr int QR32_MAX_ROWS = 1600;  // FP32 shared-memory QR: at most this many rows
 
 // Column-pivoted Householder QR of one tile (m x r, row-major), in place;
 // on exit the first k columns hold Q_k with R_jj >= 0.
 __global__ void __launch_bounds__(256) k_qr_tiles(const int *tile_alpha, const int *tile_beta, const int *tile_color,
                                                   const int *ent, int64_t n, int r, int cap, int rank, double tol,
-                                                  double *Ybase, int *kout) {
+                                                  double *Ybase, int *kout, int min_rows) {
     __shared__ double red[8][64];
     __shared__ double nrm[64], tau[64], beta[64];
     __shared__ int sh_piv, sh_stop;
@@ -94,7 +98,7 @@ __global__ void __launch_bounds__(256) k_qr_tiles(const int *tile_alpha, const i
     const int64_t p = blockIdx.x;
     const int *e = ent + (int64_t)tile_alpha[p] * ENT_FIELDS;
     const int m = e[4] - e[3];
-    if (m <= QR_WARP_ROWS_DECL) return;  // the warp kernel factors this tile
+    if (m <= min_rows) return;  // a warp or shared-memory kernel factors this tile
     double *A = Ybase + ((int64_t)tile_color[p] * n + e[3]) * r;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int *eb = ent + (int64_t)tile_beta[p] * ENT_FIELDS;
@@ -331,6 +335,150 @@ __global__ void __launch_bounds__(128) k_qr_warp(const int *tile_alpha, const in
     if (lane == 0) kout[p] = k;
 }
 
+// Mixed precision: the same pivoted QR in FP32 with the tile in shared memory,
+// one CTA of 128 threads per tile of at most max_rows rows (the samples it
+// factors carry FP32-level rounding already).  Thread t works on column
+// t % RP (RP = 32 for r <= 32, else 64) and on the rows i = t / RP (mod
+// 128 / RP) in the column passes; partial sums over the row groups are added
+// in group order.  Q_k is written back to the FP64 tile.
+__global__ void __launch_bounds__(128) k_qr32(const int *tile_alpha, const int *tile_beta, const int *tile_color,
+                                              const int *ent, int64_t n, int r, int cap, int rank, double tol,
+                                              double *Ybase, int *kout, int max_rows) {
+    extern __shared__ float qa[];  // m x r, leading dimension r
+    __shared__ float red[4][64], wv[64], tau[64], beta[64];
+    __shared__ float sh_sc;
+    __shared__ int sh_piv, sh_stop;
+    const int64_t p = blockIdx.x;
+    const int *e = ent + (int64_t)tile_alpha[p] * ENT_FIELDS;
+    const int m = e[4] - e[3];
+    if (m > max_rows) return;  // the FP64 block kernel factors this tile
+    double *Ag = Ybase + ((int64_t)tile_color[p] * n + e[3]) * r;
+    const int *eb = ent + (int64_t)tile_beta[p] * ENT_FIELDS;
+    const int kmax = min(min(m, eb[4] - eb[3]), min(r, cap));
+    const int t = threadIdx.x;
+    const int RP = r <= 32 ? 32 : 64, NG = 128 / RP;
+    const int cj = t % RP, grp = t / RP;
+    for (int o = t; o < m * r; o += 128) qa[o] = (float)Ag[o];
+    __syncthreads();
+    float n0 = 0.0f;
+    int k = 0;
+    for (int s = 0; s < kmax; ++s) {
+        // exact norms of the trailing columns
+        float a = 0.0f;
+        if (cj >= s && cj < r)
+            for (int i = s + grp; i < m; i += NG) a = fmaf(qa[i * r + cj], qa[i * r + cj], a);
+        red[grp][cj] = a;
+        __syncthreads();
+        if (t == 0) {
+            float best = -1.0f;
+            int piv = s;
+            for (int j = s; j < r; ++j) {
+                float v = 0.0f;
+                for (int g = 0; g < NG; ++g) v += red[g][j];
+                if (v > best) {  // largest norm, lowest column on ties
+                    best = v;
+                    piv = j;
+                }
+            }
+            const float nv = sqrtf(best);
+            if (s == 0) n0 = nv;
+            const int stop = rank > 0 ? (s >= rank) : (!(n0 > 0.0f) || !((double)nv > tol * (double)n0));
+            sh_stop = stop;
+            sh_piv = piv;
+            if (!stop) {
+                const float x0 = qa[s * r + piv];
+                float tt = 0.0f, b = 0.0f, sc = 0.0f;
+                if (nv > 0.0f) {
+                    b = -copysignf(nv, x0);
+                    tt = (b - x0) / b;
+                    sc = 1.0f / (x0 - b);
+                }
+                tau[s] = tt;
+                beta[s] = b;
+                sh_sc = sc;
+            }
+        }
+        __syncthreads();
+        if (sh_stop) break;
+        const int piv = sh_piv;
+        const float sc = sh_sc, ts = tau[s], bs = beta[s];
+        // swap columns s and piv, scale the reflector, set R_ss
+        for (int i = t; i < m; i += 128) {
+            float vs = qa[i * r + s];
+            if (piv != s) {
+                const float vp = qa[i * r + piv];
+                qa[i * r + piv] = vs;
+                vs = vp;
+            }
+            if (i > s) vs *= sc;
+            else if (i == s && bs != 0.0f) vs = bs;
+            qa[i * r + s] = vs;
+        }
+        __syncthreads();
+        // w_j = A(s, j) + sum_{i > s} v_i A(i, j), then A(i, j) -= tau v_i w_j
+        a = 0.0f;
+        if (cj > s && cj < r)
+            for (int i = s + 1 + grp; i < m; i += NG) a = fmaf(qa[i * r + s], qa[i * r + cj], a);
+        red[grp][cj] = a;
+        __syncthreads();
+        if (t > s && t < r) {
+            float w = qa[s * r + t];
+            for (int g = 0; g < NG; ++g) w += red[g][t];
+            wv[t] = w;
+        }
+        __syncthreads();
+        if (cj > s && cj < r) {
+            const float w = ts * wv[cj];
+            for (int i = s + grp; i < m; i += NG) {
+                const float vi = (i == s) ? 1.0f : qa[i * r + s];
+                qa[i * r + cj] -= vi * w;
+            }
+        }
+        __syncthreads();
+        k = s + 1;
+    }
+    // explicit Q_k, backward accumulation of the reflectors
+    for (int j = k - 1; j >= 0; --j) {
+        const float tj = tau[j];
+        if (j < k - 1) {
+            float a = 0.0f;
+            if (cj > j && cj < k)
+                for (int i = j + 1 + grp; i < m; i += NG) a = fmaf(qa[i * r + j], qa[i * r + cj], a);
+            red[grp][cj] = a;
+            __syncthreads();
+            if (t > j && t < k) {
+                float w = qa[j * r + t];
+                for (int g = 0; g < NG; ++g) w += red[g][t];
+                wv[t] = w;
+            }
+            __syncthreads();
+            if (cj > j && cj < k) {
+                const float w = tj * wv[cj];
+                for (int i = j + grp; i < m; i += NG) {
+                    const float vi = (i == j) ? 1.0f : qa[i * r + j];
+                    qa[i * r + cj] -= vi * w;
+                }
+            }
+            __syncthreads();
+        }
+        for (int i = t; i < m; i += 128) {
+            float v;
+            if (i < j) v = 0.0f;
+            else if (i == j) v = 1.0f - tj;
+            else v = -tj * qa[i * r + j];
+            qa[i * r + j] = v;
+        }
+        __syncthreads();
+    }
+    // R_jj >= 0; Q_k back to the FP64 tile
+    for (int o = t; o < m * k; o += 128) {
+        const int i = o / k, j = o % k;
+        const float v = qa[i * r + j];
+        Ag[(int64_t)i * r + j] = (double)(beta[j] < 0.0f ? -v : v);
+    }
+    if (t == 0) kout[p] = k;
+}
+
 __global__ void k_factor_sizes(const int *pair_alpha, const int *pair_col, const int *pairT, const int *kY,
                                const int *kZ, const int *ent, int64_t np, int *kU, int *kV, int64_t *sU, int64_t *sV,
                                int64_t *sB) {
@@ -500,18 +648,32 @@ Err bases_and_cores(hm_ctx *c, int level) {
     HM_TRY(alloc(kY, np * sizeof(int)));
     HM_TRY(alloc(kZ, np * sizeof(int)));
     const int cap = c->cfg.rank > 0 ? r : r - c->cfg.oversample;
-    k_qr_tiles<<<(int)np, 256, 0, st>>>(g.pair_alpha.as<int>(), cu.int_idx.as<int>(), g.pair_color.as<int>(),
-                                        cu.ent.as<int>(), n, r, cap, c->cfg.rank, c->cfg.tol, c->cur.Y.as<double>(),
-                                        kY.as<int>()); ::hm::count_launch();
-    k_qr_warp<<<ceil_div(np, 4), 128, 0, st>>>(g.pair_alpha.as<int>(), cu.int_idx.as<int>(), g.pair_color.as<int>(),
-                                               cu.ent.as<int>(), n, r, cap, c->cfg.rank, c->cfg.tol,
-                                               c->cur.Y.as<double>(), kY.as<int>(), np); ::hm::count_launch();
-    k_qr_tiles<<<(int)np, 256, 0, st>>>(g.pair_alpha.as<int>(), cu.int_idx.as<int>(), g.pair_color.as<int>(),
-                                        cu.ent.as<int>(), n, r, cap, c->cfg.rank, c->cfg.tol, c->cur.Z.as<double>(),
-                                        kZ.as<int>()); ::hm::count_launch();
-    k_qr_warp<<<ceil_div(np, 4), 128, 0, st>>>(g.pair_alpha.as<int>(), cu.int_idx.as<int>(), g.pair_color.as<int>(),
-                                               cu.ent.as<int>(), n, r, cap, c->cfg.rank, c->cfg.tol,
-                                               c->cur.Z.as<double>(), kZ.as<int>(), np); ::hm::count_launch();
+    // tiles up to qr32_rows rows: FP32 shared-memory kernel (mixed precision);
+    // otherwise the FP64 warp kernel for up to QR_WARP_ROWS rows; the FP64
+    // block kernel takes the rest
+    const bool mixed = c->cfg.precision == HM_MIXED_BF16X6;
+    const int qr32_rows = mixed ? std::min(QR32_MAX_ROWS, (200 * 1024) / (4 * r)) : 0;
+    const int small_rows = mixed ? qr32_rows : QR_WARP_ROWS;
+    const size_t qr32_smem = (size_t)std::max(1, std::min(qr32_rows, cu.max_rows)) * r * sizeof(float);
+    if (mixed) HM_CUDA(cudaFuncSetAttribute(k_qr32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)qr32_smem));
+    for (int side = 0; side < 2; ++side) {
+        double *T = side ? c->cur.Z.as<double>() : c->cur.Y.as<double>();
+        int *kk = side ? kZ.as<int>() : kY.as<int>();
+        if (cu.max_rows > small_rows) {
+            k_qr_tiles<<<(int)np, 256, 0, st>>>(g.pair_alpha.as<int>(), cu.int_idx.as<int>(), g.pair_color.as<int>(),
+                                                cu.ent.as<int>(), n, r, cap, c->cfg.rank, c->cfg.tol, T, kk,
+                                                small_rows); ::hm::count_launch();
+        }
+        if (mixed) {
+            k_qr32<<<(int)np, 128, qr32_smem, st>>>(g.pair_alpha.as<int>(), cu.int_idx.as<int>(),
+                                                    g.pair_color.as<int>(), cu.ent.as<int>(), n, r, cap, c->cfg.rank,
+                                                    c->cfg.tol, T, kk, qr32_rows); ::hm::count_launch();
+        } else {
+            k_qr_warp<<<ceil_div(np, 4), 128, 0, st>>>(g.pair_alpha.as<int>(), cu.int_idx.as<int>(),
+                                                       g.pair_color.as<int>(), cu.ent.as<int>(), n, r, cap,
+                                                       c->cfg.rank, c->cfg.tol, T, kk, np); ::hm::count_launch();
+        }
+    }
     HM_LAUNCH("qr_tiles");
     HM_TRY(alloc(f.kU, np * sizeof(int)));
     HM_TRY(alloc(f.kV, np * sizeof(int)));
