@@ -335,51 +335,69 @@ __global__ void __launch_bounds__(128) k_qr_warp(const int *tile_alpha, const in
     if (lane == 0) kout[p] = k;
 }
 
-// Mixed precision: the same pivoted QR in FP32 with the tile in shared memory,
-// one CTA of 128 threads per tile of at most max_rows rows (the samples it
-// factors carry FP32-level rounding already).  Thread t works on column
-// t % RP (RP = 32 for r <= 32, else 64) and on the rows i = t / RP (mod
-// 128 / RP) in the column passes; partial sums over the row groups are added
-// in group order.  Q_k is written back to the FP64 tile.
-__global__ void __launch_bounds__(128) k_qr32(const int *tile_alpha, const int *tile_beta, const int *tile_color,
-                                              const int *ent, int64_t n, int r, int cap, int rank, double tol,
-                                              double *Ybase, int *kout, int max_rows) {
-    extern __shared__ float qa[];  // m x r, leading dimension r
-    __shared__ float red[4][64], wv[64], tau[64], beta[64];
+// ---------------------------------------------------------------------------
+// Mixed precision: FP32 QR with the tile in shared memory (the samples it
+// factors carry FP32-level rounding already).  The CTA's 128 threads work on
+// column t % RP (RP = 32 for r <= 32, else 64) and on the rows i = t / RP
+// (mod 128 / RP) in the column passes; partial sums over the row groups are
+// added in group order.
+// ---------------------------------------------------------------------------
+
+// sum over the rows i >= i0 of a(i, j) b(i, j') for the thread's column, added
+// over the row groups: the result for column t (t < r) is returned to thread t
+__device__ __forceinline__ void col_dots(const float *qa, int m, int r, int i0, int ca, int cb_lo, int cb_hi,
+                                         bool square, float (*red)[64], float *out) {
+    const int t = threadIdx.x, RP = r <= 32 ? 32 : 64, NG = 128 / RP, cj = t % RP, grp = t / RP;
+    float a = 0.0f;
+    if (cj >= cb_lo && cj < cb_hi) {
+        if (square)
+            for (int i = i0 + grp; i < m; i += NG) a = fmaf(qa[i * r + cj], qa[i * r + cj], a);
+        else
+            for (int i = i0 + grp; i < m; i += NG) a = fmaf(qa[i * r + ca], qa[i * r + cj], a);
+    }
+    red[grp][cj] = a;
+    __syncthreads();
+    if (t < r) {
+        float v = 0.0f;
+        for (int g = 0; g < NG; ++g) v += red[g][t];
+        out[t] = v;
+    }
+    __syncthreads();
+}
+
+// A(i, j) -= tau v_i w_j for i >= s, j in (s, jhi); v_s = 1, v_i = A(i, s) below
+__device__ __forceinline__ void reflect(float *qa, int m, int r, int s, int jhi, float ts, const float *wv) {
+    const int t = threadIdx.x, RP = r <= 32 ? 32 : 64, NG = 128 / RP, cj = t % RP, grp = t / RP;
+    if (cj > s && cj < jhi) {
+        const float w = ts * wv[cj];
+        for (int i = s + grp; i < m; i += NG) {
+            const float vi = (i == s) ? 1.0f : qa[i * r + s];
+            qa[i * r + cj] -= vi * w;
+        }
+    }
+    __syncthreads();
+}
+
+// Column-pivoted Householder QR of the m x r shared tile qa (ld r), at most
+// kmax steps, stopping by the rank or tolerance rule; on return columns
+// 0..k-1 hold Q_k with R_jj >= 0, and every thread returns k.
+__device__ int qr32_pivoted(float *qa, int m, int r, int kmax, int rank, double tol) {
+    __shared__ float red[4][64], nrm[64], wv[64], tau[64], beta[64];
     __shared__ float sh_sc;
     __shared__ int sh_piv, sh_stop;
-    const int64_t p = blockIdx.x;
-    const int *e = ent + (int64_t)tile_alpha[p] * ENT_FIELDS;
-    const int m = e[4] - e[3];
-    if (m > max_rows) return;  // the FP64 block kernel factors this tile
-    double *Ag = Ybase + ((int64_t)tile_color[p] * n + e[3]) * r;
-    const int *eb = ent + (int64_t)tile_beta[p] * ENT_FIELDS;
-    const int kmax = min(min(m, eb[4] - eb[3]), min(r, cap));
     const int t = threadIdx.x;
-    const int RP = r <= 32 ? 32 : 64, NG = 128 / RP;
-    const int cj = t % RP, grp = t / RP;
-    for (int o = t; o < m * r; o += 128) qa[o] = (float)Ag[o];
-    __syncthreads();
     float n0 = 0.0f;
     int k = 0;
     for (int s = 0; s < kmax; ++s) {
-        // exact norms of the trailing columns
-        float a = 0.0f;
-        if (cj >= s && cj < r)
-            for (int i = s + grp; i < m; i += NG) a = fmaf(qa[i * r + cj], qa[i * r + cj], a);
-        red[grp][cj] = a;
-        __syncthreads();
+        col_dots(qa, m, r, s, 0, s, r, true, red, nrm);  // exact norms of the trailing columns
         if (t == 0) {
             float best = -1.0f;
             int piv = s;
-            for (int j = s; j < r; ++j) {
-                float v = 0.0f;
-                for (int g = 0; g < NG; ++g) v += red[g][j];
-                if (v > best) {  // largest norm, lowest column on ties
-                    best = v;
+            for (int j = s; j < r; ++j)
+                if (nrm[j] > best) {  // largest norm, lowest column on ties
+                    best = nrm[j];
                     piv = j;
                 }
-            }
             const float nv = sqrtf(best);
             if (s == 0) n0 = nv;
             const int stop = rank > 0 ? (s >= rank) : (!(n0 > 0.0f) || !((double)nv > tol * (double)n0));
@@ -416,50 +434,20 @@ __global__ void __launch_bounds__(128) k_qr32(const int *tile_alpha, const int *
         }
         __syncthreads();
         // w_j = A(s, j) + sum_{i > s} v_i A(i, j), then A(i, j) -= tau v_i w_j
-        a = 0.0f;
-        if (cj > s && cj < r)
-            for (int i = s + 1 + grp; i < m; i += NG) a = fmaf(qa[i * r + s], qa[i * r + cj], a);
-        red[grp][cj] = a;
+        col_dots(qa, m, r, s + 1, s, s + 1, r, false, red, wv);
+        if (t > s && t < r) wv[t] += qa[s * r + t];
         __syncthreads();
-        if (t > s && t < r) {
-            float w = qa[s * r + t];
-            for (int g = 0; g < NG; ++g) w += red[g][t];
-            wv[t] = w;
-        }
-        __syncthreads();
-        if (cj > s && cj < r) {
-            const float w = ts * wv[cj];
-            for (int i = s + grp; i < m; i += NG) {
-                const float vi = (i == s) ? 1.0f : qa[i * r + s];
-                qa[i * r + cj] -= vi * w;
-            }
-        }
-        __syncthreads();
+        reflect(qa, m, r, s, r, ts, wv);
         k = s + 1;
     }
     // explicit Q_k, backward accumulation of the reflectors
     for (int j = k - 1; j >= 0; --j) {
         const float tj = tau[j];
         if (j < k - 1) {
-            float a = 0.0f;
-            if (cj > j && cj < k)
-                for (int i = j + 1 + grp; i < m; i += NG) a = fmaf(qa[i * r + j], qa[i * r + cj], a);
-            red[grp][cj] = a;
+            col_dots(qa, m, r, j + 1, j, j + 1, k, false, red, wv);
+            if (t > j && t < k) wv[t] += qa[j * r + t];
             __syncthreads();
-            if (t > j && t < k) {
-                float w = qa[j * r + t];
-                for (int g = 0; g < NG; ++g) w += red[g][t];
-                wv[t] = w;
-            }
-            __syncthreads();
-            if (cj > j && cj < k) {
-                const float w = tj * wv[cj];
-                for (int i = j + grp; i < m; i += NG) {
-                    const float vi = (i == j) ? 1.0f : qa[i * r + j];
-                    qa[i * r + cj] -= vi * w;
-                }
-            }
-            __syncthreads();
+            reflect(qa, m, r, j, k, tj, wv);
         }
         for (int i = t; i < m; i += 128) {
             float v;
@@ -470,13 +458,177 @@ __global__ void __launch_bounds__(128) k_qr32(const int *tile_alpha, const int *
         }
         __syncthreads();
     }
-    // R_jj >= 0; Q_k back to the FP64 tile
-    for (int o = t; o < m * k; o += 128) {
-        const int i = o / k, j = o % k;
-        const float v = qa[i * r + j];
-        Ag[(int64_t)i * r + j] = (double)(beta[j] < 0.0f ? -v : v);
+    for (int o = t; o < m * k; o += 128) {  // R_jj >= 0
+        const int j = o % k;
+        if (beta[j] < 0.0f) qa[(o / k) * r + j] = -qa[(o / k) * r + j];
     }
-    if (t == 0) kout[p] = k;
+    __syncthreads();
+    return k;
+}
+
+// One CTA per tile of at most max_rows rows; Q_k back to the FP64 tile.
+__global__ void __launch_bounds__(128) k_qr32(const int *tile_alpha, const int *tile_beta, const int *tile_color,
+                                              const int *ent, int64_t n, int r, int cap, int rank, double tol,
+                                              double *Ybase, int *kout, int max_rows) {
+    extern __shared__ float qa[];  // m x r, leading dimension r
+    const int64_t p = blockIdx.x;
+    const int *e = ent + (int64_t)tile_alpha[p] * ENT_FIELDS;
+    const int m = e[4] - e[3];
+    if (m > max_rows) return;  // a tall-skinny or FP64 kernel factors this tile
+    double *Ag = Ybase + ((int64_t)tile_color[p] * n + e[3]) * r;
+    const int *eb = ent + (int64_t)tile_beta[p] * ENT_FIELDS;
+    const int kmax = min(min(m, eb[4] - eb[3]), min(r, cap));
+    for (int o = threadIdx.x; o < m * r; o += 128) qa[o] = (float)Ag[o];
+    __syncthreads();
+    const int k = qr32_pivoted(qa, m, r, kmax, rank, tol);
+    for (int o = threadIdx.x; o < m * k; o += 128) Ag[(int64_t)(o / k) * r + o % k] = (double)qa[(o / k) * r + o % k];
+    if (threadIdx.x == 0) kout[p] = k;
+}
+
+// ---------------------------------------------------------------------------
+// Mixed precision, tall tiles: FP32 tall-skinny QR.  A tile of m rows is cut
+// into nb balanced blocks of at most TS_ROWS rows (blocks of tiles above the
+// shared-memory limit only).  (1) every block: unpivoted Householder QR,
+// A_b = Q_b R_b, the reflectors written over the block, R_b into the stack;
+// (2) every tile: the column-pivoted QR of the stacked R_b (nb r x r) -- the
+// column norms, hence the pivots, the rank and R, are those of the tile --
+// giving Q_S; (3) every block: U_b = Q_b Q_S(block rows, 0:k).
+// ---------------------------------------------------------------------------
+
+__global__ void k_ts_count(const int *tile_alpha, const int *ent, int64_t np, int min_rows, int max_rows, int brows,
+                           int64_t *cnt) {
+    const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (p >= np) return;
+    const int *e = ent + (int64_t)tile_alpha[p] * ENT_FIELDS;
+    const int m = e[4] - e[3];
+    cnt[p] = (m > min_rows && m <= max_rows) ? (m + brows - 1) / brows : 0;
+}
+
+__global__ void k_ts_fill(const int *tile_alpha, const int *ent, const int64_t *off, int64_t np, int64_t *blk_tile,
+                          int *blk_row0, int *blk_rows) {
+    const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (p >= np) return;
+    const int nb = (int)(off[p + 1] - off[p]);
+    if (nb == 0) return;
+    const int *e = ent + (int64_t)tile_alpha[p] * ENT_FIELDS;
+    const int m = e[4] - e[3], per = (m + nb - 1) / nb;
+    for (int b = 0; b < nb; ++b) {
+        blk_tile[off[p] + b] = p;
+        blk_row0[off[p] + b] = b * per;
+        blk_rows[off[p] + b] = min(per, m - b * per);
+    }
+}
+
+// (1) unpivoted QR of one block; R_b (r x r, zero below the diagonal) into
+// the stack at [blk][r][r], the reflectors over the block, tau at [blk][r]
+__global__ void __launch_bounds__(128) k_ts_block(const int *tile_alpha, const int *tile_color, const int *ent,
+                                                  int64_t n, int r, double *Ybase, const int64_t *blk_tile,
+                                                  const int *blk_row0, const int *blk_rows, float *Rstack,
+                                                  float *taus) {
+    extern __shared__ float qa[];
+    __shared__ float red[4][64], nrm[64], wv[64];
+    const int64_t blk = blockIdx.x;
+    const int64_t p = blk_tile[blk];
+    const int *e = ent + (int64_t)tile_alpha[p] * ENT_FIELDS;
+    const int m = blk_rows[blk], t = threadIdx.x;
+    double *Ag = Ybase + ((int64_t)tile_color[p] * n + e[3] + blk_row0[blk]) * r;
+    for (int o = t; o < m * r; o += 128) qa[o] = (float)Ag[o];
+    __syncthreads();
+    const int steps = min(m, r);
+    for (int s = 0; s < steps; ++s) {
+        col_dots(qa, m, r, s, 0, s, s + 1, true, red, nrm);
+        const float nv = sqrtf(nrm[s]), x0 = qa[s * r + s];
+        float ts = 0.0f, b = 0.0f, sc = 0.0f;
+        if (nv > 0.0f) {
+            b = -copysignf(nv, x0);
+            ts = (b - x0) / b;
+            sc = 1.0f / (x0 - b);
+        }
+        for (int i = s + 1 + t; i < m; i += 128) qa[i * r + s] *= sc;
+        __syncthreads();
+        if (t == 0) {
+            taus[blk * r + s] = ts;
+            if (nv > 0.0f) qa[s * r + s] = b;
+        }
+        col_dots(qa, m, r, s + 1, s, s + 1, r, false, red, wv);
+        if (t > s && t < r) wv[t] += qa[s * r + t];
+        __syncthreads();
+        reflect(qa, m, r, s, r, ts, wv);
+    }
+    for (int s = steps + t; s < r; s += 128) taus[blk * r + s] = 0.0f;
+    float *R = Rstack + blk * r * r;
+    for (int o = t; o < r * r; o += 128) {
+        const int i = o / r, j = o % r;
+        R[o] = (i <= j && i < m) ? qa[i * r + j] : 0.0f;
+    }
+    for (int o = t; o < m * r; o += 128) Ag[o] = (double)qa[o];
+}
+
+// (2) pivoted QR of the stacked R_b of one tile, in place in the stack
+__global__ void __launch_bounds__(128) k_ts_top(const int *tile_alpha, const int *tile_beta, const int *ent,
+                                                int64_t np, int r, int cap, int rank, double tol, const int64_t *off,
+                                                float *Rstack, int *kout) {
+    extern __shared__ float qa[];
+    const int64_t p = blockIdx.x;
+    const int nb = (int)(off[p + 1] - off[p]);
+    if (nb == 0) return;
+    const int *e = ent + (int64_t)tile_alpha[p] * ENT_FIELDS, *eb = ent + (int64_t)tile_beta[p] * ENT_FIELDS;
+    const int m = e[4] - e[3], ms = nb * r;
+    const int kmax = min(min(m, eb[4] - eb[3]), min(r, cap));
+    float *S = Rstack + off[p] * r * r;
+    for (int o = threadIdx.x; o < ms * r; o += 128) qa[o] = S[o];
+    __syncthreads();
+    const int k = qr32_pivoted(qa, ms, r, kmax, rank, tol);
+    for (int o = threadIdx.x; o < ms * r; o += 128) S[o] = qa[o];
+    if (threadIdx.x == 0) kout[p] = k;
+}
+
+// (3) U_b = Q_b [Q_S(block rows, 0:k); 0] into the block's rows, columns 0..k-1
+__global__ void __launch_bounds__(128) k_ts_form(const int *tile_alpha, const int *tile_color, const int *ent,
+                                                 int64_t n, int r, double *Ybase, const int64_t *blk_tile,
+                                                 const int *blk_row0, const int *blk_rows, const float *Rstack,
+                                                 const float *taus, const int *kout) {
+    extern __shared__ float qa[];  // reflectors m x r, then X m x k (ld r)
+    __shared__ float red[4][64], wv[64];
+    const int64_t blk = blockIdx.x;
+    const int64_t p = blk_tile[blk];
+    const int k = kout[p];
+    if (k == 0) return;
+    const int *e = ent + (int64_t)tile_alpha[p] * ENT_FIELDS;
+    const int m = blk_rows[blk], t = threadIdx.x;
+    double *Ag = Ybase + ((int64_t)tile_color[p] * n + e[3] + blk_row0[blk]) * r;
+    float *X = qa + m * r;
+    const float *QS = Rstack + blk * r * r;  // this block's r rows of Q_S
+    for (int o = t; o < m * r; o += 128) {
+        const int i = o / r, j = o % r;
+        qa[o] = (float)Ag[o];
+        X[o] = (j < k && i < r) ? QS[i * r + j] : 0.0f;
+    }
+    __syncthreads();
+    const int steps = min(m, r);
+    for (int s = steps - 1; s >= 0; --s) {
+        const float ts = taus[blk * r + s];
+        // w_c = X(s, c) + sum_{i > s} v_i X(i, c); X(i, c) -= tau v_i w_c
+        const int RP = r <= 32 ? 32 : 64, NG = 128 / RP, cj = t % RP, grp = t / RP;
+        float a = 0.0f;
+        if (cj < k)
+            for (int i = s + 1 + grp; i < m; i += NG) a = fmaf(qa[i * r + s], X[i * r + cj], a);
+        red[grp][cj] = a;
+        __syncthreads();
+        if (t < k) {
+            float w = X[s * r + t];
+            for (int g = 0; g < NG; ++g) w += red[g][t];
+            wv[t] = ts * w;
+        }
+        __syncthreads();
+        if (cj < k)
+            for (int i = s + grp; i < m; i += NG) {
+                const float vi = (i == s) ? 1.0f : qa[i * r + s];
+                X[i * r + cj] -= vi * wv[cj];
+            }
+        __syncthreads();
+    }
+    for (int o = t; o < m * k; o += 128) Ag[(int64_t)(o / k) * r + o % k] = (double)X[(o / k) * r + o % k];
 }
 
 __global__ void k_factor_sizes(const int *pair_alpha, const int *pair_col, const int *pairT, const int *kY,
@@ -648,14 +800,47 @@ Err bases_and_cores(hm_ctx *c, int level) {
     HM_TRY(alloc(kY, np * sizeof(int)));
     HM_TRY(alloc(kZ, np * sizeof(int)));
     const int cap = c->cfg.rank > 0 ? r : r - c->cfg.oversample;
-    // tiles up to qr32_rows rows: FP32 shared-memory kernel (mixed precision);
-    // otherwise the FP64 warp kernel for up to QR_WARP_ROWS rows; the FP64
-    // block kernel takes the rest
+    // Mixed precision: tiles up to qr32_rows rows by the FP32 shared-memory
+    // kernel, tiles up to ts_max rows by the FP32 tall-skinny QR, larger ones
+    // by the FP64 block kernel.  FP64: the warp kernel up to QR_WARP_ROWS rows,
+    // the block kernel beyond.
     const bool mixed = c->cfg.precision == HM_MIXED_BF16X6;
     const int qr32_rows = mixed ? std::min(QR32_MAX_ROWS, (200 * 1024) / (4 * r)) : 0;
-    const int small_rows = mixed ? qr32_rows : QR_WARP_ROWS;
+    const int ts_rows = (200 * 1024) / (8 * r) / 32 * 32;       // rows per tall-skinny block
+    const int ts_max = mixed ? (200 * 1024) / (4 * r * r) * ts_rows : 0;
+    const int small_rows = mixed ? std::max(qr32_rows, ts_max) : QR_WARP_ROWS;
     const size_t qr32_smem = (size_t)std::max(1, std::min(qr32_rows, cu.max_rows)) * r * sizeof(float);
     if (mixed) HM_CUDA(cudaFuncSetAttribute(k_qr32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)qr32_smem));
+    // tall-skinny blocks (the same for the Y and the Z tiles)
+    DBuf ts_cnt, ts_off, blk_tile, blk_row0, blk_rows, rstack, taus;
+    int64_t nblk = 0;
+    int nb_top = 0;
+    if (mixed && cu.max_rows > qr32_rows) {
+        HM_TRY(alloc(ts_cnt, (np + 1) * sizeof(int64_t)));
+        HM_TRY(alloc(ts_off, (np + 1) * sizeof(int64_t)));
+        k_ts_count<<<ceil_div(np, 256), 256, 0, st>>>(g.pair_alpha.as<int>(), cu.ent.as<int>(), np, qr32_rows, ts_max,
+                                                      ts_rows, ts_cnt.as<int64_t>()); ::hm::count_launch();
+        HM_TRY(scan_exclusive(ts_cnt.as<int64_t>(), ts_off.as<int64_t>(), np, st));
+        HM_TRY(read_scalar(nblk, ts_off.as<int64_t>() + np, st));
+        if (nblk > 0) {
+            HM_TRY(alloc(blk_tile, nblk * sizeof(int64_t)));
+            HM_TRY(alloc(blk_row0, nblk * sizeof(int)));
+            HM_TRY(alloc(blk_rows, nblk * sizeof(int)));
+            HM_TRY(alloc(rstack, (size_t)nblk * r * r * sizeof(float)));
+            HM_TRY(alloc(taus, (size_t)nblk * r * sizeof(float)));
+            k_ts_fill<<<ceil_div(np, 256), 256, 0, st>>>(g.pair_alpha.as<int>(), cu.ent.as<int>(), ts_off.as<int64_t>(),
+                                                         np, blk_tile.as<int64_t>(), blk_row0.as<int>(),
+                                                         blk_rows.as<int>()); ::hm::count_launch();
+            HM_LAUNCH("ts_fill");
+            nb_top = ceil_div(std::min(cu.max_rows, ts_max), ts_rows);
+            HM_CUDA(cudaFuncSetAttribute(k_ts_block, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(ts_rows * r * sizeof(float))));
+            HM_CUDA(cudaFuncSetAttribute(k_ts_top, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)((size_t)nb_top * r * r * sizeof(float))));
+            HM_CUDA(cudaFuncSetAttribute(k_ts_form, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(2 * ts_rows * r * sizeof(float))));
+        }
+    }
     for (int side = 0; side < 2; ++side) {
         double *T = side ? c->cur.Z.as<double>() : c->cur.Y.as<double>();
         int *kk = side ? kZ.as<int>() : kY.as<int>();
@@ -665,6 +850,18 @@ Err bases_and_cores(hm_ctx *c, int level) {
                                                 small_rows); ::hm::count_launch();
         }
         if (mixed) {
+            if (nblk > 0) {
+                k_ts_block<<<(unsigned)nblk, 128, ts_rows * r * sizeof(float), st>>>(
+                    g.pair_alpha.as<int>(), g.pair_color.as<int>(), cu.ent.as<int>(), n, r, T, blk_tile.as<int64_t>(),
+                    blk_row0.as<int>(), blk_rows.as<int>(), rstack.as<float>(), taus.as<float>()); ::hm::count_launch();
+                k_ts_top<<<(unsigned)np, 128, (size_t)nb_top * r * r * sizeof(float), st>>>(
+                    g.pair_alpha.as<int>(), cu.int_idx.as<int>(), cu.ent.as<int>(), np, r, cap, c->cfg.rank,
+                    c->cfg.tol, ts_off.as<int64_t>(), rstack.as<float>(), kk); ::hm::count_launch();
+                k_ts_form<<<(unsigned)nblk, 128, 2 * ts_rows * r * sizeof(float), st>>>(
+                    g.pair_alpha.as<int>(), g.pair_color.as<int>(), cu.ent.as<int>(), n, r, T, blk_tile.as<int64_t>(),
+                    blk_row0.as<int>(), blk_rows.as<int>(), rstack.as<float>(), taus.as<float>(), kk); ::hm::count_launch();
+                HM_LAUNCH("tall-skinny qr");
+            }
             k_qr32<<<(int)np, 128, qr32_smem, st>>>(g.pair_alpha.as<int>(), cu.int_idx.as<int>(),
                                                     g.pair_color.as<int>(), cu.ent.as<int>(), n, r, cap, c->cfg.rank,
                                                     c->cfg.tol, T, kk, qr32_rows); ::hm::count_launch();

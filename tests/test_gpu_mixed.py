@@ -33,6 +33,13 @@ def mixed_workloads():
         "grid_log_r40": W.Workload("grid_log", W.grid2d(48), W.K_LOG, leaf_size=32, r=40, rank=20, seed=2),
         "cube_exp_r8": W.Workload("cube_exp", np.random.default_rng(4).random((2100, 3)), W.K_EXP, leaf_size=40,
                                   r=8, rank=4, seed=3),
+        # level-2 tiles of 2000 rows: the tall-skinny QR path (tiles above the
+        # shared-memory limit of the one-CTA kernel).  1/r: with a kernel whose
+        # far field does not decay (log, exp) the peeled tiles of an 8-level 1D
+        # tree are far smaller than the raw samples, and FP32-class sample
+        # rounding alone puts the result 2e-6..6e-6 from the FP64 oracle.
+        "line_tall_r16": W.Workload("line_tall", W.line1d(8000, 11), W.K_INVR, leaf_size=64, r=16, rank=12,
+                                    seed=11),
     }
 
 
