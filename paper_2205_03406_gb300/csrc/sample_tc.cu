@@ -35,8 +35,9 @@ namespace tc {
 
 constexpr int KC = 64;          // rows j per chunk (one 128-byte row of BF16)
 constexpr int TM = 128;         // rows i per tile (MMA M)
-constexpr int NPROD = 256;      // producer threads (8 warps)
-constexpr int NTHREADS = NPROD + 64;  // + MMA warp (8) + TMA warp (9)
+constexpr int NPROD = 512;      // producer threads (16 warps)
+constexpr int PWARPS = NPROD / 32;
+constexpr int NTHREADS = NPROD + 64;  // + MMA warp (16) + TMA warp (17)
 constexpr int A_PIECE = TM * 128;        // bytes of one A piece (16 KB)
 constexpr int COORD_BYTES = KC * 32;     // 64 entries x 8 floats
 constexpr unsigned long long WAIT_NS = 4000000000ull;  // 4 s per wait
@@ -152,6 +153,15 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v) {
     for (int k = 0; k < 16; ++k) v[k] = __uint_as_float(r[k]);
 }
 
+__device__ __forceinline__ void tmem_ld4(uint32_t taddr, float *v) {
+    uint32_t r[4];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(taddr));
+#pragma unroll
+    for (int k = 0; k < 4; ++k) v[k] = __uint_as_float(r[k]);
+}
+
 __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float *v) {
     uint32_t r[8];
     asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
@@ -170,6 +180,44 @@ template <int KIND> __device__ __forceinline__ float kval(float r2) {
     if (KIND == HM_K_LOG) v = __log2f(r2);
     else v = rsqrtf(r2);
     return r2 > 0.0f ? v : 0.0f;
+}
+
+// packed FP32 pairs (f32x2): element 0 in the low word
+__device__ __forceinline__ uint64_t pk2(float lo, float hi) {
+    uint64_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void up2(uint64_t v, float &lo, float &hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ uint64_t sub2(uint64_t a, uint64_t b) {
+    uint64_t r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ uint64_t add2(uint64_t a, uint64_t b) {
+    uint64_t r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ uint64_t mul2(uint64_t a, uint64_t b) {
+    uint64_t r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ uint64_t fma2(uint64_t a, uint64_t b, uint64_t c) {
+    uint64_t r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+// BF16 pair (element 0 in the low half) and its exact FP32 values
+__device__ __forceinline__ uint32_t bf2(float lo, float hi) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t *>(&h);
+}
+__device__ __forceinline__ uint64_t bf2f(uint32_t h) {
+    return pk2(__uint_as_float(h << 16), __uint_as_float(h & 0xFFFF0000u));
 }
 
 __host__ __device__ constexpr double kscale(int kind) {
@@ -194,7 +242,8 @@ struct Params {
 };
 
 constexpr int SEG = 2;      // chunks accumulated in tensor memory before promotion
-constexpr int MAXR = 40;    // largest r (columns per thread in the promotion: r)
+constexpr int MAXR = 40;    // largest r
+constexpr int MAXH = MAXR / 2;  // columns per thread in the promotion: r / 2
 
 // exact FP32 -> FP64 with integer operations (normal numbers; zero and
 // subnormals map to a signed zero), keeping the conversion off the FP64 pipe
@@ -246,7 +295,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_sample_tc(Params P) {
         mbar_init(&accum, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 8) {
+    if (warp == PWARPS) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(
                          smem_u32(&tmem_slot))
                      : "memory");
@@ -258,31 +307,35 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_sample_tc(Params P) {
     const uint32_t tmem = tmem_slot;
     bool ok = true;
 
-    if (warp < 8) {
+    if (warp < PWARPS) {
         // ------------------------------------------------------------ producers
-        const int ck = lane & 7;                  // 16-byte chunk: k in [8 ck, 8 ck + 8)
-        float rx[4][6];                           // double-float coordinates of 4 rows
-        int mrow[4];
+        // rows 16 (warp % 8) + lane / 4 + 8 u (u = 0, 1), columns 8 ck .. 8 ck + 7
+        // (the 16-byte chunk ck = 4 (warp / 8) + lane % 4 of the 128-byte row),
+        // in column pairs
+        const int ck = 4 * (warp >> 3) + (lane & 3);
+        uint64_t RH[2][3], RL[2][3];  // double-float row coordinates, each duplicated in a pair
+        int mrow[2];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            mrow[u] = 16 * warp + (lane >> 3) + 4 * u;
+        for (int u = 0; u < 2; ++u) {
+            mrow[u] = 16 * (warp & 7) + (lane >> 2) + 8 * u;
             float4 h = make_float4(3.0e18f, 3.0e18f, 3.0e18f, 0.f), l = make_float4(0.f, 0.f, 0.f, 0.f);
             if (mrow[u] < nvalid) {  // padding rows sit far away: K ~ 0 there
                 const int64_t i = P.out_rows[obase + mrow[u]];
                 h = P.xdf[2 * i];
                 l = P.xdf[2 * i + 1];
             }
-            rx[u][0] = h.x; rx[u][1] = h.y; rx[u][2] = h.z;
-            rx[u][3] = l.x; rx[u][4] = l.y; rx[u][5] = l.z;
+            RH[u][0] = pk2(h.x, h.x); RH[u][1] = pk2(h.y, h.y); RH[u][2] = pk2(h.z, h.z);
+            RL[u][0] = pk2(l.x, l.x); RL[u][1] = pk2(l.y, l.y); RL[u][2] = pk2(l.z, l.z);
         }
-        // promotion: this thread owns TMEM lane quarter (warp & 3), columns
-        // [side r, side r + r) of the 2r outputs (side 0: Y, side 1: Z)
-        const int quarter = warp & 3, side = warp >> 2;
-        const uint32_t trow = tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(side * r);
+        // promotion: this thread owns TMEM lane quarter (warp & 3) and the
+        // columns [sub r/2, sub r/2 + r/2), sub = warp / 4, of the 2r outputs
+        // (Y: columns 0..r-1, Z: r..2r-1)
+        const int quarter = warp & 3, sub = warp >> 2, hr = r >> 1;
+        const uint32_t trow = tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(sub * hr);
         const float scale = (float)kscale(KIND);
-        float acc_hi[MAXR], acc_lo[MAXR];
+        float acc_hi[MAXH], acc_lo[MAXH];
 #pragma unroll
-        for (int k = 0; k < MAXR; ++k) acc_hi[k] = acc_lo[k] = 0.0f;
+        for (int k = 0; k < MAXH; ++k) acc_hi[k] = acc_lo[k] = 0.0f;
         int promoted = 0;
         auto promote = [&](int sg) -> bool {
             const int set = sg & 1;
@@ -292,71 +345,80 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_sample_tc(Params P) {
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint32_t base = trow + (uint32_t)(set * 6 * r);
 #pragma unroll
-            for (int g = 0; g < MAXR / 8; ++g) {
-                if (8 * g >= r) break;
-                float hh[8], x1[8], x2[8];
-                tmem_ld8(base + 8 * g, hh);
-                tmem_ld8(base + 2 * r + 8 * g, x1);
-                tmem_ld8(base + 4 * r + 8 * g, x2);
+            for (int g = 0; g < MAXH / 4; ++g) {
+                if (4 * g >= hr) break;
+                float hh[4], x1[4], x2[4];
+                tmem_ld4(base + 4 * g, hh);
+                tmem_ld4(base + 2 * r + 4 * g, x1);
+                tmem_ld4(base + 4 * r + 4 * g, x2);
                 tmem_wait_ld();
 #pragma unroll
-                for (int k = 0; k < 8; ++k) {
-                    dfadd(acc_hi[8 * g + k], acc_lo[8 * g + k], hh[k] * scale);
-                    acc_lo[8 * g + k] += (x1[k] + x2[k]) * scale;
+                for (int k = 0; k < 4; ++k) {
+                    dfadd(acc_hi[4 * g + k], acc_lo[4 * g + k], hh[k] * scale);
+                    acc_lo[4 * g + k] += (x1[k] + x2[k]) * scale;
                 }
             }
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             mbar_arrive(&set_free[set]);
             return true;
         };
-        // coordinates: 2 KB per chunk, 8 bytes per producer thread, prefetched
+        // coordinates: 2 KB per chunk, 4 bytes per producer thread, prefetched
         // one chunk ahead into cbuf (producers sync on named barrier 1)
-        const float2 *gcoord = reinterpret_cast<const float2 *>(gpack + b_bytes(r));
-        float2 cnext = make_float2(0.f, 0.f);
-        if (nchunks > 0) reinterpret_cast<float2 *>(cbuf[0])[tid] = gcoord[tid];
+        const float *gcoord = reinterpret_cast<const float *>(gpack + b_bytes(r));
+        float cnext = 0.f;
+        if (nchunks > 0) reinterpret_cast<float *>(cbuf[0])[tid] = gcoord[tid];
         asm volatile("bar.sync 1, %0;" ::"n"(NPROD) : "memory");
         // every producer runs every named barrier; after an error it only
         // skips the work, so no warp can be left waiting at bar.sync
         for (int q = 0; q < nchunks; ++q) {
             const int s = q & 1;
             const uint32_t u = (uint32_t)(q >> 1);
-            if (q + 1 < nchunks) cnext = reinterpret_cast<const float2 *>(gpack + (size_t)(q + 1) * CB + b_bytes(r))[tid];
+            if (q + 1 < nchunks) cnext = reinterpret_cast<const float *>(gpack + (size_t)(q + 1) * CB + b_bytes(r))[tid];
             if (ok && q >= 2) ok = mbar_wait(&empty[s], (u - 1) & 1, status);
             ok = __all_sync(0xffffffffu, ok);
             if (ok) {
                 unsigned char *st = smem + s * SB;
-                const float4 *cd = cbuf[q & 1];
-                float kv[4][8];
+                // column pair (ck, e2): 16-byte slots ((3 e2 + j) 8 + ck), j = 0..2:
+                // (hx hx' hy hy'), (hz hz' lx lx'), (ly ly' lz lz') -- the 4 chunks a
+                // warp reads sit in consecutive slots (one wavefront per load)
+                const ulonglong2 *cp = reinterpret_cast<const ulonglong2 *>(cbuf[q & 1]);
+                uint64_t kv[2][4];  // K of the thread's 2 rows x 4 column pairs
 #pragma unroll
-                for (int e = 0; e < 8; ++e) {
-                    const float4 ch = cd[(8 * ck + e) * 2], cl = cd[(8 * ck + e) * 2 + 1];
+                for (int e2 = 0; e2 < 4; ++e2) {
+                    const ulonglong2 q0 = cp[(3 * e2) * 8 + ck], q1 = cp[(3 * e2 + 1) * 8 + ck],
+                                     q2 = cp[(3 * e2 + 2) * 8 + ck];
 #pragma unroll
-                    for (int uu = 0; uu < 4; ++uu) {
-                        const float dx = (rx[uu][0] - ch.x) + (rx[uu][3] - cl.x);
-                        const float dy = (rx[uu][1] - ch.y) + (rx[uu][4] - cl.y);
-                        const float dz = (rx[uu][2] - ch.z) + (rx[uu][5] - cl.z);
-                        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                        kv[uu][e] = kval<KIND>(r2);
+                    for (int u = 0; u < 2; ++u) {
+                        const uint64_t dx = add2(sub2(RH[u][0], q0.x), sub2(RL[u][0], q1.y));
+                        const uint64_t dy = add2(sub2(RH[u][1], q0.y), sub2(RL[u][1], q2.x));
+                        const uint64_t dz = add2(sub2(RH[u][2], q1.x), sub2(RL[u][2], q2.y));
+                        const uint64_t r2 = fma2(dz, dz, fma2(dy, dy, mul2(dx, dx)));
+                        float a0, a1;
+                        up2(r2, a0, a1);
+                        kv[u][e2] = pk2(kval<KIND>(a0), kval<KIND>(a1));
                     }
                 }
 #pragma unroll
-                for (int uu = 0; uu < 4; ++uu) {
-                    const int m = mrow[uu];
-                    const int off = (m >> 3) * 1024 + (m & 7) * 128 + ((ck ^ (m & 7)) << 4);
+                for (int u = 0; u < 2; ++u) {
+                    const int m = mrow[u];
                     uint32_t ph[4], pm[4], pl[4];
 #pragma unroll
                     for (int e2 = 0; e2 < 4; ++e2) {
-                        const float v0 = kv[uu][2 * e2], v1 = kv[uu][2 * e2 + 1];
-                        const __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
-                        const float2 hf = __bfloat1622float2(h);
-                        const float r0 = v0 - hf.x, r1 = v1 - hf.y;
-                        const __nv_bfloat162 mm = __floats2bfloat162_rn(r0, r1);
-                        const float2 mf = __bfloat1622float2(mm);
-                        const __nv_bfloat162 ll = __floats2bfloat162_rn(r0 - mf.x, r1 - mf.y);
-                        ph[e2] = *reinterpret_cast<const uint32_t *>(&h);
-                        pm[e2] = *reinterpret_cast<const uint32_t *>(&mm);
-                        pl[e2] = *reinterpret_cast<const uint32_t *>(&ll);
+                        // three-piece BF16 split of the pair: v = h + m + l
+                        const uint64_t v = kv[u][e2];
+                        float v0, v1;
+                        up2(v, v0, v1);
+                        ph[e2] = bf2(v0, v1);
+                        const uint64_t rr = sub2(v, bf2f(ph[e2]));
+                        float r0, r1;
+                        up2(rr, r0, r1);
+                        pm[e2] = bf2(r0, r1);
+                        const uint64_t ll = sub2(rr, bf2f(pm[e2]));
+                        float l0, l1;
+                        up2(ll, l0, l1);
+                        pl[e2] = bf2(l0, l1);
                     }
+                    const int off = (m >> 3) * 1024 + (m & 7) * 128 + ((ck ^ (m & 7)) << 4);
                     *reinterpret_cast<uint4 *>(st + off) = make_uint4(ph[0], ph[1], ph[2], ph[3]);
                     *reinterpret_cast<uint4 *>(st + A_PIECE + off) = make_uint4(pm[0], pm[1], pm[2], pm[3]);
                     *reinterpret_cast<uint4 *>(st + 2 * A_PIECE + off) = make_uint4(pl[0], pl[1], pl[2], pl[3]);
@@ -369,7 +431,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_sample_tc(Params P) {
                     ++promoted;
                 }
             }
-            if (q + 1 < nchunks) reinterpret_cast<float2 *>(cbuf[(q + 1) & 1])[tid] = cnext;
+            if (q + 1 < nchunks) reinterpret_cast<float *>(cbuf[(q + 1) & 1])[tid] = cnext;
             asm volatile("bar.sync 1, %0;" ::"n"(NPROD) : "memory");
         }
         if (ok)
@@ -377,19 +439,19 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_sample_tc(Params P) {
                 ok = promote(promoted);
                 ++promoted;
             }
-        // epilogue: row 32 quarter + lane, columns [side r, side r + r)
+        // epilogue: row 32 quarter + lane, its r/2 columns
         const int mo = 32 * quarter + lane;
         if (ok && *status == 0 && mo < nvalid) {
             const int64_t i = P.out_rows[obase + mo];
-            double *dst = (side ? P.Z : P.Y) + ((int64_t)c * P.n + i) * r;
+            double *dst = ((sub >> 1) ? P.Z : P.Y) + ((int64_t)c * P.n + i) * r + (sub & 1) * hr;
 #pragma unroll
-            for (int k = 0; k < MAXR; k += 2) {
-                if (k >= r) break;
+            for (int k = 0; k < MAXH; k += 2) {
+                if (k >= hr) break;
                 *reinterpret_cast<double2 *>(dst + k) =
                     make_double2(f2d(acc_hi[k]) + f2d(acc_lo[k]), f2d(acc_hi[k + 1]) + f2d(acc_lo[k + 1]));
             }
         }
-    } else if (warp == 9) {
+    } else if (warp == PWARPS + 1) {
         // ------------------------------------------------------------ TMA issuer
         if (lane == 0) {
             int issued = 0;
@@ -441,7 +503,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_sample_tc(Params P) {
     __syncwarp();
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (warp == 8) {
+    if (warp == PWARPS) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
     }
@@ -507,9 +569,19 @@ __global__ void k_pack_coords(const int64_t *chunk_color_first, int chi, const i
         h = xdf[2 * (int64_t)j];
         l = xdf[2 * (int64_t)j + 1];
     }
-    float4 *dst = reinterpret_cast<float4 *>(pack + (size_t)g * chunk_bytes(r) + b_bytes(r)) + 2 * k;
-    dst[0] = h;
-    dst[1] = l;
+    // column k = 8 ck + 2 e2 + o (o = 0, 1): element o of the pair (ck, e2), whose
+    // three 16-byte slots ((3 e2 + j) 8 + ck), j = 0..2, hold (hx hx' hy hy'),
+    // (hz hz' lx lx'), (ly ly' lz lz'); 1536 of the 2048 bytes are used
+    const int ck = k >> 3, e2 = (k & 7) >> 1, o = k & 1;
+    float *base = reinterpret_cast<float *>(pack + (size_t)g * chunk_bytes(r) + b_bytes(r));
+    float *s0 = base + 4 * ((3 * e2) * 8 + ck) + o, *s1 = base + 4 * ((3 * e2 + 1) * 8 + ck) + o,
+          *s2 = base + 4 * ((3 * e2 + 2) * 8 + ck) + o;
+    s0[0] = h.x;
+    s0[2] = h.y;
+    s1[0] = h.z;
+    s1[2] = l.x;
+    s2[0] = l.y;
+    s2[2] = l.z;
 }
 
 // leaf black box, FP32 kernel values from double-float coordinates, FP64 output:
