@@ -309,15 +309,16 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_sample_tc(Params P) {
 
     if (warp < PWARPS) {
         // ------------------------------------------------------------ producers
-        // rows 16 (warp % 8) + lane / 4 + 8 u (u = 0, 1), columns 8 ck .. 8 ck + 7
-        // (the 16-byte chunk ck = 4 (warp / 8) + lane % 4 of the 128-byte row),
-        // in column pairs
-        const int ck = 4 * (warp >> 3) + (lane & 3);
+        // rows 16 (warp % 8) + lane % 8 + 8 u (u = 0, 1), columns 8 ck .. 8 ck + 7
+        // (the 16-byte chunk ck = 4 (warp / 8) + lane / 8 of the 128-byte row),
+        // in column pairs.  The 8 lanes of a quarter-warp store 8 rows of one
+        // chunk: with the 128-byte swizzle they hit 8 distinct bank groups.
+        const int ck = 4 * (warp >> 3) + (lane >> 3);
         uint64_t RH[2][3], RL[2][3];  // double-float row coordinates, each duplicated in a pair
         int mrow[2];
 #pragma unroll
         for (int u = 0; u < 2; ++u) {
-            mrow[u] = 16 * (warp & 7) + (lane >> 2) + 8 * u;
+            mrow[u] = 16 * (warp & 7) + (lane & 7) + 8 * u;
             float4 h = make_float4(3.0e18f, 3.0e18f, 3.0e18f, 0.f), l = make_float4(0.f, 0.f, 0.f, 0.f);
             if (mrow[u] < nvalid) {  // padding rows sit far away: K ~ 0 there
                 const int64_t i = P.out_rows[obase + mrow[u]];
@@ -380,7 +381,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_sample_tc(Params P) {
                 unsigned char *st = smem + s * SB;
                 // column pair (ck, e2): 16-byte slots ((3 e2 + j) 8 + ck), j = 0..2:
                 // (hx hx' hy hy'), (hz hz' lx lx'), (ly ly' lz lz') -- the 4 chunks a
-                // warp reads sit in consecutive slots (one wavefront per load)
+                // warp reads sit in consecutive slots
                 const ulonglong2 *cp = reinterpret_cast<const ulonglong2 *>(cbuf[q & 1]);
                 uint64_t kv[2][4];  // K of the thread's 2 rows x 4 column pairs
 #pragma unroll
