@@ -22,9 +22,9 @@
  *    cudaStream_t passed as void*; NULL = the legacy default stream).  Calls
  *    that return sizes to the host (hm_tree_build, hm_color, hm_compress,
  *    hm_get_info, hm_export) synchronise that stream; the others do not.
- *    hm_compress also colours the levels on a second stream that the context
- *    creates (non-blocking, highest priority), from a host thread of its own,
- *    ahead of the level loop; both have finished when hm_compress returns.
+ *    hm_compress also colours the levels on two more streams that the context
+ *    creates (non-blocking, highest priority), from two host threads of its
+ *    own, ahead of the level loop; all have finished when hm_compress returns.
  *  - The context owns every device buffer it allocates (tree, colourings,
  *    samples, factors); hm_destroy frees them.
  *  - Matrices at the boundary are column-major with leading dimension n and are

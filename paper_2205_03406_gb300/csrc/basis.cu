@@ -29,13 +29,17 @@ namespace hm {
 // G the level's Gaussians [n][r], s0 the first row of box[p], F_p the pair's
 // block: the peeled Y tile of colour color[p] (kdim == nullptr, kf = r) or the
 // packed factor at offF[p] with kf = kdim[p] columns.  A chunk beyond the box
-// writes zeros; the consumer adds the chunks in order.
+// writes zeros; the consumer adds the chunks in order.  T is the type of the
+// products and of the sums over 32-row blocks, TA that of the sums over the
+// blocks and of the output (double and double, or float and float in the
+// mixed-precision mode, whose P, U and V carry FP32-class rounding already).
 constexpr int GRAM_CHUNK = 1024;
 
+template <typename T, typename TA>
 __global__ void __launch_bounds__(256) k_gram(const int *box, const int *ent, int64_t np, int r, const double *G,
                                               const double *F, const int *color, int64_t n, const int64_t *offF,
-                                              const int *kdim, double *out) {
-    __shared__ double gs[32][64], fs[32][64];
+                                              const int *kdim, TA *out) {
+    __shared__ T gs[32][64], fs[32][64];
     const int64_t p = blockIdx.x;
     const int *e = ent + (int64_t)box[p] * ENT_FIELDS;
     const int s0 = e[3], m = e[4] - e[3];
@@ -49,18 +53,18 @@ __global__ void __launch_bounds__(256) k_gram(const int *box, const int *ent, in
         Fp = F + ((int64_t)color[p] * n + s0) * r;
     }
     const int i_begin = blockIdx.y * GRAM_CHUNK, i_end = min(m, i_begin + GRAM_CHUNK);
-    double acc[16];
+    TA acc[16];
 #pragma unroll
-    for (int q = 0; q < 16; ++q) acc[q] = 0.0;
+    for (int q = 0; q < 16; ++q) acc[q] = TA(0);
     for (int i0 = i_begin; i0 < i_end; i0 += 32) {
         const int mm = min(32, i_end - i0);
         for (int o = threadIdx.x; o < 32 * r; o += 256) {
             const int i = o / r, j = o % r;
-            gs[i][j] = (i < mm) ? G[(int64_t)(s0 + i0 + i) * r + j] : 0.0;
+            gs[i][j] = (i < mm) ? (T)G[(int64_t)(s0 + i0 + i) * r + j] : T(0);
         }
         for (int o = threadIdx.x; o < 32 * kf; o += 256) {
             const int i = o / kf, j = o % kf;
-            fs[i][j] = (i < mm) ? Fp[(int64_t)(i0 + i) * kf + j] : 0.0;
+            fs[i][j] = (i < mm) ? (T)Fp[(int64_t)(i0 + i) * kf + j] : T(0);
         }
         __syncthreads();
 #pragma unroll
@@ -68,14 +72,14 @@ __global__ void __launch_bounds__(256) k_gram(const int *box, const int *ent, in
             const int o = threadIdx.x + q * 256;
             if (o < r * kf) {
                 const int a = o / kf, b = o % kf;
-                double sacc = acc[q];
+                T sacc = T(0);  // the 32-row block in T, added to the TA sum
                 for (int i = 0; i < mm; ++i) sacc = fma(gs[i][a], fs[i][b], sacc);
-                acc[q] = sacc;
+                acc[q] += (TA)sacc;
             }
         }
         __syncthreads();
     }
-    double *o_ = out + ((int64_t)blockIdx.y * np + p) * r * r;
+    TA *o_ = out + ((int64_t)blockIdx.y * np + p) * r * r;
 #pragma unroll
     for (int q = 0; q < 16; ++q) {
         const int o = threadIdx.x + q * 256;
@@ -661,28 +665,28 @@ __global__ void k_pack(const int *pair_alpha, const int *pair_col, const int *pa
 // --- warp-level small dense helpers (row-major, leading dimension ld) -------
 
 // Householder QR of A (m x k), R in the upper triangle, v below (v0 = 1).
-__device__ void warp_house_qr(double *A, int m, int k, int ld, double *tau) {
+template <typename T> __device__ void warp_house_qr(T *A, int m, int k, int ld, T *tau) {
     const int lane = threadIdx.x & 31;
     for (int s = 0; s < k; ++s) {
-        double ss = 0.0;
+        T ss = T(0);
         for (int i = s + lane; i < m; i += 32) ss = fma(A[i * ld + s], A[i * ld + s], ss);
         ss = warp_sum(ss);
-        const double x0 = A[s * ld + s], nx = sqrt(ss);
-        double t = 0.0, b = 0.0, sc = 0.0;
-        if (nx > 0.0) {
+        const T x0 = A[s * ld + s], nx = sqrt(ss);
+        T t = T(0), b = T(0), sc = T(0);
+        if (nx > T(0)) {
             b = -copysign(nx, x0);
             t = (b - x0) / b;
-            sc = 1.0 / (x0 - b);
+            sc = T(1) / (x0 - b);
         }
         __syncwarp();
         for (int i = s + 1 + lane; i < m; i += 32) A[i * ld + s] *= sc;
         if (lane == 0) {
             tau[s] = t;
-            if (nx > 0.0) A[s * ld + s] = b;
+            if (nx > T(0)) A[s * ld + s] = b;
         }
         __syncwarp();
         for (int j = s + 1 + lane; j < k; j += 32) {
-            double wv = A[s * ld + j];
+            T wv = A[s * ld + j];
             for (int i = s + 1; i < m; ++i) wv = fma(A[i * ld + s], A[i * ld + j], wv);
             A[s * ld + j] -= t * wv;
             for (int i = s + 1; i < m; ++i) A[i * ld + j] -= t * A[i * ld + s] * wv;
@@ -692,12 +696,13 @@ __device__ void warp_house_qr(double *A, int m, int k, int ld, double *tau) {
 }
 
 // X (m x nc) := Q^T X for the reflectors stored in A (m x k)
-__device__ void warp_apply_qt(const double *A, int m, int k, int lda, const double *tau, double *X, int nc, int ldx) {
+template <typename T>
+__device__ void warp_apply_qt(const T *A, int m, int k, int lda, const T *tau, T *X, int nc, int ldx) {
     const int lane = threadIdx.x & 31;
     for (int s = 0; s < k; ++s) {
-        const double t = tau[s];
+        const T t = tau[s];
         for (int j = lane; j < nc; j += 32) {
-            double wv = X[s * ldx + j];
+            T wv = X[s * ldx + j];
             for (int i = s + 1; i < m; ++i) wv = fma(A[i * lda + s], X[i * ldx + j], wv);
             X[s * ldx + j] -= t * wv;
             for (int i = s + 1; i < m; ++i) X[i * ldx + j] -= t * A[i * lda + s] * wv;
@@ -707,11 +712,11 @@ __device__ void warp_apply_qt(const double *A, int m, int k, int lda, const doub
 }
 
 // X (k x nc) := R^{-1} X, R the k x k upper triangle of A
-__device__ void warp_back_solve(const double *A, int k, int lda, double *X, int nc, int ldx) {
+template <typename T> __device__ void warp_back_solve(const T *A, int k, int lda, T *X, int nc, int ldx) {
     const int lane = threadIdx.x & 31;
     for (int j = lane; j < nc; j += 32)
         for (int i = k - 1; i >= 0; --i) {
-            double v = X[i * ldx + j];
+            T v = X[i * ldx + j];
             for (int t = i + 1; t < k; ++t) v -= A[i * lda + t] * X[t * ldx + j];
             X[i * ldx + j] = v / A[i * lda + i];
         }
@@ -725,29 +730,35 @@ __device__ void warp_back_solve(const double *A, int k, int lda, double *X, int 
 // M leading dimension r.
 constexpr int CORE_WARPS = 4;
 
-__device__ __forceinline__ double sum_chunks(const double *part, int nsplit, int64_t np, int64_t p, int r, int idx) {
-    double s = 0.0;
+template <typename T, typename TP>
+__device__ __forceinline__ T sum_chunks(const TP *part, int nsplit, int64_t np, int64_t p, int r, int idx) {
+    T s = T(0);
     for (int c = 0; c < nsplit; ++c) s += part[((int64_t)c * np + p) * r * r + idx];
     return s;
 }
 
+// T: compute type of the solves; TP: type of the partial products
+template <typename T, typename TP>
 __global__ void __launch_bounds__(128) k_core(int r, int kc, int64_t np, int nsplit, const int *kU, const int *kV,
-                                              const int64_t *offB, const double *Mpart, const double *S1part,
-                                              const double *S2part, double *B) {
-    extern __shared__ double sm[];
+                                              const int64_t *offB, const TP *Mpart, const TP *S1part,
+                                              const TP *S2part, double *B) {
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    T *sm = reinterpret_cast<T *>(sm_raw);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
     const int64_t p = (int64_t)blockIdx.x * nwarps + warp;
     if (p >= np) return;
     const int ku = kU[p], kv = kV[p];
     if (ku == 0 || kv == 0) return;
-    double *S1 = sm + (size_t)warp * (3 * r * kc + r + r * r);  // r x ku  (ld kc)
-    double *S2 = S1 + r * kc;                                    // r x kv
-    double *X = S2 + r * kc;                                     // r x ku: X^T
-    double *tau = X + r * kc;                                    // r
-    double *Mx = tau + r;                                        // r x r (ld r)
-    for (int o = lane; o < r * ku; o += 32) S1[(o / ku) * kc + o % ku] = sum_chunks(S1part, nsplit, np, p, r, (o / ku) * r + o % ku);
-    for (int o = lane; o < r * kv; o += 32) S2[(o / kv) * kc + o % kv] = sum_chunks(S2part, nsplit, np, p, r, (o / kv) * r + o % kv);
-    for (int o = lane; o < r * r; o += 32) Mx[o] = sum_chunks(Mpart, nsplit, np, p, r, o);
+    T *S1 = sm + (size_t)warp * (3 * r * kc + r + r * r);  // r x ku  (ld kc)
+    T *S2 = S1 + r * kc;                                    // r x kv
+    T *X = S2 + r * kc;                                     // r x ku: X^T
+    T *tau = X + r * kc;                                    // r
+    T *Mx = tau + r;                                        // r x r (ld r)
+    for (int o = lane; o < r * ku; o += 32)
+        S1[(o / ku) * kc + o % ku] = sum_chunks<T>(S1part, nsplit, np, p, r, (o / ku) * r + o % ku);
+    for (int o = lane; o < r * kv; o += 32)
+        S2[(o / kv) * kc + o % kv] = sum_chunks<T>(S2part, nsplit, np, p, r, (o / kv) * r + o % kv);
+    for (int o = lane; o < r * r; o += 32) Mx[o] = sum_chunks<T>(Mpart, nsplit, np, p, r, o);
     __syncwarp();
     // X = R1^{-1} (Q1^T M)(0:ku, :)
     warp_house_qr(S1, r, ku, kc, tau);
@@ -765,8 +776,32 @@ __global__ void __launch_bounds__(128) k_core(int r, int kc, int64_t np, int nsp
     double *Bp = B + offB[p];
     for (int o = lane; o < ku * kv; o += 32) {
         const int u = o / kv, v = o % kv;
-        Bp[o] = X[v * kc + u];
+        Bp[o] = (double)X[v * kc + u];
     }
+}
+
+template <typename T, typename TA>
+static void launch_gram(unsigned np, int nsplit, cudaStream_t st, const int *box, const int *ent, int r,
+                        const double *G, const double *F, const int *color, int64_t n, const int64_t *offF,
+                        const int *kdim, void *out) {
+    k_gram<T, TA><<<dim3(np, nsplit), 256, 0, st>>>(box, ent, (int64_t)np, r, G, F, color, n, offF, kdim,
+                                                   static_cast<TA *>(out));
+    ::hm::count_launch();
+}
+
+template <typename T, typename TP>
+static Err launch_core(int64_t np, int nsplit, int r, int kc, cudaStream_t st, const int *kU, const int *kV,
+                       const int64_t *offB, const void *Mpart, const void *S1part, const void *S2part, double *B) {
+    const size_t per_warp = (3 * (size_t)r * kc + r + (size_t)r * r) * sizeof(T);
+    const int core_warps = (int)std::min<size_t>(CORE_WARPS, (200 * 1024) / per_warp);
+    if (core_warps < 1) return fail(HM_ENOTSUP, "cores: r x k too large for shared memory");
+    const size_t smem = (size_t)core_warps * per_warp;
+    HM_CUDA(cudaFuncSetAttribute(k_core<T, TP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_core<T, TP><<<ceil_div(np, core_warps), core_warps * 32, smem, st>>>(
+        r, kc, np, nsplit, kU, kV, offB, static_cast<const TP *>(Mpart), static_cast<const TP *>(S1part),
+        static_cast<const TP *>(S2part), B);
+    ::hm::count_launch();
+    return ok();
 }
 
 Err bases_and_cores(hm_ctx *c, int level) {
@@ -787,13 +822,19 @@ Err bases_and_cores(hm_ctx *c, int level) {
     // M = G_alpha^T P for every pair (tile p is read only by pair p), before the
     // tiles are factored in place
     if (r > 64) return fail(HM_ENOTSUP, "cores: r > 64");
+    // mixed precision: the three products and the solves in FP32 (P, U and V
+    // carry FP32-class rounding already); FP64 otherwise.  The products are
+    // summed over 32-row blocks first: one running FP32 sum over a 1024-row
+    // chunk raised the compression error at 200k points from 5.1e-7 to 6.5e-7.
+    const bool core32 = c->cfg.precision == HM_MIXED_BF16X6;
+    const size_t elem = core32 ? sizeof(float) : sizeof(double);
     const int nsplit = std::max(1, ceil_div(cu.max_rows, GRAM_CHUNK));
-    const size_t part_bytes = (size_t)nsplit * np * r * r * sizeof(double);
-    HM_TRY(ensure(c->scratch_a, part_bytes));
-    k_gram<<<dim3((unsigned)np, nsplit), 256, 0, st>>>(g.pair_alpha.as<int>(), cu.ent.as<int>(), np, r,
-                                                       c->GP.as<double>(), c->cur.Y.as<double>(),
-                                                       g.pair_color.as<int>(), n, nullptr, nullptr,
-                                                       c->scratch_a.as<double>()); ::hm::count_launch();
+    const size_t part_elems = (size_t)nsplit * np * r * r;
+    HM_TRY(ensure(c->scratch_a, part_elems * elem));
+    (core32 ? launch_gram<float, float> : launch_gram<double, double>)((unsigned)np, nsplit, st, g.pair_alpha.as<int>(),
+                                                         cu.ent.as<int>(), r, c->GP.as<double>(),
+                                                         c->cur.Y.as<double>(), g.pair_color.as<int>(), n, nullptr,
+                                                         nullptr, c->scratch_a.p);
     HM_LAUNCH("gram M");
     // QR of every Y tile and every Z tile
     DBuf kY, kZ;
@@ -901,23 +942,19 @@ Err bases_and_cores(hm_ctx *c, int level) {
     const int kc = std::max(1, c->cfg.rank > 0 ? std::min(r, c->cfg.rank) : std::min(r, cap));
     // S1 = G_alpha^T U (Psi side) and S2 = G_beta^T V (Omega side)
     DBuf spart;
-    HM_TRY(alloc(spart, 2 * part_bytes));
-    double *S1part = spart.as<double>(), *S2part = S1part + (size_t)nsplit * np * r * r;
-    k_gram<<<dim3((unsigned)np, nsplit), 256, 0, st>>>(g.pair_alpha.as<int>(), cu.ent.as<int>(), np, r,
-                                                       c->GP.as<double>(), f.U.as<double>(), nullptr, n,
-                                                       f.offU.as<int64_t>(), f.kU.as<int>(), S1part); ::hm::count_launch();
-    k_gram<<<dim3((unsigned)np, nsplit), 256, 0, st>>>(cu.int_idx.as<int>(), cu.ent.as<int>(), np, r,
-                                                       c->GO.as<double>(), f.V.as<double>(), nullptr, n,
-                                                       f.offV.as<int64_t>(), f.kV.as<int>(), S2part); ::hm::count_launch();
+    HM_TRY(alloc(spart, 2 * part_elems * elem));
+    void *S1part = spart.p;
+    void *S2part = static_cast<unsigned char *>(spart.p) + part_elems * elem;
+    (core32 ? launch_gram<float, float> : launch_gram<double, double>)((unsigned)np, nsplit, st, g.pair_alpha.as<int>(),
+                                                         cu.ent.as<int>(), r, c->GP.as<double>(), f.U.as<double>(),
+                                                         nullptr, n, f.offU.as<int64_t>(), f.kU.as<int>(), S1part);
+    (core32 ? launch_gram<float, float> : launch_gram<double, double>)((unsigned)np, nsplit, st, cu.int_idx.as<int>(),
+                                                         cu.ent.as<int>(), r, c->GO.as<double>(), f.V.as<double>(),
+                                                         nullptr, n, f.offV.as<int64_t>(), f.kV.as<int>(), S2part);
     HM_LAUNCH("gram S");
-    const size_t per_warp = (3 * (size_t)r * kc + r + (size_t)r * r) * sizeof(double);
-    const int core_warps = (int)std::min<size_t>(CORE_WARPS, (200 * 1024) / per_warp);
-    if (core_warps < 1) return fail(HM_ENOTSUP, "cores: r x k too large for shared memory");
-    const size_t smem = (size_t)core_warps * per_warp;
-    HM_CUDA(cudaFuncSetAttribute(k_core, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_core<<<ceil_div(np, core_warps), core_warps * 32, smem, st>>>(r, kc, np, nsplit, f.kU.as<int>(), f.kV.as<int>(),
-                                                                    f.offB.as<int64_t>(), c->scratch_a.as<double>(),
-                                                                    S1part, S2part, f.B.as<double>()); ::hm::count_launch();
+    HM_TRY((core32 ? launch_core<float, float> : launch_core<double, double>)(np, nsplit, r, kc, st, f.kU.as<int>(), f.kV.as<int>(),
+                                                               f.offB.as<int64_t>(), c->scratch_a.p, S1part, S2part,
+                                                               f.B.as<double>()));
     HM_LAUNCH("core");
     std::vector<int> hk;
     HM_TRY(to_host(hk, f.kU.p, np, st));

@@ -126,10 +126,10 @@ struct hm_ctx {
     // scratch
     hm::DBuf scratch_a, scratch_b, scratch_c, scratch_d, scan_tmp;
 
-    // second stream on which a host thread colours the levels ahead of the
-    // level loop (created on first use, destroyed with the context)
-    cudaStream_t color_st = nullptr;
-    hm::DBuf color_scan_tmp;
+    // streams on which two host threads colour the levels ahead of the level
+    // loop (created on first use, destroyed with the context)
+    cudaStream_t color_st[2] = {nullptr, nullptr};
+    hm::DBuf color_scan_tmp[2];
 
     hm_info info;
     double t_sample = 0.0;

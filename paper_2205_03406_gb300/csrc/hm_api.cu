@@ -141,10 +141,11 @@ hm_status hm_destroy(hm_ctx *c) {
     if (!c) return HM_OK;
     {
         StreamScope ss(c->st);
-        cudaStream_t st = c->st, cst = c->color_st;
+        cudaStream_t st = c->st, cst0 = c->color_st[0], cst1 = c->color_st[1];
         delete c;
         cudaStreamSynchronize(st);
-        if (cst) cudaStreamDestroy(cst);
+        if (cst0) cudaStreamDestroy(cst0);
+        if (cst1) cudaStreamDestroy(cst1);
     }
     cudaGetLastError();
     return HM_OK;
@@ -218,31 +219,38 @@ static Err keep_current(hm_ctx *c, int idx, bool leaf) {
     return ok();
 }
 
-// The colourings (Section 4.1.1) depend on the tree alone, so a host thread
-// computes them for levels 2..L and the leaf level, in that order, on a second
-// stream of the highest priority (its one-CTA DSatur launches get the next
-// free SM) while the calling thread samples, peels and compresses the levels
-// already coloured.  wait(idx) returns once colouring idx is complete on the
-// device; its Coloring is then only read.
+// The colourings (Section 4.1.1) depend on the tree alone, so two host
+// threads compute them while the calling thread samples, peels and compresses
+// the levels already coloured: one colours levels 2..L in order, the other the
+// leaf level, each on a stream of its own of the highest priority (their
+// one-CTA DSatur launches get the next free SM).  wait(idx) returns once
+// colouring idx is complete on the device; its Coloring is then only read.
 class ColorAhead {
 public:
     explicit ColorAhead(hm_ctx *c) : c_(c), state_(c->L + 2, 0), errs_(c->L + 2) {}
     ~ColorAhead() {
         stop_ = true;
-        if (th_.joinable()) th_.join();
+        for (auto &t : th_)
+            if (t.joinable()) t.join();
     }
     Err start() {
         int dev = 0;
         HM_CUDA(cudaGetDevice(&dev));
-        if (!c_->color_st) {
-            int least = 0, greatest = 0;
-            HM_CUDA(cudaDeviceGetStreamPriorityRange(&least, &greatest));
-            HM_CUDA(cudaStreamCreateWithPriority(&c_->color_st, cudaStreamNonBlocking, greatest));
-        }
+        for (int w = 0; w < 2; ++w)
+            if (!c_->color_st[w]) {
+                int least = 0, greatest = 0;
+                HM_CUDA(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+                HM_CUDA(cudaStreamCreateWithPriority(&c_->color_st[w], cudaStreamNonBlocking, greatest));
+            }
+        // worker 0: levels 2..L; worker 1: the leaf level at index L + 1
+        std::vector<int> levels;
+        for (int l = 2; l <= c_->L; ++l) levels.push_back(l);
         try {
-            th_ = std::thread([this, dev] { run(dev); });
+            th_[0] = std::thread([this, dev, levels] { run(dev, 0, levels); });
+            th_[1] = std::thread([this, dev] { run(dev, 1, std::vector<int>{c_->L + 1}); });
         } catch (const std::exception &e) {
-            return fail(HM_ENOMEM, std::string("colour: cannot start the colouring thread: ") + e.what());
+            stop_ = true;
+            return fail(HM_ENOMEM, std::string("colour: cannot start the colouring threads: ") + e.what());
         }
         return ok();
     }
@@ -256,29 +264,25 @@ public:
     }
 
 private:
-    void run(int dev) {
+    void run(int dev, int w, std::vector<int> order) {
         Err e;
         if (cudaSetDevice(dev) != cudaSuccess) e = fail(HM_ECUDA, "colour: cudaSetDevice failed");
-        StreamScope ss(c_->color_st);
-        // levels 2..L, then the leaf level at index L + 1 (which is below 2 when L < 1)
-        std::vector<int> order;
-        for (int l = 2; l <= c_->L; ++l) order.push_back(l);
-        order.push_back(c_->L + 1);
+        StreamScope ss(c_->color_st[w]);
         for (int idx : order) {
             const bool leaf = idx == c_->L + 1;
             if (!e && stop_) e = fail(HM_ECUDA, "colour: cancelled");
             if (!e && !c_->colorings[idx].done)
-                e = color_cut(c_, leaf ? 0 : idx, leaf, c_->color_st, c_->color_scan_tmp);
+                e = color_cut(c_, leaf ? 0 : idx, leaf, c_->color_st[w], c_->color_scan_tmp[w]);
             {
                 std::lock_guard<std::mutex> lk(m_);
                 state_[idx] = e ? 2 : 1;
-                errs_[idx] = e;  // after a failure every later level reports it too
+                errs_[idx] = e;  // after a failure every later level of this worker reports it too
             }
             cv_.notify_all();
         }
     }
     hm_ctx *c_;
-    std::thread th_;
+    std::thread th_[2];
     std::mutex m_;
     std::condition_variable cv_;
     std::vector<int> state_;  // 0 pending, 1 done, 2 failed
