@@ -586,14 +586,21 @@ __global__ void k_pack_coords(const int64_t *chunk_color_first, int chi, const i
 }
 
 // leaf black box, FP32 kernel values from double-float coordinates, FP64 output:
-// Y(i, c m + t) = sum over active boxes beta of K(i, start_beta + t)
+// Y(i, c m + t) = sum over active boxes beta of K(i, start_beta + t), for the
+// output rows i of colour c only (the rows of its leaf tiles): CTA (b, z)
+// takes 64 of them from out_rows[item_base[b]], colour item_color[b], and
+// the columns t in [64 z, 64 z + 64)
 template <int KIND>
 __global__ void __launch_bounds__(256) k_sample_leaf32(const float4 *xdf, int64_t n, const int *act_ptr,
-                                                       const int *act_box, const int *ent, int m, double *out) {
-    const int c = blockIdx.y;
-    const int64_t i = (int64_t)blockIdx.x * 64 + (threadIdx.x >> 2);
-    const int ph = threadIdx.x & 3, t0 = blockIdx.z * 64;
-    if (i >= n) return;
+                                                       const int *act_box, const int *ent, int m,
+                                                       const int *out_rows, const int64_t *out_ptr,
+                                                       const int *item_color, const int64_t *item_base,
+                                                       double *out) {
+    const int c = item_color[blockIdx.x];
+    const int64_t oi = item_base[blockIdx.x] + (threadIdx.x >> 2);
+    const int ph = threadIdx.x & 3, t0 = blockIdx.y * 64;
+    if (oi >= out_ptr[c + 1]) return;
+    const int64_t i = out_rows[oi];
     const float4 ih = xdf[2 * i], il = xdf[2 * i + 1];
     float acc[16];
 #pragma unroll
@@ -744,13 +751,30 @@ Err sample_leaf_mixed(hm_ctx *c, int kernel) {
     const Cut &cu = c->cuts[c->L];
     const int chi = g.n_colors, m = g.m_cols;
     const int64_t n = c->n;
+    cudaStream_t st = c->st;
     HM_TRY(make_xdf(c));
-    dim3 grid(ceil_div(n, 64), chi, ceil_div(m, 64));
+    // one CTA per 64 output rows of a colour (and 64 columns)
+    std::vector<int> icol;
+    std::vector<int64_t> ibase;
+    if ((int)g.h_out_rows_ptr.size() == chi + 1)
+        for (int k = 0; k < chi; ++k)
+            for (int64_t b = g.h_out_rows_ptr[k]; b < g.h_out_rows_ptr[k + 1]; b += 64) {
+                icol.push_back(k);
+                ibase.push_back(b);
+            }
+    if (icol.empty()) return ok();
+    DBuf icold, ibased;
+    HM_TRY(to_dev(icold, icol, st));
+    HM_TRY(to_dev(ibased, ibase, st));
+    dim3 grid((unsigned)icol.size(), ceil_div(m, 64));
     switch (kernel) {
-#define LAUNCH(K)                                                                                       \
-    case K:                                                                                             \
-        k_sample_leaf32<K><<<grid, 256, 0, c->st>>>(c->xdf.as<float4>(), n, g.act_ptr.as<int>(),          \
-                                                     g.act_box.as<int>(), cu.ent.as<int>(), m, c->cur.Y.as<double>()); ::hm::count_launch(); \
+#define LAUNCH(K)                                                                                              \
+    case K:                                                                                                    \
+        k_sample_leaf32<K><<<grid, 256, 0, st>>>(c->xdf.as<float4>(), n, g.act_ptr.as<int>(), g.act_box.as<int>(), \
+                                                 cu.ent.as<int>(), m, g.out_rows.as<int>(),                     \
+                                                 g.out_rows_ptr.as<int64_t>(), icold.as<int>(),                 \
+                                                 ibased.as<int64_t>(), c->cur.Y.as<double>());                  \
+        ::hm::count_launch();                                                                                  \
         break;
         LAUNCH(HM_K_LOG)
         LAUNCH(HM_K_LAPLACE3D)
