@@ -34,6 +34,14 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "time-to-compress (s) and jobs/s at stated rel. error; p50/p99 latency"
+
+# precision modes: (hm_precision value, description, dtype key of the JSON line)
+PRECISIONS = {
+    "mixed-f32": (2, "split-BF16x6 tensor-core black box; FP32 peel products, QR and core solves; "
+                     "FP64 samples, factors and subtractions", "bf16x6-f32acc+f32+f64"),
+    "mixed": (1, "split-BF16x6 tensor-core black box; FP64 peel, QR and core solves", "bf16x6-f32acc+f64"),
+    "fp64": (0, "FP64 throughout", "f64"),
+}
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
 
 # dram bytes (read + write) of the tensor-core contraction kernel per evaluated
@@ -50,7 +58,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--n", type=int, default=200_000)
-    ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
+    ap.add_argument("--precision", choices=list(PRECISIONS), default="mixed-f32")
+    ap.add_argument("--no-modes", action="store_true",
+                    help="skip timing the other two precision modes beside the main line")
     ap.add_argument("--relerr-iters", type=int, default=20)
     ap.add_argument("--no-relerr", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -67,8 +77,7 @@ def config_of(args, w):
     return {"workload": f"torus_laplace_{w.n}", "n": w.n, "geometry": "torus R=1 rho=0.3, uniform (u,v)",
             "kernel": "1/(4 pi |x-y|), zero diagonal, on the fly", "leaf_size": w.leaf_size, "tol": w.tol,
             "r": w.r, "oversample": w.oversample,
-            "precision": "split-BF16x6 tensor-core black box; FP32 peel products, QR and core solves; FP64 samples and factors"
-            if args.precision == "mixed" else "FP64 throughout",
+            "precision": PRECISIONS[args.precision][1],
             "l2": "working set larger than L2 (samples ~5 GB per level); no flush", "seed": w.seed}
 
 
@@ -143,6 +152,7 @@ def roofline_tc(info, r: int):
     flops, executed as 6 BF16 products each."""
     useful = 4.0 * r * info.tc_kernel_evals
     t = info.seconds_phase[7]
+    launches = sum(1 for l in range(2, info.L + 1) if info.colors[l] > 0)  # one k_sample_tc per level
     pk, src = peaks()
     bf16_flops = 6.0 * useful
     achieved = bf16_flops / t / 1e12 if t > 0 else 0.0
@@ -152,13 +162,14 @@ def roofline_tc(info, r: int):
         src_path = os.path.join(ROOT, TRAFFIC["file"])
         sha = hashlib.sha256(open(src_path, "rb").read()).hexdigest()[:16]
         if TRAFFIC["sha256"] == sha and TRAFFIC["bytes_per_eval"]:
-            traffic = round(TRAFFIC["bytes_per_eval"] * info.tc_kernel_evals)
+            traffic = round(TRAFFIC["bytes_per_eval"] * info.tc_kernel_evals / max(launches, 1))
     except OSError:
         pass
     return {"kernel": "k_sample_tc (split-BF16 kernel-matrix x Omega contraction)", "bound": "tensor",
             "achieved": round(achieved, 2), "peak": peak, "unit": "TFLOP/s",
             "frac": round(achieved / peak, 4), "peak_source": f"{src} bf16_tflops_sustained",
-            "traffic": traffic, "seconds": round(t, 4), "bf16_flops": bf16_flops,
+            "traffic": traffic, "traffic_unit": "dram bytes per launch (ncu, scaled by evaluated entries)",
+            "launches_per_step": launches, "seconds": round(t, 4), "bf16_flops": bf16_flops,
             "useful_fp64_equiv_flops": useful}
 
 
@@ -182,6 +193,32 @@ def rank_seed(base: int, rank: int) -> int:
     return base + rank
 
 
+def time_mode(hm, w, pts, op, precision: int, rank: int, steps: int, relerr_iters):
+    """Time-to-compress (CUDA events, after one warm-up job) and relative error
+    of the same job in another precision mode."""
+    import torch
+    s = hm.Settings(d=3, leaf_size=w.leaf_size, r=w.r, oversample=w.oversample, tol=w.tol, precision=precision,
+                    seed=rank_seed(w.seed, rank))
+    comp = hm.Compressor(s, torch.cuda.current_stream())
+    comp.tree_build(pts)
+    comp.compress(op)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(steps):
+        comp.tree_build(pts)
+        comp.compress(op)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) / 1e3 / steps
+    out = {"time_to_compress_s": round(t, 4), "steps": steps,
+           "rel_error": None if relerr_iters is None else comp.relerr(op, relerr_iters),
+           "phases_s": {n: round(comp.info().seconds_phase[i], 4) for i, n in enumerate(hm.PHASES)}}
+    comp.close()
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -202,7 +239,7 @@ def run_ours(args):
             dist.barrier()
 
     w = workload(args.n)
-    prec = hm.HM_MIXED_BF16X6 if args.precision == "mixed" else hm.HM_FP64
+    prec = PRECISIONS[args.precision][0]
     s = hm.Settings(d=3, leaf_size=w.leaf_size, r=w.r, oversample=w.oversample, tol=w.tol, precision=prec,
                     seed=rank_seed(w.seed, rank))
     stream = torch.cuda.current_stream()
@@ -275,6 +312,17 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(w, rows_per_level=100)
 
+    # the other precision modes on the same job, for the error / time trade-off
+    modes = None
+    if rank == 0 and not args.no_modes:
+        modes = {}
+        for name, (pv, desc, _) in PRECISIONS.items():
+            if name == args.precision:
+                continue
+            modes[name] = time_mode(hm, w, pts, op, pv, rank, steps=1 if pv == 0 else 3,
+                                    relerr_iters=None if args.no_relerr else args.relerr_iters)
+            modes[name]["precision"] = desc
+
     if rank != 0:
         comp.close()
         if dist is not None:
@@ -289,7 +337,7 @@ def run_ours(args):
         "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * tmax / args.steps, 2),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "bf16x6-f32acc+f64" if args.precision == "mixed" else "f64",
+        "dtype": PRECISIONS[args.precision][2],
         "data": "synthetic (seeded torus point cloud)",
         "config": dict(config_of(args, w), parallelism=f"replicas x{world}"),
         "time_to_compress_s": round(tmax / args.steps, 4),
@@ -300,6 +348,7 @@ def run_ours(args):
         "phases_s": phases, "host_elapsed_s": round(elapsed_host, 3),
         "roofline": roofline_tc(info, w.r),
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
+        "modes": modes,
     }
     print(json.dumps(out), flush=True)
     comp.close()

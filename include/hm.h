@@ -51,13 +51,20 @@ typedef enum {
     HM_ENOTSUP = 7    /* outside the implemented limits (e.g. > 1024 colours) */
 } hm_status;
 
-/* Arithmetic of the built-in black-box contraction K(X, X) Omega.  The peel
- * subtraction, the QR factorisations and the core solves are FP64 in both. */
+/* Arithmetic of the path.  Samples, factors and every subtraction from a
+ * sample are stored and done in FP64 in all three modes. */
 typedef enum {
-    HM_FP64 = 0,         /* FP64 kernel evaluation and FP64 products */
-    HM_MIXED_BF16X6 = 1  /* FP32 kernel evaluation, 3-piece BF16 split of both
-                            operands, 6 tcgen05 products, FP32 accumulation,
-                            FP64 output */
+    HM_FP64 = 0,             /* FP64 throughout */
+    HM_MIXED_BF16X6 = 1,     /* black box (built-in kernel operator): FP32 kernel
+                                evaluation, 3-piece BF16 split of both operands,
+                                6 tcgen05 products, FP32 accumulation promoted to
+                                double-float, FP64 output; peel, QR and core
+                                solves FP64 */
+    HM_MIXED_BF16X6_F32 = 2  /* the same black box; the products of the peel, the
+                                pivoted QR factorisations, the core's Gram
+                                products and least-squares solves in FP32 (the
+                                samples they work on carry FP32-class rounding
+                                from the black box already) */
 } hm_precision;
 
 /* Kernel functions of the built-in operator (A_ij = K(x_i, x_j)). */

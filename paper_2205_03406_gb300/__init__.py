@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(_HERE, "libhm.so")
 HM_OK, HM_EINVAL, HM_ENOMEM, HM_ESTATE, HM_ECUDA, HM_EOP, HM_ETIMEOUT, HM_ENOTSUP = range(8)
 STATUS_NAMES = ["HM_OK", "HM_EINVAL", "HM_ENOMEM", "HM_ESTATE", "HM_ECUDA", "HM_EOP", "HM_ETIMEOUT",
                 "HM_ENOTSUP"]
-HM_FP64, HM_MIXED_BF16X6 = 0, 1
+HM_FP64, HM_MIXED_BF16X6, HM_MIXED_BF16X6_F32 = 0, 1, 2
 HM_K_LOG, HM_K_LAPLACE3D, HM_K_INVR, HM_K_EXP = 1, 2, 3, 4
 HM_OP_KERNEL, HM_OP_DENSE, HM_OP_CALLBACK = 0, 1, 2
 HM_LEVEL_LEAF = -1

@@ -9,7 +9,7 @@
 //       R_jj >= 0.  The same kernel factors every Z tile; V of pair
 //       (alpha, beta) is the Q of the Z tile of the pair (beta, alpha).
 //       FP64 mode: one warp per tile up to 256 rows, one CTA per larger tile.
-//       Mixed precision: FP32 in shared memory, one CTA per tile up to
+//       HM_MIXED_BF16X6_F32: FP32 in shared memory, one CTA per tile up to
 //       QR32_MAX_ROWS rows (FP64 CTA kernel beyond).
 //  K10  B = (G_alpha^T U)^+ (G_alpha^T Y(I_alpha, c)) (V^T G_beta)^+ with
 //       G_alpha the Psi-side block of alpha and G_beta the Omega-side block of
@@ -32,7 +32,7 @@ namespace hm {
 // writes zeros; the consumer adds the chunks in order.  T is the type of the
 // products and of the sums over 32-row blocks, TA that of the sums over the
 // blocks and of the output (double and double, or float and float in the
-// mixed-precision mode, whose P, U and V carry FP32-class rounding already).
+// HM_MIXED_BF16X6_F32 mode, whose P, U and V carry FP32-class rounding already).
 constexpr int GRAM_CHUNK = 1024;
 
 template <typename T, typename TA>
@@ -340,7 +340,7 @@ __global__ void __launch_bounds__(128) k_qr_warp(const int *tile_alpha, const in
 }
 
 // ---------------------------------------------------------------------------
-// Mixed precision: FP32 QR with the tile in shared memory (the samples it
+// HM_MIXED_BF16X6_F32: FP32 QR with the tile in shared memory (the samples it
 // factors carry FP32-level rounding already).  The CTA's 128 threads work on
 // column t % RP (RP = 32 for r <= 32, else 64) and on the rows i = t / RP
 // (mod 128 / RP) in the column passes; partial sums over the row groups are
@@ -490,7 +490,7 @@ __global__ void __launch_bounds__(128) k_qr32(const int *tile_alpha, const int *
 }
 
 // ---------------------------------------------------------------------------
-// Mixed precision, tall tiles: FP32 tall-skinny QR.  A tile of m rows is cut
+// HM_MIXED_BF16X6_F32, tall tiles: FP32 tall-skinny QR.  A tile of m rows is cut
 // into nb balanced blocks of at most TS_ROWS rows (blocks of tiles above the
 // shared-memory limit only).  (1) every block: unpivoted Householder QR,
 // A_b = Q_b R_b, the reflectors written over the block, R_b into the stack;
@@ -822,11 +822,11 @@ Err bases_and_cores(hm_ctx *c, int level) {
     // M = G_alpha^T P for every pair (tile p is read only by pair p), before the
     // tiles are factored in place
     if (r > 64) return fail(HM_ENOTSUP, "cores: r > 64");
-    // mixed precision: the three products and the solves in FP32 (P, U and V
+    // HM_MIXED_BF16X6_F32: the three products and the solves in FP32 (P, U and V
     // carry FP32-class rounding already); FP64 otherwise.  The products are
     // summed over 32-row blocks first: one running FP32 sum over a 1024-row
     // chunk raised the compression error at 200k points from 5.1e-7 to 6.5e-7.
-    const bool core32 = c->cfg.precision == HM_MIXED_BF16X6;
+    const bool core32 = c->cfg.precision == HM_MIXED_BF16X6_F32;
     const size_t elem = core32 ? sizeof(float) : sizeof(double);
     const int nsplit = std::max(1, ceil_div(cu.max_rows, GRAM_CHUNK));
     const size_t part_elems = (size_t)nsplit * np * r * r;
@@ -841,11 +841,11 @@ Err bases_and_cores(hm_ctx *c, int level) {
     HM_TRY(alloc(kY, np * sizeof(int)));
     HM_TRY(alloc(kZ, np * sizeof(int)));
     const int cap = c->cfg.rank > 0 ? r : r - c->cfg.oversample;
-    // Mixed precision: tiles up to qr32_rows rows by the FP32 shared-memory
+    // HM_MIXED_BF16X6_F32: tiles up to qr32_rows rows by the FP32 shared-memory
     // kernel, tiles up to ts_max rows by the FP32 tall-skinny QR, larger ones
     // by the FP64 block kernel.  FP64: the warp kernel up to QR_WARP_ROWS rows,
     // the block kernel beyond.
-    const bool mixed = c->cfg.precision == HM_MIXED_BF16X6;
+    const bool mixed = c->cfg.precision == HM_MIXED_BF16X6_F32;
     const int qr32_rows = mixed ? std::min(QR32_MAX_ROWS, (200 * 1024) / (4 * r)) : 0;
     const int ts_rows = (200 * 1024) / (8 * r) / 32 * 32;       // rows per tall-skinny block
     const int ts_max = mixed ? (200 * 1024) / (4 * r * r) * ts_rows : 0;

@@ -72,7 +72,7 @@ struct Factors {
     DBuf kU, kV;              // int32
     DBuf offU, offV, offB;    // int64 element offsets
     DBuf U, V, B;
-    DBuf U32, V32, B32;       // FP32 copies for the mixed-precision peel (made on first use)
+    DBuf U32, V32, B32;       // FP32 copies for the HM_MIXED_BF16X6_F32 peel (made on first use)
     int64_t nU = 0, nV = 0, nB = 0;
     int max_k = 0;
 };

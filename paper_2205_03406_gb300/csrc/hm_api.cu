@@ -117,7 +117,8 @@ hm_status hm_create(hm_ctx **out, const hm_config *cfg, void *stream) {
     if ((cfg->rank > 0) == (cfg->tol > 0.0) || cfg->rank > cfg->r || cfg->rank < 0 || !(cfg->tol >= 0.0))
         return HM_EINVAL;
     if (cfg->tol > 0.0 && (cfg->oversample < 0 || cfg->oversample >= cfg->r)) return HM_EINVAL;
-    if (cfg->precision != HM_FP64 && cfg->precision != HM_MIXED_BF16X6) return HM_EINVAL;
+    if (cfg->precision != HM_FP64 && cfg->precision != HM_MIXED_BF16X6 && cfg->precision != HM_MIXED_BF16X6_F32)
+        return HM_EINVAL;
     if (cfg->uniform_depth < 0 || cfg->uniform_depth > QBITS) return HM_EINVAL;
     hm_ctx *c = new (std::nothrow) hm_ctx();
     if (!c) return HM_ENOMEM;

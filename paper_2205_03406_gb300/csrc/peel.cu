@@ -169,7 +169,7 @@ Err peel_level(hm_ctx *c, int level, bool leaf) {
     const Coloring &g = c->colorings[idx];
     if (g.n_pairs == 0 || g.n_colors == 0) return ok();
     const int cols = g.m_cols;
-    if (c->cfg.precision == HM_MIXED_BF16X6 && cols <= 64) return peel_level_mixed(c, level, leaf);
+    if (c->cfg.precision == HM_MIXED_BF16X6_F32 && cols <= 64) return peel_level_mixed(c, level, leaf);
     const int jmax = leaf ? c->L : level - 1;
     const Cut &cl = c->cuts[l];
     cudaStream_t st = c->st;

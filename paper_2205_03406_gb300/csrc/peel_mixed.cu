@@ -1,4 +1,4 @@
-// Peeling for the mixed-precision mode (Section 4.1.2, Algorithm 4.1):
+// Peeling for HM_MIXED_BF16X6_F32 (Section 4.1.2, Algorithm 4.1):
 //     Y_l(I_alpha, c) -= sum over coarse pairs q of U_q(I_alpha) B_q V_q^T Omega_l(I_b, c)
 // (and the transpose for Z).  The products of the coarse factors run in FP32
 // from FP32 copies of U, V, B and of the level's Gaussians; the subtraction from

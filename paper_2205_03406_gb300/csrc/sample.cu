@@ -305,7 +305,7 @@ Err sample_level(hm_ctx *c, const hm_op *op, int level, bool leaf) {
     if (op->kind != HM_OP_KERNEL && op->kind != HM_OP_DENSE) return fail(HM_EINVAL, "unknown operator kind");
     const OpDev o = make_opdev(c, op);
     const Cut &cu = c->cuts[g.level];
-    if (leaf && c->cfg.precision == HM_MIXED_BF16X6 && op->kind == HM_OP_KERNEL)
+    if (leaf && c->cfg.precision != HM_FP64 && op->kind == HM_OP_KERNEL)
         return sample_leaf_mixed(c, op->kernel);
     if (leaf) {
         dim3 grid(ceil_div(n, 64), chi, ceil_div(cols, 64));
@@ -314,7 +314,7 @@ Err sample_level(hm_ctx *c, const hm_op *op, int level, bool leaf) {
         HM_LAUNCH("sample_leaf64");
         return ok();
     }
-    if (c->cfg.precision == HM_MIXED_BF16X6 && op->kind == HM_OP_KERNEL && tc_supported(c))
+    if (c->cfg.precision != HM_FP64 && op->kind == HM_OP_KERNEL && tc_supported(c))
         return sample_tc(c, level, op->kernel);
     const int64_t *rp = g.act_rows_ptr.as<int64_t>();
     const int *rows = g.act_rows.as<int>();

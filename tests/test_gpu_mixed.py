@@ -1,4 +1,6 @@
-"""Mixed precision (tcgen05 split-BF16 black box) against the FP64 oracle.
+"""Mixed precision (tcgen05 split-BF16 black box) against the FP64 oracle,
+with the peel, QR and core solves in FP64 (HM_MIXED_BF16X6) and in FP32
+(HM_MIXED_BF16X6_F32).
 
 The black-box samples must match the FP64 products to FP32-class accuracy
 (<= 1e-6 relative per level) on the entries the method reads (the rows of
@@ -19,7 +21,8 @@ from gpu_helpers import hm, oracle_op, run_gpu, samples, tile_mask
 
 pytestmark = pytest.mark.gpu
 
-MIXED = 1
+MIXED = 1        # split-BF16 black box; FP64 peel, QR and core solves
+MIXED_F32 = 2    # the same black box; FP32 peel products, QR and core solves
 TOL_MIXED = 1e-6
 
 
@@ -74,11 +77,12 @@ def test_mixed_raw_samples(name):
     comp.close()
 
 
+@pytest.mark.parametrize("precision", [MIXED, MIXED_F32], ids=["fp64-solves", "fp32-solves"])
 @pytest.mark.parametrize("name", list(mixed_workloads()))
-def test_mixed_compression_matches_oracle(name):
+def test_mixed_compression_matches_oracle(name, precision):
     import torch
     w = mixed_workloads()[name]
-    comp, info = run_gpu(w, precision=MIXED, keep=False)
+    comp, info = run_gpu(w, precision=precision, keep=False)
     t = ot.build_tree(w.points, w.leaf_size, w.uniform_depth)
     H = oh1.compress(t, oracle_op(w, t), w.r, rank=w.rank, tol=w.tol, seed=w.seed, oversample=w.oversample)
     x = np.random.default_rng(1).standard_normal((w.n, 3))
