@@ -155,7 +155,8 @@ Err sample_leaf_mixed(hm_ctx *c, int kernel);
 bool tc_supported(const hm_ctx *c);
 // peel.cu, peel_mixed.cu
 Err peel_level(hm_ctx *c, int level, bool leaf);
-Err peel_level_mixed(hm_ctx *c, int level, bool leaf);
+Err peel_level_mixed(hm_ctx *c, int level, bool leaf);  // FP32 products (HM_MIXED_BF16X6_F32)
+Err peel_level_fp64(hm_ctx *c, int level, bool leaf);   // the same structure in FP64
 // basis.cu
 Err bases_and_cores(hm_ctx *c, int level);
 Err extract_leaf(hm_ctx *c);

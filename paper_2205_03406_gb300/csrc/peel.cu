@@ -169,7 +169,10 @@ Err peel_level(hm_ctx *c, int level, bool leaf) {
     const Coloring &g = c->colorings[idx];
     if (g.n_pairs == 0 || g.n_colors == 0) return ok();
     const int cols = g.m_cols;
-    if (c->cfg.precision == HM_MIXED_BF16X6_F32 && cols <= 64) return peel_level_mixed(c, level, leaf);
+    // up to 64 columns per colour: T = B W once per (coarse pair, colour) and a
+    // register-tiled update (peel_mixed.cu), in FP32 or FP64; wider leaves: below
+    if (cols <= 64)
+        return c->cfg.precision == HM_MIXED_BF16X6_F32 ? peel_level_mixed(c, level, leaf) : peel_level_fp64(c, level, leaf);
     const int jmax = leaf ? c->L : level - 1;
     const Cut &cl = c->cuts[l];
     cudaStream_t st = c->st;

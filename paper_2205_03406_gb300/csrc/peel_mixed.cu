@@ -37,11 +37,12 @@ __global__ void k_xsize(const int *pair_alpha, const int *pair_col, int64_t np, 
     xsz[q] = (int64_t)(pt2ent_l[e[4] - 1] + 1 - pt2ent_l[e[3]]) * kdim[q] * cols;
 }
 
-// X_{q,gamma} (k x cols, FP32): F_q(I_gamma)^T G(I_gamma), or the identity
+// X_{q,gamma} (k x cols, type R): F_q(I_gamma)^T G(I_gamma), or the identity
 // block's F rows at the leaf step; CTA (q, y) takes the gammas y, y + gridDim.y, ...
-__global__ void k_peel_x32(const int *pair_alpha, const int *pair_col, const int *entj, const int *entl,
-                           const int *pt2ent_l, const int *kdim, const int64_t *offF, const float *F, const float *G,
-                           int cols, int identity, int side, const int64_t *xoff, float *X) {
+template <typename R>
+__global__ void k_peel_xr(const int *pair_alpha, const int *pair_col, const int *entj, const int *entl,
+                          const int *pt2ent_l, const int *kdim, const int64_t *offF, const R *F, const R *G,
+                          int cols, int identity, int side, const int64_t *xoff, R *X) {
     const int64_t q = blockIdx.x;
     const int k = kdim[q];
     if (k == 0) return;
@@ -49,37 +50,38 @@ __global__ void k_peel_x32(const int *pair_alpha, const int *pair_col, const int
     const int *e = entj + (int64_t)box * ENT_FIELDS;
     const int bstart = e[3];
     const int kb = pt2ent_l[e[3]], ke = pt2ent_l[e[4] - 1] + 1;
-    const float *Fq = F + offF[q];
-    float *Xq = X + xoff[q];
+    const R *Fq = F + offF[q];
+    R *Xq = X + xoff[q];
     for (int g = kb + blockIdx.y; g < ke; g += gridDim.y) {
         const int *eg = entl + (int64_t)g * ENT_FIELDS;
         const int s0 = eg[3], len = eg[4] - eg[3];
-        float *xg = Xq + (int64_t)(g - kb) * k * cols;
+        R *xg = Xq + (int64_t)(g - kb) * k * cols;
         for (int o = threadIdx.x; o < k * cols; o += blockDim.x) {
             const int v = o / cols, t = o % cols;
-            float acc = 0.0f;
+            R acc = R(0);
             if (identity) {
-                acc = (t < len) ? Fq[(int64_t)(s0 - bstart + t) * k + v] : 0.0f;
+                acc = (t < len) ? Fq[(int64_t)(s0 - bstart + t) * k + v] : R(0);
             } else {
                 for (int i = 0; i < len; ++i)
-                    acc = fmaf(Fq[(int64_t)(s0 - bstart + i) * k + v], G[(int64_t)(s0 + i) * cols + t], acc);
+                    acc = fma(Fq[(int64_t)(s0 - bstart + i) * k + v], G[(int64_t)(s0 + i) * cols + t], acc);
             }
             xg[o] = acc;
         }
     }
 }
 
-struct Coarse {
+template <typename R> struct CoarseT {
     const int *ent, *pt2ent, *int_ptr, *int_idx, *pairT;
     const int *kU, *kV;
     const int64_t *offU, *offV, *offB;
-    const float *U, *V, *B;
+    const R *U, *V, *B;
     const int64_t *xoff;
-    const float *X;
+    const R *X;
     const int64_t *base;        // [nc_j * chi + 1]: first T slot of (A, c)
-    float *T;                   // [slots][kcap][cols]
+    R *T;                       // [slots][kcap][cols]
     unsigned char *live;        // [slots]: T holds a nonzero product
 };
+using Coarse = CoarseT<float>;
 
 __device__ __forceinline__ int lower_bound(const int *a, int lo, int hi, int key) {
     while (lo < hi) {
@@ -103,17 +105,19 @@ __global__ void k_anc_mark(const int *tile_alpha, const int *tile_color, int64_t
 // One warp per (A, c) combination of level j; for every entry t of A's
 // interaction list: W = sum of X_{q,gamma} over the gammas of colour c in the
 // other box, T[slot] = B W (Y side, B is kout x kin) or B^T W (Z side).
-__global__ void __launch_bounds__(WARPS * 32) k_peel_T(Coarse C, int64_t ncomb, int chi, int side, int cols,
+template <typename R>
+__global__ void __launch_bounds__(WARPS * 32) k_peel_T(CoarseT<R> C, int64_t ncomb, int chi, int side, int cols,
                                                      int kcap, const int *pt2ent_l, const int *act_ptr,
                                                      const int *act_box) {
-    extern __shared__ float sm[];
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    R *sm = reinterpret_cast<R *>(sm_raw);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t e = (int64_t)blockIdx.x * WARPS + warp;
     if (e >= ncomb) return;
     const int64_t s0 = C.base[e];
     if (C.base[e + 1] == s0) return;  // no tile needs (A, c)
     const int A = (int)(e / chi), c = (int)(e % chi);
-    float *W = sm + (size_t)warp * kcap * cols;
+    R *W = sm + (size_t)warp * kcap * cols;
     const int a0 = act_ptr[c], a1 = act_ptr[c + 1];
     const int t0 = C.int_ptr[A];
     for (int t = t0; t < C.int_ptr[A + 1]; ++t) {
@@ -128,20 +132,20 @@ __global__ void __launch_bounds__(WARPS * 32) k_peel_T(Coarse C, int64_t ncomb, 
             lo = lower_bound(act_box, a0, a1, kb);
             hi = lower_bound(act_box, lo, a1, ke);
             if (lo < hi) {
-                const float *Xq = C.X + C.xoff[q];
+                const R *Xq = C.X + C.xoff[q];
                 for (int o = lane; o < kin * cols; o += 32) {
-                    float sacc = 0.0f;
+                    R sacc = R(0);
                     for (int g = lo; g < hi; ++g) sacc += Xq[(int64_t)(act_box[g] - kb) * kin * cols + o];
                     W[o] = sacc;
                 }
                 __syncwarp();
-                const float *Bq = C.B + C.offB[q];
-                float *To = C.T + slot * kcap * cols;
+                const R *Bq = C.B + C.offB[q];
+                R *To = C.T + slot * kcap * cols;
                 for (int o = lane; o < kout * cols; o += 32) {
                     const int u = o / cols, col = o % cols;
-                    float sacc = 0.0f;
+                    R sacc = R(0);
                     for (int v = 0; v < kin; ++v)
-                        sacc = fmaf(side ? Bq[v * kout + u] : Bq[u * kin + v], W[v * cols + col], sacc);
+                        sacc = fma(side ? Bq[v * kout + u] : Bq[u * kin + v], W[v * cols + col], sacc);
                     To[o] = sacc;
                 }
                 __syncwarp();
@@ -151,19 +155,20 @@ __global__ void __launch_bounds__(WARPS * 32) k_peel_T(Coarse C, int64_t ncomb, 
     }
 }
 
-__global__ void k_item_count(const int *tile_alpha, const int *entl, int64_t ntiles, int64_t *cnt) {
+// work items of the update: chunks of gr rows of every tile
+__global__ void k_item_count(const int *tile_alpha, const int *entl, int64_t ntiles, int gr, int64_t *cnt) {
     const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (p >= ntiles) return;
     const int *e = entl + (int64_t)tile_alpha[p] * ENT_FIELDS;
-    cnt[p] = (e[4] - e[3] + 63) / 64;
+    cnt[p] = (e[4] - e[3] + gr - 1) / gr;
 }
 
-__global__ void k_item_fill(const int64_t *off, int64_t ntiles, int64_t *item_tile, int *item_row) {
+__global__ void k_item_fill(const int64_t *off, int64_t ntiles, int gr, int64_t *item_tile, int *item_row) {
     const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (p >= ntiles) return;
     for (int64_t k = off[p]; k < off[p + 1]; ++k) {
         item_tile[k] = p;
-        item_row[k] = (int)(k - off[p]) * 64;
+        item_row[k] = (int)(k - off[p]) * gr;
     }
 }
 
@@ -253,6 +258,89 @@ __global__ void __launch_bounds__(128) k_peel_gemm(const Coarse *cl, int ncl, in
     }
 }
 
+// FP64 variant (HM_FP64 and HM_MIXED_BF16X6): one CTA of 128 threads per
+// 32-row chunk of a tile (FP64 arithmetic is the bound, so fewer padding rows
+// than the FP32 kernel's 64); thread (rg, cg) owns rows 4 rg .. 4 rg + 3 and
+// columns cg CW .. cg CW + CW - 1 (CW = MAXC / 16); F' and T staged in
+// dynamic shared memory (kcap x 36 and kcap x MAXC doubles).
+constexpr int GEMM64_ROWS = 32, GEMM64_LDF = 36;
+
+template <int MAXC>
+__global__ void __launch_bounds__(128) k_peel_gemm64(const CoarseT<double> *cl, int ncl, int side, int chi,
+                                                     const int *tile_alpha, const int *tile_color, const int *entl,
+                                                     const int64_t *item_tile, const int *item_row, int64_t nitems,
+                                                     int cols, int kcap, int64_t n, double *OUT) {
+    constexpr int CW = MAXC / 16;
+    extern __shared__ __align__(16) unsigned char sm64_raw[];
+    double *Fs = reinterpret_cast<double *>(sm64_raw);  // kcap x GEMM64_LDF
+    double *Ts = Fs + kcap * GEMM64_LDF;                  // kcap x MAXC
+    const int64_t item = blockIdx.x;
+    if (item >= nitems) return;
+    const int tid = threadIdx.x, rg = tid >> 4, cg = tid & 15;
+    const int64_t p = item_tile[item];
+    const int alpha = tile_alpha[p], c = tile_color[p];
+    const int *ea = entl + (int64_t)alpha * ENT_FIELDS;
+    const int sa = ea[3] + item_row[item];
+    const int rows = min(GEMM64_ROWS, ea[4] - sa);
+    double acc[4][CW];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < CW; ++j) acc[i][j] = 0.0;
+    for (int lvl = 0; lvl < ncl; ++lvl) {
+        const CoarseT<double> &C = cl[lvl];
+        const int A = C.pt2ent[sa];
+        const int anc_start = C.ent[(int64_t)A * ENT_FIELDS + 3];
+        const int t0 = C.int_ptr[A], t1 = C.int_ptr[A + 1];
+        const int64_t s0 = C.base[(int64_t)A * chi + c];
+        for (int t = t0; t < t1; ++t) {
+            const int64_t slot = s0 + (t - t0);
+            if (!C.live[slot]) continue;  // uniform over the CTA
+            const int q = side ? C.pairT[t] : t;
+            const int kout = side ? C.kV[q] : C.kU[q];
+            const double *F = (side ? C.V + C.offV[q] : C.U + C.offU[q]) + (int64_t)(sa - anc_start) * kout;
+            const double *Tq = C.T + slot * kcap * cols;
+            __syncthreads();  // the previous step's reads of Fs / Ts are done
+            for (int o = tid; o < GEMM64_ROWS * kout; o += 128) {
+                const int row = o / kout, u = o % kout;
+                Fs[u * GEMM64_LDF + row] = row < rows ? F[o] : 0.0;
+            }
+            for (int o = tid; o < kout * MAXC; o += 128) {
+                const int u = o / MAXC, col = o % MAXC;
+                Ts[o] = col < cols ? Tq[u * cols + col] : 0.0;
+            }
+            __syncthreads();
+            for (int u = 0; u < kout; ++u) {
+                const double2 f01 = *reinterpret_cast<const double2 *>(&Fs[u * GEMM64_LDF + rg * 4]);
+                const double2 f23 = *reinterpret_cast<const double2 *>(&Fs[u * GEMM64_LDF + rg * 4 + 2]);
+                const double fv[4] = {f01.x, f01.y, f23.x, f23.y};
+                double tv[CW];
+#pragma unroll
+                for (int j2 = 0; j2 < CW / 2; ++j2) {
+                    const double2 x = *reinterpret_cast<const double2 *>(&Ts[u * MAXC + cg * CW + 2 * j2]);
+                    tv[2 * j2] = x.x;
+                    tv[2 * j2 + 1] = x.y;
+                }
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < CW; ++j) acc[i][j] = fma(fv[i], tv[j], acc[i][j]);
+            }
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int row = rg * 4 + i;
+        if (row >= rows) continue;
+        double *out = OUT + ((int64_t)c * n + sa + row) * cols;
+#pragma unroll
+        for (int j = 0; j < CW; ++j) {
+            const int col = cg * CW + j;
+            if (col < cols) out[col] -= acc[i][j];
+        }
+    }
+}
+
 }  // namespace pm
 
 static Err f32_copy(DBuf &dst, const DBuf &src, int64_t count, cudaStream_t st) {
@@ -274,7 +362,78 @@ static Err factors_f32(Factors &f, cudaStream_t st) {
     return ok();
 }
 
-Err peel_level_mixed(hm_ctx *c, int level, bool leaf) {
+static Err launch_update(const pm::CoarseT<float> *tab, int ntab, int side, int chi, const Coloring &g,
+                         const Cut &cl, const DBuf &item_tile, const DBuf &item_row, int64_t nitems, int cols, int r,
+                         int64_t n, double *OUT, cudaStream_t st) {
+    if (cols <= 32)
+        pm::k_peel_gemm<32><<<(unsigned)nitems, 128, 0, st>>>(tab, ntab, side, chi, g.pair_alpha.as<int>(),
+                                                              g.pair_color.as<int>(), cl.ent.as<int>(),
+                                                              item_tile.as<int64_t>(), item_row.as<int>(), nitems,
+                                                              cols, r, n, OUT);
+    else
+        pm::k_peel_gemm<64><<<(unsigned)nitems, 128, 0, st>>>(tab, ntab, side, chi, g.pair_alpha.as<int>(),
+                                                              g.pair_color.as<int>(), cl.ent.as<int>(),
+                                                              item_tile.as<int64_t>(), item_row.as<int>(), nitems,
+                                                              cols, r, n, OUT);
+    count_launch();
+    HM_LAUNCH("peel_gemm");
+    return ok();
+}
+
+static Err launch_update(const pm::CoarseT<double> *tab, int ntab, int side, int chi, const Coloring &g,
+                         const Cut &cl, const DBuf &item_tile, const DBuf &item_row, int64_t nitems, int cols, int r,
+                         int64_t n, double *OUT, cudaStream_t st) {
+    const size_t smem = (size_t)r * (pm::GEMM64_LDF + (cols <= 32 ? 32 : 64)) * sizeof(double);
+    if (cols <= 32) {
+        HM_CUDA(cudaFuncSetAttribute(pm::k_peel_gemm64<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        pm::k_peel_gemm64<32><<<(unsigned)nitems, 128, smem, st>>>(tab, ntab, side, chi, g.pair_alpha.as<int>(),
+                                                                   g.pair_color.as<int>(), cl.ent.as<int>(),
+                                                                   item_tile.as<int64_t>(), item_row.as<int>(),
+                                                                   nitems, cols, r, n, OUT);
+    } else {
+        HM_CUDA(cudaFuncSetAttribute(pm::k_peel_gemm64<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        pm::k_peel_gemm64<64><<<(unsigned)nitems, 128, smem, st>>>(tab, ntab, side, chi, g.pair_alpha.as<int>(),
+                                                                   g.pair_color.as<int>(), cl.ent.as<int>(),
+                                                                   item_tile.as<int64_t>(), item_row.as<int>(),
+                                                                   nitems, cols, r, n, OUT);
+    }
+    count_launch();
+    HM_LAUNCH("peel_gemm64");
+    return ok();
+}
+
+// the factors and Gaussians the peel of type R reads: FP32 copies for float,
+// the FP64 arrays themselves for double
+template <typename R> struct PeelData;
+template <> struct PeelData<float> {
+    static Err factors(Factors &f, cudaStream_t st) { return factors_f32(f, st); }
+    static const float *U(const Factors &f) { return f.U32.as<float>(); }
+    static const float *V(const Factors &f) { return f.V32.as<float>(); }
+    static const float *B(const Factors &f) { return f.B32.as<float>(); }
+    static Err gauss(hm_ctx *c, DBuf *G32, const float **G) {
+        HM_TRY(f32_copy(G32[0], c->GO, c->n * c->cfg.r, c->st));
+        HM_TRY(f32_copy(G32[1], c->GP, c->n * c->cfg.r, c->st));
+        G[0] = G32[0].as<float>();
+        G[1] = G32[1].as<float>();
+        return ok();
+    }
+    static constexpr int rows = 64;  // rows per update chunk
+};
+template <> struct PeelData<double> {
+    static Err factors(Factors &, cudaStream_t) { return ok(); }
+    static const double *U(const Factors &f) { return f.U.as<double>(); }
+    static const double *V(const Factors &f) { return f.V.as<double>(); }
+    static const double *B(const Factors &f) { return f.B.as<double>(); }
+    static Err gauss(hm_ctx *c, DBuf *, const double **G) {
+        G[0] = c->GO.as<double>();
+        G[1] = c->GP.as<double>();
+        return ok();
+    }
+    static constexpr int rows = pm::GEMM64_ROWS;
+};
+
+template <typename R> static Err peel_level_t(hm_ctx *c, int level, bool leaf) {
+    using PD = PeelData<R>;
     const int l = leaf ? c->L : level;
     const int idx = leaf ? c->L + 1 : level;
     const Coloring &g = c->colorings[idx];
@@ -285,20 +444,18 @@ Err peel_level_mixed(hm_ctx *c, int level, bool leaf) {
     cudaStream_t st = c->st;
     const int r = c->cfg.r;
     const int64_t n = c->n;
-    // FP32 Gaussians of this level (not used at the leaf: identity test matrices)
+    // Gaussians of this level (not used at the leaf: identity test matrices)
     DBuf G32[2];
-    if (!leaf) {
-        HM_TRY(f32_copy(G32[0], c->GO, n * r, st));
-        HM_TRY(f32_copy(G32[1], c->GP, n * r, st));
-    }
-    // work items: 64-row chunks of every tile
+    const R *Gl[2] = {nullptr, nullptr};
+    if (!leaf) HM_TRY(PD::gauss(c, G32, Gl));
+    // work items: chunks of PD::rows rows of every tile
     const int64_t ntiles = g.n_pairs;
     const int chi = g.n_colors;
     DBuf cnt, off, item_tile, item_row;
     HM_TRY(alloc(cnt, (ntiles + 1) * sizeof(int64_t)));
     HM_TRY(alloc(off, (ntiles + 1) * sizeof(int64_t)));
     pm::k_item_count<<<ceil_div(ntiles, 256), 256, 0, st>>>(g.pair_alpha.as<int>(), cl.ent.as<int>(), ntiles,
-                                                            cnt.as<int64_t>());
+                                                            PD::rows, cnt.as<int64_t>());
     count_launch();
     HM_LAUNCH("item_count");
     HM_TRY(scan_exclusive(cnt.as<int64_t>(), off.as<int64_t>(), ntiles, st));
@@ -306,8 +463,8 @@ Err peel_level_mixed(hm_ctx *c, int level, bool leaf) {
     HM_TRY(read_scalar(nitems, off.as<int64_t>() + ntiles, st));
     HM_TRY(alloc(item_tile, nitems * sizeof(int64_t)));
     HM_TRY(alloc(item_row, nitems * sizeof(int)));
-    pm::k_item_fill<<<ceil_div(ntiles, 256), 256, 0, st>>>(off.as<int64_t>(), ntiles, item_tile.as<int64_t>(),
-                                                           item_row.as<int>());
+    pm::k_item_fill<<<ceil_div(ntiles, 256), 256, 0, st>>>(off.as<int64_t>(), ntiles, PD::rows,
+                                                           item_tile.as<int64_t>(), item_row.as<int>());
     count_launch();
     HM_LAUNCH("item_fill");
 
@@ -336,7 +493,7 @@ Err peel_level_mixed(hm_ctx *c, int level, bool leaf) {
     }
 
     for (int side = 0; side < (leaf ? 1 : 2); ++side) {
-        std::vector<pm::Coarse> tab;
+        std::vector<pm::CoarseT<R>> tab;
         std::vector<DBuf> keep;  // X, offsets, T and live flags of every coarse level
         for (size_t i = 0; i < js.size(); ++i) {
             const int j = js[i];
@@ -344,7 +501,7 @@ Err peel_level_mixed(hm_ctx *c, int level, bool leaf) {
             const Coloring &gj = c->colorings[j];
             const Cut &cj = c->cuts[j];
             const int64_t np = f.n_pairs;
-            HM_TRY(factors_f32(f, st));
+            HM_TRY(PD::factors(f, st));
             DBuf xsz, xo, X, T, live;
             HM_TRY(alloc(xsz, (np + 1) * sizeof(int64_t)));
             HM_TRY(alloc(xo, (np + 1) * sizeof(int64_t)));
@@ -357,20 +514,19 @@ Err peel_level_mixed(hm_ctx *c, int level, bool leaf) {
             HM_TRY(scan_exclusive(xsz.as<int64_t>(), xo.as<int64_t>(), np, st));
             int64_t xtot = 0;
             HM_TRY(read_scalar(xtot, xo.as<int64_t>() + np, st));
-            HM_TRY(alloc(X, std::max<int64_t>(xtot, 1) * sizeof(float)));
+            HM_TRY(alloc(X, std::max<int64_t>(xtot, 1) * sizeof(R)));
             // CTAs per coarse pair: about one per level-l box inside the largest coarse box
             const int gy = std::min(256, std::max(1, cj.max_rows / std::max(1, std::min(cl.max_rows, 64))));
-            pm::k_peel_x32<<<dim3((unsigned)np, gy), 128, 0, st>>>(gj.pair_alpha.as<int>(), cj.int_idx.as<int>(), cj.ent.as<int>(),
-                                                     cl.ent.as<int>(), cl.pt2ent.as<int>(), kdim,
-                                                     side ? f.offU.as<int64_t>() : f.offV.as<int64_t>(),
-                                                     side ? f.U32.as<float>() : f.V32.as<float>(),
-                                                     leaf ? nullptr : G32[side].as<float>(), cols, leaf ? 1 : 0, side,
-                                                     xo.as<int64_t>(), X.as<float>());
+            pm::k_peel_xr<R><<<dim3((unsigned)np, gy), 128, 0, st>>>(
+                gj.pair_alpha.as<int>(), cj.int_idx.as<int>(), cj.ent.as<int>(), cl.ent.as<int>(),
+                cl.pt2ent.as<int>(), kdim, side ? f.offU.as<int64_t>() : f.offV.as<int64_t>(),
+                side ? PD::U(f) : PD::V(f), leaf ? nullptr : Gl[side], cols, leaf ? 1 : 0, side, xo.as<int64_t>(),
+                X.as<R>());
             count_launch();
-            HM_LAUNCH("peel_x32");
-            HM_TRY(alloc(T, std::max<int64_t>(nslots[i], 1) * r * cols * sizeof(float)));
+            HM_LAUNCH("peel_x");
+            HM_TRY(alloc(T, std::max<int64_t>(nslots[i], 1) * r * cols * sizeof(R)));
             HM_TRY(alloc(live, std::max<int64_t>(nslots[i], 1)));
-            pm::Coarse co;
+            pm::CoarseT<R> co;
             co.ent = cj.ent.as<int>();
             co.pt2ent = cj.pt2ent.as<int>();
             co.int_ptr = cj.int_ptr.as<int>();
@@ -381,19 +537,19 @@ Err peel_level_mixed(hm_ctx *c, int level, bool leaf) {
             co.offU = f.offU.as<int64_t>();
             co.offV = f.offV.as<int64_t>();
             co.offB = f.offB.as<int64_t>();
-            co.U = f.U32.as<float>();
-            co.V = f.V32.as<float>();
-            co.B = f.B32.as<float>();
+            co.U = PD::U(f);
+            co.V = PD::V(f);
+            co.B = PD::B(f);
             co.xoff = xo.as<int64_t>();
-            co.X = X.as<float>();
+            co.X = X.as<R>();
             co.base = bases[i].as<int64_t>();
-            co.T = T.as<float>();
+            co.T = T.as<R>();
             co.live = live.as<unsigned char>();
             if (nslots[i] > 0) {
                 const int64_t ncomb = (int64_t)cj.nc * chi;
-                const size_t smem = (size_t)pm::WARPS * r * cols * sizeof(float);
-                HM_CUDA(cudaFuncSetAttribute(pm::k_peel_T, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-                pm::k_peel_T<<<ceil_div(ncomb, pm::WARPS), pm::WARPS * 32, smem, st>>>(
+                const size_t smem = (size_t)pm::WARPS * r * cols * sizeof(R);
+                HM_CUDA(cudaFuncSetAttribute(pm::k_peel_T<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+                pm::k_peel_T<R><<<ceil_div(ncomb, pm::WARPS), pm::WARPS * 32, smem, st>>>(
                     co, ncomb, chi, side, cols, r, cl.pt2ent.as<int>(), g.act_ptr.as<int>(), g.act_box.as<int>());
                 count_launch();
                 HM_LAUNCH("peel_T");
@@ -405,23 +561,16 @@ Err peel_level_mixed(hm_ctx *c, int level, bool leaf) {
             keep.push_back(std::move(live));
         }
         DBuf tabd;
-        HM_TRY(alloc(tabd, tab.size() * sizeof(pm::Coarse)));
-        HM_CUDA(cudaMemcpyAsync(tabd.p, tab.data(), tab.size() * sizeof(pm::Coarse), cudaMemcpyHostToDevice, st));
+        HM_TRY(alloc(tabd, tab.size() * sizeof(pm::CoarseT<R>)));
+        HM_CUDA(cudaMemcpyAsync(tabd.p, tab.data(), tab.size() * sizeof(pm::CoarseT<R>), cudaMemcpyHostToDevice, st));
         double *OUT = side ? c->cur.Z.as<double>() : c->cur.Y.as<double>();
-        if (nitems > 0) {
-            if (cols <= 32)
-                pm::k_peel_gemm<32><<<(unsigned)nitems, 128, 0, st>>>(
-                    tabd.as<pm::Coarse>(), (int)tab.size(), side, chi, g.pair_alpha.as<int>(), g.pair_color.as<int>(),
-                    cl.ent.as<int>(), item_tile.as<int64_t>(), item_row.as<int>(), nitems, cols, r, n, OUT);
-            else
-                pm::k_peel_gemm<64><<<(unsigned)nitems, 128, 0, st>>>(
-                    tabd.as<pm::Coarse>(), (int)tab.size(), side, chi, g.pair_alpha.as<int>(), g.pair_color.as<int>(),
-                    cl.ent.as<int>(), item_tile.as<int64_t>(), item_row.as<int>(), nitems, cols, r, n, OUT);
-            count_launch();
-            HM_LAUNCH("peel_gemm");
-        }
+        if (nitems > 0) HM_TRY(launch_update(tabd.as<pm::CoarseT<R>>(), (int)tab.size(), side, chi, g, cl, item_tile,
+                                             item_row, nitems, cols, r, n, OUT, st));
     }
     return ok();
 }
+
+Err peel_level_mixed(hm_ctx *c, int level, bool leaf) { return peel_level_t<float>(c, level, leaf); }
+Err peel_level_fp64(hm_ctx *c, int level, bool leaf) { return peel_level_t<double>(c, level, leaf); }
 
 }  // namespace hm
