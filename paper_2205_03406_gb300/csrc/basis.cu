@@ -341,9 +341,9 @@ __global__ void __launch_bounds__(128) k_qr_warp(const int *tile_alpha, const in
 
 // ---------------------------------------------------------------------------
 // HM_MIXED_BF16X6_F32: FP32 QR with the tile in shared memory (the samples it
-// factors carry FP32-level rounding already).  The CTA's 128 threads work on
+// factors carry FP32-level rounding already).  The CTA's threads (128 or 512) work on
 // column t % RP (RP = 32 for r <= 32, else 64) and on the rows i = t / RP
-// (mod 128 / RP) in the column passes; partial sums over the row groups are
+// (mod blockDim / RP) in the column passes; partial sums over the row groups are
 // added in group order.
 // ---------------------------------------------------------------------------
 
@@ -351,7 +351,7 @@ __global__ void __launch_bounds__(128) k_qr_warp(const int *tile_alpha, const in
 // over the row groups: the result for column t (t < r) is returned to thread t
 __device__ __forceinline__ void col_dots(const float *qa, int m, int r, int i0, int ca, int cb_lo, int cb_hi,
                                          bool square, float (*red)[64], float *out) {
-    const int t = threadIdx.x, RP = r <= 32 ? 32 : 64, NG = 128 / RP, cj = t % RP, grp = t / RP;
+    const int t = threadIdx.x, RP = r <= 32 ? 32 : 64, NG = (int)blockDim.x / RP, cj = t % RP, grp = t / RP;
     float a = 0.0f;
     if (cj >= cb_lo && cj < cb_hi) {
         if (square)
@@ -371,7 +371,7 @@ __device__ __forceinline__ void col_dots(const float *qa, int m, int r, int i0, 
 
 // A(i, j) -= tau v_i w_j for i >= s, j in (s, jhi); v_s = 1, v_i = A(i, s) below
 __device__ __forceinline__ void reflect(float *qa, int m, int r, int s, int jhi, float ts, const float *wv) {
-    const int t = threadIdx.x, RP = r <= 32 ? 32 : 64, NG = 128 / RP, cj = t % RP, grp = t / RP;
+    const int t = threadIdx.x, RP = r <= 32 ? 32 : 64, NG = (int)blockDim.x / RP, cj = t % RP, grp = t / RP;
     if (cj > s && cj < jhi) {
         const float w = ts * wv[cj];
         for (int i = s + grp; i < m; i += NG) {
@@ -386,7 +386,7 @@ __device__ __forceinline__ void reflect(float *qa, int m, int r, int s, int jhi,
 // kmax steps, stopping by the rank or tolerance rule; on return columns
 // 0..k-1 hold Q_k with R_jj >= 0, and every thread returns k.
 __device__ int qr32_pivoted(float *qa, int m, int r, int kmax, int rank, double tol) {
-    __shared__ float red[4][64], nrm[64], wv[64], tau[64], beta[64];
+    __shared__ float red[16][64], nrm[64], wv[64], tau[64], beta[64];
     __shared__ float sh_sc;
     __shared__ int sh_piv, sh_stop;
     const int t = threadIdx.x;
@@ -425,7 +425,7 @@ __device__ int qr32_pivoted(float *qa, int m, int r, int kmax, int rank, double 
         const int piv = sh_piv;
         const float sc = sh_sc, ts = tau[s], bs = beta[s];
         // swap columns s and piv, scale the reflector, set R_ss
-        for (int i = t; i < m; i += 128) {
+        for (int i = t; i < m; i += blockDim.x) {
             float vs = qa[i * r + s];
             if (piv != s) {
                 const float vp = qa[i * r + piv];
@@ -453,7 +453,7 @@ __device__ int qr32_pivoted(float *qa, int m, int r, int kmax, int rank, double 
             __syncthreads();
             reflect(qa, m, r, j, k, tj, wv);
         }
-        for (int i = t; i < m; i += 128) {
+        for (int i = t; i < m; i += blockDim.x) {
             float v;
             if (i < j) v = 0.0f;
             else if (i == j) v = 1.0f - tj;
@@ -462,7 +462,7 @@ __device__ int qr32_pivoted(float *qa, int m, int r, int kmax, int rank, double 
         }
         __syncthreads();
     }
-    for (int o = t; o < m * k; o += 128) {  // R_jj >= 0
+    for (int o = t; o < m * k; o += blockDim.x) {  // R_jj >= 0
         const int j = o % k;
         if (beta[j] < 0.0f) qa[(o / k) * r + j] = -qa[(o / k) * r + j];
     }
@@ -470,22 +470,22 @@ __device__ int qr32_pivoted(float *qa, int m, int r, int kmax, int rank, double 
     return k;
 }
 
-// One CTA per tile of at most max_rows rows; Q_k back to the FP64 tile.
-__global__ void __launch_bounds__(128) k_qr32(const int *tile_alpha, const int *tile_beta, const int *tile_color,
+// One CTA per tile of min_rows < m <= max_rows rows; Q_k back to the FP64 tile.
+__global__ void __launch_bounds__(512) k_qr32(const int *tile_alpha, const int *tile_beta, const int *tile_color,
                                               const int *ent, int64_t n, int r, int cap, int rank, double tol,
-                                              double *Ybase, int *kout, int max_rows) {
+                                              double *Ybase, int *kout, int min_rows, int max_rows) {
     extern __shared__ float qa[];  // m x r, leading dimension r
     const int64_t p = blockIdx.x;
     const int *e = ent + (int64_t)tile_alpha[p] * ENT_FIELDS;
     const int m = e[4] - e[3];
-    if (m > max_rows) return;  // a tall-skinny or FP64 kernel factors this tile
+    if (m <= min_rows || m > max_rows) return;  // another launch factors this tile
     double *Ag = Ybase + ((int64_t)tile_color[p] * n + e[3]) * r;
     const int *eb = ent + (int64_t)tile_beta[p] * ENT_FIELDS;
     const int kmax = min(min(m, eb[4] - eb[3]), min(r, cap));
-    for (int o = threadIdx.x; o < m * r; o += 128) qa[o] = (float)Ag[o];
+    for (int o = threadIdx.x; o < m * r; o += blockDim.x) qa[o] = (float)Ag[o];
     __syncthreads();
     const int k = qr32_pivoted(qa, m, r, kmax, rank, tol);
-    for (int o = threadIdx.x; o < m * k; o += 128) Ag[(int64_t)(o / k) * r + o % k] = (double)qa[(o / k) * r + o % k];
+    for (int o = threadIdx.x; o < m * k; o += blockDim.x) Ag[(int64_t)(o / k) * r + o % k] = (double)qa[(o / k) * r + o % k];
     if (threadIdx.x == 0) kout[p] = k;
 }
 
@@ -525,18 +525,18 @@ __global__ void k_ts_fill(const int *tile_alpha, const int *ent, const int64_t *
 
 // (1) unpivoted QR of one block; R_b (r x r, zero below the diagonal) into
 // the stack at [blk][r][r], the reflectors over the block, tau at [blk][r]
-__global__ void __launch_bounds__(128) k_ts_block(const int *tile_alpha, const int *tile_color, const int *ent,
+__global__ void __launch_bounds__(512) k_ts_block(const int *tile_alpha, const int *tile_color, const int *ent,
                                                   int64_t n, int r, double *Ybase, const int64_t *blk_tile,
                                                   const int *blk_row0, const int *blk_rows, float *Rstack,
                                                   float *taus) {
     extern __shared__ float qa[];
-    __shared__ float red[4][64], nrm[64], wv[64];
+    __shared__ float red[16][64], nrm[64], wv[64];
     const int64_t blk = blockIdx.x;
     const int64_t p = blk_tile[blk];
     const int *e = ent + (int64_t)tile_alpha[p] * ENT_FIELDS;
     const int m = blk_rows[blk], t = threadIdx.x;
     double *Ag = Ybase + ((int64_t)tile_color[p] * n + e[3] + blk_row0[blk]) * r;
-    for (int o = t; o < m * r; o += 128) qa[o] = (float)Ag[o];
+    for (int o = t; o < m * r; o += blockDim.x) qa[o] = (float)Ag[o];
     __syncthreads();
     const int steps = min(m, r);
     for (int s = 0; s < steps; ++s) {
@@ -548,7 +548,7 @@ __global__ void __launch_bounds__(128) k_ts_block(const int *tile_alpha, const i
             ts = (b - x0) / b;
             sc = 1.0f / (x0 - b);
         }
-        for (int i = s + 1 + t; i < m; i += 128) qa[i * r + s] *= sc;
+        for (int i = s + 1 + t; i < m; i += blockDim.x) qa[i * r + s] *= sc;
         __syncthreads();
         if (t == 0) {
             taus[blk * r + s] = ts;
@@ -559,17 +559,17 @@ __global__ void __launch_bounds__(128) k_ts_block(const int *tile_alpha, const i
         __syncthreads();
         reflect(qa, m, r, s, r, ts, wv);
     }
-    for (int s = steps + t; s < r; s += 128) taus[blk * r + s] = 0.0f;
+    for (int s = steps + t; s < r; s += blockDim.x) taus[blk * r + s] = 0.0f;
     float *R = Rstack + blk * r * r;
-    for (int o = t; o < r * r; o += 128) {
+    for (int o = t; o < r * r; o += blockDim.x) {
         const int i = o / r, j = o % r;
         R[o] = (i <= j && i < m) ? qa[i * r + j] : 0.0f;
     }
-    for (int o = t; o < m * r; o += 128) Ag[o] = (double)qa[o];
+    for (int o = t; o < m * r; o += blockDim.x) Ag[o] = (double)qa[o];
 }
 
 // (2) pivoted QR of the stacked R_b of one tile, in place in the stack
-__global__ void __launch_bounds__(128) k_ts_top(const int *tile_alpha, const int *tile_beta, const int *ent,
+__global__ void __launch_bounds__(512) k_ts_top(const int *tile_alpha, const int *tile_beta, const int *ent,
                                                 int64_t np, int r, int cap, int rank, double tol, const int64_t *off,
                                                 float *Rstack, int *kout) {
     extern __shared__ float qa[];
@@ -580,20 +580,20 @@ __global__ void __launch_bounds__(128) k_ts_top(const int *tile_alpha, const int
     const int m = e[4] - e[3], ms = nb * r;
     const int kmax = min(min(m, eb[4] - eb[3]), min(r, cap));
     float *S = Rstack + off[p] * r * r;
-    for (int o = threadIdx.x; o < ms * r; o += 128) qa[o] = S[o];
+    for (int o = threadIdx.x; o < ms * r; o += blockDim.x) qa[o] = S[o];
     __syncthreads();
     const int k = qr32_pivoted(qa, ms, r, kmax, rank, tol);
-    for (int o = threadIdx.x; o < ms * r; o += 128) S[o] = qa[o];
+    for (int o = threadIdx.x; o < ms * r; o += blockDim.x) S[o] = qa[o];
     if (threadIdx.x == 0) kout[p] = k;
 }
 
 // (3) U_b = Q_b [Q_S(block rows, 0:k); 0] into the block's rows, columns 0..k-1
-__global__ void __launch_bounds__(128) k_ts_form(const int *tile_alpha, const int *tile_color, const int *ent,
+__global__ void __launch_bounds__(512) k_ts_form(const int *tile_alpha, const int *tile_color, const int *ent,
                                                  int64_t n, int r, double *Ybase, const int64_t *blk_tile,
                                                  const int *blk_row0, const int *blk_rows, const float *Rstack,
                                                  const float *taus, const int *kout) {
     extern __shared__ float qa[];  // reflectors m x r, then X m x k (ld r)
-    __shared__ float red[4][64], wv[64];
+    __shared__ float red[16][64], wv[64];
     const int64_t blk = blockIdx.x;
     const int64_t p = blk_tile[blk];
     const int k = kout[p];
@@ -603,7 +603,7 @@ __global__ void __launch_bounds__(128) k_ts_form(const int *tile_alpha, const in
     double *Ag = Ybase + ((int64_t)tile_color[p] * n + e[3] + blk_row0[blk]) * r;
     float *X = qa + m * r;
     const float *QS = Rstack + blk * r * r;  // this block's r rows of Q_S
-    for (int o = t; o < m * r; o += 128) {
+    for (int o = t; o < m * r; o += blockDim.x) {
         const int i = o / r, j = o % r;
         qa[o] = (float)Ag[o];
         X[o] = (j < k && i < r) ? QS[i * r + j] : 0.0f;
@@ -613,7 +613,7 @@ __global__ void __launch_bounds__(128) k_ts_form(const int *tile_alpha, const in
     for (int s = steps - 1; s >= 0; --s) {
         const float ts = taus[blk * r + s];
         // w_c = X(s, c) + sum_{i > s} v_i X(i, c); X(i, c) -= tau v_i w_c
-        const int RP = r <= 32 ? 32 : 64, NG = 128 / RP, cj = t % RP, grp = t / RP;
+        const int RP = r <= 32 ? 32 : 64, NG = (int)blockDim.x / RP, cj = t % RP, grp = t / RP;
         float a = 0.0f;
         if (cj < k)
             for (int i = s + 1 + grp; i < m; i += NG) a = fmaf(qa[i * r + s], X[i * r + cj], a);
@@ -632,7 +632,7 @@ __global__ void __launch_bounds__(128) k_ts_form(const int *tile_alpha, const in
             }
         __syncthreads();
     }
-    for (int o = t; o < m * k; o += 128) Ag[(int64_t)(o / k) * r + o % k] = (double)X[(o / k) * r + o % k];
+    for (int o = t; o < m * k; o += blockDim.x) Ag[(int64_t)(o / k) * r + o % k] = (double)X[(o / k) * r + o % k];
 }
 
 __global__ void k_factor_sizes(const int *pair_alpha, const int *pair_col, const int *pairT, const int *kY,
@@ -892,20 +892,26 @@ Err bases_and_cores(hm_ctx *c, int level) {
         }
         if (mixed) {
             if (nblk > 0) {
-                k_ts_block<<<(unsigned)nblk, 128, ts_rows * r * sizeof(float), st>>>(
+                k_ts_block<<<(unsigned)nblk, 512, ts_rows * r * sizeof(float), st>>>(
                     g.pair_alpha.as<int>(), g.pair_color.as<int>(), cu.ent.as<int>(), n, r, T, blk_tile.as<int64_t>(),
                     blk_row0.as<int>(), blk_rows.as<int>(), rstack.as<float>(), taus.as<float>()); ::hm::count_launch();
-                k_ts_top<<<(unsigned)np, 128, (size_t)nb_top * r * r * sizeof(float), st>>>(
+                k_ts_top<<<(unsigned)np, 512, (size_t)nb_top * r * r * sizeof(float), st>>>(
                     g.pair_alpha.as<int>(), cu.int_idx.as<int>(), cu.ent.as<int>(), np, r, cap, c->cfg.rank,
                     c->cfg.tol, ts_off.as<int64_t>(), rstack.as<float>(), kk); ::hm::count_launch();
-                k_ts_form<<<(unsigned)nblk, 128, 2 * ts_rows * r * sizeof(float), st>>>(
+                k_ts_form<<<(unsigned)nblk, 512, 2 * ts_rows * r * sizeof(float), st>>>(
                     g.pair_alpha.as<int>(), g.pair_color.as<int>(), cu.ent.as<int>(), n, r, T, blk_tile.as<int64_t>(),
                     blk_row0.as<int>(), blk_rows.as<int>(), rstack.as<float>(), taus.as<float>(), kk); ::hm::count_launch();
                 HM_LAUNCH("tall-skinny qr");
             }
+            // tiles up to 256 rows with 128 threads, taller ones with 512
             k_qr32<<<(int)np, 128, qr32_smem, st>>>(g.pair_alpha.as<int>(), cu.int_idx.as<int>(),
                                                     g.pair_color.as<int>(), cu.ent.as<int>(), n, r, cap, c->cfg.rank,
-                                                    c->cfg.tol, T, kk, qr32_rows); ::hm::count_launch();
+                                                    c->cfg.tol, T, kk, 0, std::min(256, qr32_rows)); ::hm::count_launch();
+            if (cu.max_rows > 256 && qr32_rows > 256) {
+                k_qr32<<<(int)np, 512, qr32_smem, st>>>(g.pair_alpha.as<int>(), cu.int_idx.as<int>(),
+                                                        g.pair_color.as<int>(), cu.ent.as<int>(), n, r, cap,
+                                                        c->cfg.rank, c->cfg.tol, T, kk, 256, qr32_rows); ::hm::count_launch();
+            }
         } else {
             k_qr_warp<<<ceil_div(np, 4), 128, 0, st>>>(g.pair_alpha.as<int>(), cu.int_idx.as<int>(),
                                                        g.pair_color.as<int>(), cu.ent.as<int>(), n, r, cap,
