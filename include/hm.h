@@ -168,7 +168,10 @@ hm_status hm_color(hm_ctx *ctx, int level, int *n_colors);
  * Algorithm 4.1, sampling step of one level: draw the colour-masked Gaussian
  * test matrices Omega_l and Psi_l (identity blocks for HM_LEVEL_LEAF) and store
  * Y = A Omega_l and Z = A^* Psi_l (not yet peeled) in the context.
- * Requires hm_color(level) first.
+ * Requires hm_color(level) first.  In the two mixed-precision modes the
+ * built-in kernel operator computes only the rows the method reads: for
+ * every colour c, the rows I_alpha of its pairs (alpha, beta) (the sample
+ * tiles, Section 4.1.2); the other rows of the stored samples are unspecified.
  */
 hm_status hm_sample(hm_ctx *ctx, const hm_op *op, int level);
 
@@ -203,7 +206,8 @@ enum {
     HM_X_VERTEX_COLOR = 7,/* int32[n_vertices] */
     HM_X_VERTEX_BETA = 8, /* int32[n_vertices] */
     HM_X_GAUSS = 9,       /* double[2][n][r]: Omega-side then Psi-side G, sorted order */
-    HM_X_SAMPLE_Y = 10,   /* double[chi][n][r']: colour-major, sorted order (r' = r or m_max) */
+    HM_X_SAMPLE_Y = 10,   /* double[chi][n][r']: colour-major, sorted order (r' = r or m_max);
+                             rows outside the colour's tiles: see hm_sample */
     HM_X_SAMPLE_Z = 11,   /* double[chi][n][r] */
     HM_X_PAIR_RANKS = 12, /* int32[n_pairs][2]: k_U, k_V */
     HM_X_FACTORS = 13,    /* double: U arena, V arena, B arena concatenated */
