@@ -403,7 +403,7 @@ class OracleSample:
                 t_bb += (time.perf_counter() - t1) * (n / rows_per_level)
         est = self.t_struct + t_bb
         cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
-        return {"value": round(1.0 / est, 6), "unit": "jobs/s", "cores": cores, "kind": "oracle",
+        return {"value": float(f"{1.0 / est:.4g}"), "unit": "jobs/s", "cores": cores, "kind": "oracle",
                 "sample": f"oracle tree + all colourings timed in full ({self.t_struct:.1f} s); black-box "
                           f"product for {rows_per_level} random rows of each level ({len(self.mats)} levels), "
                           f"extrapolated to all {n} rows ({t_bb:.1f} s); peel/QR/cores/leaf not timed, so "
@@ -430,11 +430,12 @@ def run_reference(args):
         ests.append(orc.sample(40, seed=100 + k))
     wall = time.perf_counter() - t0
     est = sum(e["seconds_estimate"] for e in ests) / len(ests)
-    value = round(1.0 / est, 6)
+    value = float(f"{1.0 / est:.4g}")
     out = {"metric": METRIC, "value": value, "unit": "jobs/s", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": round(1e3 * est, 1), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded torus point cloud)",
-           "impl": "reference", "config": dict(config_of(args, w), parallelism="cpu oracle"),
+           "impl": "reference",
+           "config": dict(config_of(args, w), precision="FP64 CPU oracle (plain loops, numpy)", parallelism="cpu oracle"),
            "cpu_baseline": {"value": value, "unit": "jobs/s", "cores": ests[-1]["cores"], "kind": "oracle",
                             "sample": ests[-1]["sample"]},
            "e2e": {"value": value, "unit": "jobs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
