@@ -46,9 +46,9 @@ PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustain
 
 # dram bytes (read + write) of the tensor-core contraction kernel per evaluated
 # kernel entry, from the ncu capture summarised in profiles/ (scaled by the
-# entries a step evaluates); valid only for the source whose sha256 prefix is
-# recorded here, None until that source has been captured
-TRAFFIC = {"file": "paper_2205_03406_gb300/csrc/sample_tc.cu", "sha256": "c686738267b260f1", "bytes_per_eval": 0.5968}
+# entries a step evaluates); valid only for the source whose sha256 prefix
+# (full-line comments excluded, see source_sha) is recorded here
+TRAFFIC = {"file": "paper_2205_03406_gb300/csrc/sample_tc.cu", "sha256": "ffc9f6e9401545c1", "bytes_per_eval": 0.5968}
 
 
 def parse():
@@ -146,6 +146,14 @@ def peaks():
         return PEAKS_FALLBACK, "fallback"
 
 
+def source_sha(path: str) -> str:
+    """sha256 prefix of a source file without its full-line // comments (a
+    comment edit does not change the compiled kernel the counters describe)."""
+    with open(path, "rb") as f:
+        lines = [ln for ln in f.read().decode().splitlines() if not ln.strip().startswith("//")]
+    return hashlib.sha256("\n".join(ln.rstrip() for ln in lines).encode()).hexdigest()[:16]
+
+
 def roofline_tc(info, r: int):
     """Tensor-core contraction: every evaluated kernel entry (a row of a colour's
     sample tiles x one of its active rows) feeds r Y and r Z outputs, 4 r useful
@@ -160,7 +168,7 @@ def roofline_tc(info, r: int):
     traffic = None
     try:
         src_path = os.path.join(ROOT, TRAFFIC["file"])
-        sha = hashlib.sha256(open(src_path, "rb").read()).hexdigest()[:16]
+        sha = source_sha(src_path)
         if TRAFFIC["sha256"] == sha and TRAFFIC["bytes_per_eval"]:
             traffic = round(TRAFFIC["bytes_per_eval"] * info.tc_kernel_evals / max(launches, 1))
     except OSError:

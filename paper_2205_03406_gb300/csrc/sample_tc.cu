@@ -1,26 +1,31 @@
 // Mixed-precision black-box contraction on the 5th-generation tensor cores
-// (tcgen05, sm_103a): for colour c and a tile of 128 rows,
-//     [Y | Z](tile, c) = sum_{j in rows(c)} K(x_i, x_j) [G^Omega_j | G^Psi_j],
+// (tcgen05, sm_103a): for colour c and a block of 128 of its output rows (the
+// rows of its sample tiles, Section 4.1.2),
+//     [Y | Z](rows, c) = sum_{j in rows(c)} K(x_i, x_j) [G^Omega_j | G^Psi_j],
 // the sampling step of Algorithm 4.1 with the kernel matrix evaluated on the fly.
 //
-// Precision (HM_MIXED_BF16X6): K is evaluated in FP32 from double-float point
+// Precision (both mixed modes): K is evaluated in FP32 from double-float point
 // coordinates (x = hi + lo, both FP32), so differences of nearby points keep
 // FP32 accuracy; K and G are split into three BF16 pieces (h + m + l carries
 // 24 bits) and the six products hh, hm, mh, hl, mm, lh accumulate in FP32 in
-// tensor memory; the epilogue sums them small-to-large and writes FP64.
+// tensor memory, merged into three accumulators (hh | hm + mh | hl + mm + lh);
+// every two chunks the producers add them into double-float registers, and
+// the epilogue writes FP64.
 //
 // Per level a pack kernel writes, for every colour, chunks of 64 active rows
 // in the exact shared-memory image the tensor core reads: the three BF16
 // pieces of [G^Omega | G^Psi]^T (K-major, 128-byte swizzle) followed by the
-// chunk's double-float coordinates.  The main kernel (one CTA per (tile,
-// colour)) streams chunks through two shared-memory stages:
-//   - one thread issues cp.async.bulk (TMA) copies of the next chunk,
-//   - eight producer warps evaluate the 128 x 64 kernel tile, split it and
-//     store it swizzled, then arrive on an mbarrier,
+// chunk's double-float coordinates.  The main kernel (one CTA per 128 output
+// rows of a colour) streams chunks through two shared-memory stages:
+//   - one thread of the TMA warp issues cp.async.bulk copies of the next chunk,
+//   - sixteen producer warps evaluate the 128 x 64 kernel tile with packed
+//     FP32x2 arithmetic, split it and store it swizzled, then arrive on an
+//     mbarrier,
 //   - one thread of the MMA warp issues tcgen05.mma (M = 128, K = 16 per
 //     instruction, three instructions per K step: A_h x [B_h B_m B_l],
 //     A_m x [B_h B_m], A_l x B_h) and tcgen05.commit frees the stage,
-//   - the epilogue reads the accumulators with tcgen05.ld.
+//   - the producers read the accumulators with tcgen05.ld (promotion and
+//     epilogue).
 // Every mbarrier wait is bounded; on expiry a status word is set and the CTA
 // drains and frees its tensor memory before returning.
 #include "ctx.cuh"
