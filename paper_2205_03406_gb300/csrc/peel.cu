@@ -1,5 +1,9 @@
 // Peeling (Section 4.1.2, Algorithm 4.1): remove the contribution of the
-// coarser levels already compressed from the samples of cut level l,
+// coarser levels already compressed from the samples of cut level l.  Colours
+// of up to 64 columns (every admissible level, and leaves of up to 64 points)
+// go to peel_mixed.cu, which forms T = B W once per (coarse pair, colour), in
+// FP32 or FP64; this file holds that dispatch and the per-tile FP64 peel that
+// serves wider leaf colours:
 //     Y_l -= A^(l-1) Omega_l,   Z_l -= A^(l-1)* Psi_l,
 // where A^(l-1) holds the factors U B V^T of every admissible pair of levels
 // 2..l-1 (2..L for the leaf step).  Only the tiles that a pair of level l reads
