@@ -67,3 +67,41 @@ def test_no_cpu_fallback_in_product_package():
             if f.endswith((".py", ".cu", ".cuh", ".h")):
                 src = open(os.path.join(dirpath, f)).read()
                 assert "oracle" not in src.replace("oracle's", ""), f
+
+
+def test_call_order_and_argument_checks_without_gpu():
+    """The C ABI's state machine and argument checks (no device work is done
+    before they pass): out-of-order calls return HM_ESTATE, null pointers and
+    bad sizes HM_EINVAL, and the context stays destroyable."""
+    import ctypes
+
+    import paper_2205_03406_gb300 as hm
+    L = hm.lib()
+    assert L.hm_color(None, 2, None) == hm.HM_EINVAL
+    assert L.hm_destroy(None) == hm.HM_OK
+    for prec in (hm.HM_FP64, hm.HM_MIXED_BF16X6, hm.HM_MIXED_BF16X6_F32):
+        ctx = hm.hm_create(hm.Settings(d=3, leaf_size=16, r=8, rank=4, precision=prec).to_c())
+        try:
+            nc = ctypes.c_int(0)
+            op = hm.kernel_op(hm.HM_K_LAPLACE3D)
+            e = ctypes.c_double(0.0)
+            size = ctypes.c_size_t(0)
+            info = hm.hm_info()
+            # nothing is built yet
+            assert L.hm_color(ctx, 2, ctypes.byref(nc)) == hm.HM_ESTATE
+            assert L.hm_sample(ctx, ctypes.byref(op), 2) == hm.HM_ESTATE
+            assert L.hm_compress(ctx, ctypes.byref(op)) == hm.HM_ESTATE
+            assert L.hm_apply(ctx, ctypes.c_void_p(16), ctypes.c_void_p(16), 1, 0) == hm.HM_ESTATE
+            assert L.hm_apply_noalloc(ctx, ctypes.c_void_p(16), ctypes.c_void_p(16), 1, 0) == hm.HM_ESTATE
+            assert L.hm_relerr(ctx, ctypes.byref(op), 20, ctypes.byref(e)) == hm.HM_ESTATE
+            assert L.hm_export(ctx, hm.HM_X_PERM, 0, None, ctypes.byref(size)) == hm.HM_ESTATE
+            assert L.hm_get_info(ctx, ctypes.byref(info)) == hm.HM_OK
+            # null pointers and bad sizes
+            assert L.hm_tree_build(ctx, None, 10) == hm.HM_EINVAL
+            assert "tree_build" in L.hm_last_error(ctx).decode()
+            assert L.hm_tree_build(ctx, ctypes.c_void_p(16), 0) == hm.HM_EINVAL
+            assert L.hm_sample(ctx, None, 2) == hm.HM_EINVAL
+            assert L.hm_compress(ctx, None) == hm.HM_EINVAL
+            assert L.hm_get_info(ctx, None) == hm.HM_EINVAL
+        finally:
+            assert L.hm_destroy(ctx) == hm.HM_OK
