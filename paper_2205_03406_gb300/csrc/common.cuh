@@ -50,6 +50,12 @@ extern thread_local cudaStream_t g_alloc_stream;
 void count_launch();
 long long launches_so_far();
 
+// Host-side fault injection for the error-path tests: with the environment
+// variable HM_FAULT_ALLOC_AFTER=k set when the library is loaded, the device
+// allocation after k successful ones fails once with HM_ENOMEM (before any
+// CUDA call is made for it); unset, this is never true.
+bool fault_alloc_now();
+
 // A device allocation: move-only, freed (stream-ordered) when it goes out of
 // scope, so temporaries of a call never outlive it and never force a device
 // synchronisation.
@@ -85,6 +91,7 @@ struct DBuf {
 inline Err alloc(DBuf &b, size_t bytes) {
     b.release();
     if (bytes == 0) bytes = 16;
+    if (fault_alloc_now()) return fail(HM_ENOMEM, "injected allocation failure (HM_FAULT_ALLOC_AFTER)");
     cudaError_t e = cudaMallocAsync(&b.p, bytes, g_alloc_stream);
     if (e != cudaSuccess) {
         cudaGetLastError();

@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 
 #include <atomic>
@@ -16,6 +17,16 @@ namespace hm {
 thread_local cudaStream_t g_alloc_stream = nullptr;
 static std::atomic<long long> g_launches{0};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+// allocations left before the injected failure; -1: injection off
+static std::atomic<long long> g_alloc_countdown{[] {
+    const char *s = getenv("HM_FAULT_ALLOC_AFTER");
+    return s && *s ? atoll(s) : -1ll;
+}()};
+bool fault_alloc_now() {
+    if (g_alloc_countdown.load(std::memory_order_relaxed) < 0) return false;
+    return g_alloc_countdown.fetch_sub(1, std::memory_order_relaxed) == 0;  // fires once, then stays off
+}
 long long launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
 }
 

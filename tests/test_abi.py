@@ -105,3 +105,27 @@ def test_call_order_and_argument_checks_without_gpu():
             assert L.hm_get_info(ctx, None) == hm.HM_EINVAL
         finally:
             assert L.hm_destroy(ctx) == hm.HM_OK
+
+
+def test_injected_allocation_failure_without_gpu(tmp_path):
+    """Host-side fault injection (HM_FAULT_ALLOC_AFTER): the first device
+    allocation of hm_tree_build fails with HM_ENOMEM before any CUDA call, the
+    error message says so, and the context is still destroyable."""
+    import subprocess
+    import sys
+    script = tmp_path / "inject.py"
+    script.write_text(
+        "import sys, ctypes\n"
+        f"sys.path.insert(0, {ROOT!r})\n"
+        "import paper_2205_03406_gb300 as hm\n"
+        "L = hm.lib()\n"
+        "ctx = hm.hm_create(hm.Settings(d=3, leaf_size=16, r=8, rank=4).to_c())\n"
+        "st = L.hm_tree_build(ctx, ctypes.c_void_p(16), 10)\n"
+        "msg = L.hm_last_error(ctx).decode()\n"
+        "assert st == hm.HM_ENOMEM, st\n"
+        "assert 'injected' in msg, msg\n"
+        "assert L.hm_destroy(ctx) == hm.HM_OK\n"
+        "print('ok')\n")
+    env = dict(os.environ, HM_FAULT_ALLOC_AFTER="0")
+    out = subprocess.run([sys.executable, str(script)], env=env, capture_output=True, text=True, timeout=120)
+    assert out.returncode == 0 and "ok" in out.stdout, out.stdout + out.stderr
