@@ -144,7 +144,14 @@ typedef struct {
                                  (the rows of its sample tiles) x its active rows */
 } hm_info;
 
-/* Create a context.  cfg is copied.  stream: a cudaStream_t or NULL. */
+/*
+ * Create a context for one compression job.  cfg is copied (Section 2.5 for r,
+ * p, rank and tol; Section 3 for d, leaf_size, uniform_depth).  stream: a
+ * cudaStream_t or NULL.  *out receives the context, owned by the caller until
+ * hm_destroy.  Errors: HM_EINVAL (null out or cfg; d not 1..3; leaf_size < 1;
+ * r not 1..64; not exactly one of rank > 0 and tol > 0; rank > r; with tol,
+ * p not in 0..r-1; unknown precision; uniform_depth not 0..21), HM_ENOMEM.
+ */
 hm_status hm_create(hm_ctx **out, const hm_config *cfg, void *stream);
 
 /* Free the context and everything it owns.  Safe on NULL and after errors. */
@@ -153,14 +160,19 @@ hm_status hm_destroy(hm_ctx *ctx);
 /*
  * Section 3: cluster tree over n points (points_dev: device, n x d row-major
  * FP64, original order), neighbour and interaction lists of every cut.  The
- * points are copied into the context (permuted into Morton order).
+ * points are copied into the context (permuted into Morton order); a second
+ * call starts a new job on the same context.  Errors: HM_EINVAL (null ctx or
+ * points, n < 1 or n > 2^30), HM_ENOMEM, HM_ECUDA.
  */
 hm_status hm_tree_build(hm_ctx *ctx, const double *points_dev, int64_t n);
 
 /*
  * Sections 4.1.2-4.1.3, Algorithm 2.3: build the constraint-incompatibility
  * graph of cut `level` (2..L, or HM_LEVEL_LEAF for the leaf neighbour pairs)
- * and colour it with DSatur.  *n_colors receives chi.
+ * and colour it with DSatur.  *n_colors (host, may be NULL) receives chi.
+ * Errors: HM_EINVAL (null ctx, level out of range), HM_ESTATE (no tree),
+ * HM_ENOTSUP (more than 2^20 constraint sets or 1024 colours), HM_ENOMEM,
+ * HM_ECUDA.
  */
 hm_status hm_color(hm_ctx *ctx, int level, int *n_colors);
 
@@ -174,25 +186,43 @@ hm_status hm_color(hm_ctx *ctx, int level, int *n_colors);
  * tiles, Section 4.1.2); the other rows of the stored samples are unspecified.
  */
 hm_status hm_sample(hm_ctx *ctx, const hm_op *op, int level);
+/* Errors of hm_sample: HM_EINVAL (null ctx or op, null callback or dense
+ * matrix, level out of range), HM_ESTATE (no tree, or the level not coloured),
+ * HM_EOP (the callback failed), HM_ETIMEOUT, HM_ENOMEM, HM_ECUDA. */
 
 /*
  * Algorithm 4.1: the whole compression (colour, sample, peel, bases, cores for
- * levels 2..L, then the leaf blocks).  Requires hm_tree_build.
+ * levels 2..L, then the leaf blocks).  Requires hm_tree_build; the factors
+ * stay in the context for hm_apply / hm_relerr / hm_export.  Errors: HM_EINVAL
+ * (null ctx or op, null callback or dense matrix, unknown kernel), HM_ESTATE
+ * (no tree), HM_EOP (the callback failed; the context stays usable),
+ * HM_ETIMEOUT (a bounded wait of the tensor-core sampler expired), HM_ENOTSUP
+ * (r x k or r x columns beyond shared memory), HM_ENOMEM, HM_ECUDA.
  */
 hm_status hm_compress(hm_ctx *ctx, const hm_op *op);
 
 /*
- * y = A~ x (trans = 0) or A~^* x (trans = 1) with the compressed operator:
- * x_dev, y_dev device, column-major n x nrhs, original order.
+ * Section 4.1.2 (level-truncated product over every level, plus the leaf
+ * blocks): y = A~ x (trans = 0) or A~^* x (trans = 1) with the compressed
+ * operator; x_dev, y_dev device, column-major n x nrhs (1 <= nrhs <= 64),
+ * original order.  Errors: HM_EINVAL (null ctx or vectors, nrhs out of
+ * range), HM_ESTATE (not compressed), HM_ENOMEM, HM_ECUDA.
  */
 hm_status hm_apply(hm_ctx *ctx, const double *x_dev, double *y_dev, int64_t nrhs, int trans);
 
 /*
  * Section 5: E = ||A~ - A|| / ||A|| by `iters` power iterations (20 in the
- * paper) on both operators from one Philox Gaussian start vector.
+ * paper) on both operators from one Philox Gaussian start vector; *err (host)
+ * receives E.  Errors: HM_EINVAL (null ctx, op or err, iters < 1), HM_ESTATE
+ * (not compressed), HM_EOP, HM_ENOMEM, HM_ECUDA.
  */
 hm_status hm_relerr(hm_ctx *ctx, const hm_op *op, int iters, double *err);
 
+/*
+ * Counters of the last hm_compress (Section 5's four quantities: time,
+ * matvec columns, error inputs, storage) copied into *out (host).  Valid at
+ * any stage (zeros before a compression).  Errors: HM_EINVAL (null ctx or out).
+ */
 hm_status hm_get_info(hm_ctx *ctx, hm_info *out);
 
 /* Export selectors for hm_export (structure and numbers, for tests). */
@@ -219,6 +249,9 @@ enum {
 /*
  * Copy an exported array to host memory.  With host_buf == NULL only *bytes is
  * set to the size needed; otherwise *bytes must be at least that size.
+ * Errors: HM_EINVAL (null ctx or bytes, unknown selector, level out of range,
+ * buffer too small), HM_ESTATE (no tree, or the requested part not built, or
+ * samples not kept: hm_config.keep_samples), HM_ECUDA.
  */
 hm_status hm_export(hm_ctx *ctx, int what, int level, void *host_buf, size_t *bytes);
 
