@@ -26,7 +26,10 @@
  *    creates (non-blocking, highest priority), from two host threads of its
  *    own, ahead of the level loop; all have finished when hm_compress returns.
  *  - The context owns every device buffer it allocates (tree, colourings,
- *    samples, factors); hm_destroy frees them.
+ *    samples, factors); hm_destroy frees them.  Allocation is stream-ordered
+ *    (cudaMallocAsync) from the device's default memory pool, whose release
+ *    threshold hm_create raises to the maximum, so freed blocks stay cached in
+ *    the process for the next call instead of returning to the driver.
  *  - Matrices at the boundary are column-major with leading dimension n and are
  *    indexed in the caller's ORIGINAL point order.
  */
