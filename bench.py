@@ -321,8 +321,9 @@ def run_ours(args):
         cpu = cpu_baseline(w, rows_per_level=100)
 
     # the other precision modes on the same job, for the error / time trade-off
+    # (one GPU only: under torchrun every GPU would be held meanwhile)
     modes = None
-    if rank == 0 and not args.no_modes:
+    if rank == 0 and world == 1 and not args.no_modes:
         modes = {}
         for name, (pv, desc, _) in PRECISIONS.items():
             if name == args.precision:
