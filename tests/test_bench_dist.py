@@ -1,4 +1,5 @@
-"""The N > 1 host logic of bench.py on CPU: world-size-2 gloo ranks.
+"""bench.py host logic on CPU: the N > 1 cross-rank helpers (world-size-2 gloo
+ranks) and the CPU-oracle arm.
 
 bench.py runs one independent compression job per GPU (weak scaling, no
 collective in the data path); across ranks it only takes the slowest rank's
@@ -69,3 +70,16 @@ def test_two_gloo_ranks_take_the_slowest_time():
     assert [r[2] for r in res] == pytest.approx([2 * 5 / 2.0] * 2)
     # the two replicas are independent jobs (distinct test-matrix seeds)
     assert res[0][3] != res[1][3]
+
+
+def test_oracle_sample_of_the_reference_arm_runs_on_cpu():
+    """bench.py's CPU-oracle arm (the reference line and the cpu_baseline key)
+    on a small job: a positive throughput estimate, the cores it used, and a
+    description of the bounded sample."""
+    import sys
+    sys.path.insert(0, ROOT)
+    import bench
+    import hm_workloads as W
+    out = bench.cpu_baseline(W.torus_laplace(n=3000, tol=1e-6, r=32), rows_per_level=5)
+    assert out["kind"] == "oracle" and out["value"] > 0 and out["cores"] >= 1
+    assert out["seconds_estimate"] > 0 and "lower bound" in out["sample"]
