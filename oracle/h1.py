@@ -300,6 +300,26 @@ def test_matrix(tree, l: int, col: og.Coloring, G: np.ndarray, r: int) -> np.nda
     return Om
 
 
+def sample_rows(op, tree, l: int, col: og.Coloring, G: np.ndarray, r: int, rows: np.ndarray,
+                colors: np.ndarray) -> np.ndarray:
+    """Selected entries of the raw sample Y_l = A Omega_l without forming Omega_l
+    (used for sampled checks at full size): row k of the result is
+    Y_l(rows[k], colors[k] r : (colors[k] + 1) r).  Colour c of Omega_l holds
+    G_beta on the rows of every box beta active in c and zeros elsewhere
+    (eq. neartestmatrices), so the product needs only those rows of A."""
+    rows = np.asarray(rows, dtype=np.int64)
+    colors = np.asarray(colors, dtype=np.int64)
+    out = np.zeros((len(rows), r))
+    for c in np.unique(colors):
+        X = np.zeros((tree.n, r))
+        for b in col.active(int(c)):
+            s, e = tree.rng(l, b)
+            X[s:e] = G[s:e]
+        k = np.flatnonzero(colors == c)
+        out[k] = op.rows(rows[k], X)
+    return out
+
+
 # ----------------------------------------------------------------------------
 # Algorithm 4.1
 # ----------------------------------------------------------------------------

@@ -230,3 +230,38 @@ def test_core_least_squares_equals_pseudo_inverse():
     B = h1.core(Ga, P, Gb, U, V)
     ref = np.linalg.pinv(Ga.T @ U) @ (Ga.T @ P) @ np.linalg.pinv(V.T @ Gb)
     assert np.allclose(B, ref, rtol=1e-10, atol=1e-12)
+
+
+def test_kernelop_rows_equals_dense_rows():
+    """KernelOp.rows (the sampled-row product used at full size) equals the
+    assembled matrix's rows times X, zero rows of X included, across chunks."""
+    w = W.torus_laplace(n=900)
+    op = h1.KernelOp(w.points, w.kernel, chunk_elems=5000)  # several chunks
+    rng = np.random.default_rng(3)
+    X = rng.standard_normal((w.n, 5))
+    X[rng.random(w.n) < 0.6] = 0.0
+    idx = np.sort(rng.choice(w.n, 77, replace=False))
+    ref = op.dense()[idx] @ X
+    assert np.allclose(op.rows(idx, X), ref, rtol=0, atol=1e-13 * np.abs(ref).max())
+
+
+def test_sample_rows_equals_full_sample():
+    """sample_rows gives the entries of Y_l = A Omega_l (Omega_l formed in full
+    by test_matrix) for arbitrary (row, colour) pairs of every level."""
+    from oracle import graph as og
+    w = W.torus_laplace(n=1500)
+    t = ot.build_tree(w.points, 24)
+    op = h1.KernelOp(w.points[t.perm], w.kernel)
+    rng = np.random.default_rng(8)
+    r = 6
+    for l in range(2, t.L + 1):
+        col = og.color_level(t, l)
+        if col.n_vertices == 0:
+            continue
+        G = h1.gaussians(t, l, 0, r, w.seed)
+        Y = op.apply(h1.test_matrix(t, l, col, G, r))
+        rows = rng.integers(0, w.n, 40)
+        colors = rng.integers(0, col.n_colors, 40)
+        got = h1.sample_rows(op, t, l, col, G, r, rows, colors)
+        ref = np.stack([Y[i, c * r:(c + 1) * r] for i, c in zip(rows, colors)])
+        assert np.allclose(got, ref, rtol=0, atol=1e-13 * max(np.abs(ref).max(), 1e-300)), l
