@@ -91,12 +91,16 @@ typedef struct hm_ctx hm_ctx;
 
 typedef struct {
     int d;                /* dimension of the points: 1, 2 or 3 */
-    int leaf_size;        /* m: a box is split while it holds more than m points */
+    int leaf_size;        /* m: a box is split while it holds more than m points; the
+                             default of hm_tree_build when its leaf_size is 0 */
     int uniform_depth;    /* 0: adaptive tree; > 0: split every box down to this level */
     int r;                /* columns per colour of the Gaussian test matrices (k + p), 1..64 */
     int oversample;       /* p: in tolerance mode k <= r - p (Section 2.5 suggests p = 10) */
-    int rank;             /* > 0: fixed rank k (<= r); exactly one of rank, tol is set */
-    double tol;           /* > 0: keep pivots with |R_jj| > tol |R_11| (at most r - p) */
+    int rank;             /* default rank of hm_compress (used when its tol and rank are
+                             both 0): > 0 fixed rank k (<= r), or the cap with tol */
+    double tol;           /* default tolerance of hm_compress (same rule): > 0 keep pivots
+                             with |R_jj| > tol |R_11| (at most r - p, and at most rank
+                             when rank > 0 too) */
     int precision;        /* hm_precision */
     int keep_samples;     /* non-zero: keep every level's peeled samples for hm_export */
     uint64_t seed;        /* Philox4x32-10 key of all test matrices */
@@ -145,15 +149,35 @@ typedef struct {
     int64_t tc_kernel_evals;  /* kernel-matrix entries the tensor-core sampler evaluated
                                  during hm_compress: for every colour, its output rows
                                  (the rows of its sample tiles) x its active rows */
+    int64_t device_allocs;    /* device allocations this library has made since it was
+                                 loaded (all contexts; hm_apply_noalloc makes none) */
+    int bb_tc_levels;         /* admissible levels of the last hm_compress whose black box
+                                 ran on the tensor cores (split-BF16) */
+    int bb_fp64_levels;       /* levels (admissible and leaf) whose black box ran in FP64:
+                                 HM_FP64, a dense or callback operator, or, in a mixed
+                                 mode, an r the tensor-core sampler does not take
+                                 (r % 8 != 0 or r > 40).  The leaf level of a mixed mode
+                                 with the kernel operator evaluates K in FP32 and sums
+                                 in FP64, and counts in neither field */
+    int leaf_size;            /* m of the current tree (hm_tree_build) */
+    int rank;                 /* rank (or rank cap) of the last hm_compress; 0 = none */
+    double tol;               /* tolerance of the last hm_compress; 0 = fixed rank */
+    double seconds_peel_update; /* HM_MIXED_BF16X6: device time (CUDA events) of the
+                                 double-float peel update kernels during hm_compress */
+    int64_t peel_update_macs; /* their multiply-adds: sum over tile rows, live coarse
+                                 pairs and columns of rows x k x columns */
 } hm_info;
 
 /*
  * Create a context for one compression job.  cfg is copied (Section 2.5 for r,
  * p, rank and tol; Section 3 for d, leaf_size, uniform_depth).  stream: a
- * cudaStream_t or NULL.  *out receives the context, owned by the caller until
- * hm_destroy.  Errors: HM_EINVAL (null out or cfg; d not 1..3; leaf_size < 1;
- * r not 1..64; not exactly one of rank > 0 and tol > 0; rank > r; with tol,
- * p not in 0..r-1; unknown precision; uniform_depth not 0..21), HM_ENOMEM.
+ * cudaStream_t or NULL.  The device current at this call is the context's
+ * device: every later call on the context runs on it (and restores the
+ * caller's current device before returning).  *out receives the context,
+ * owned by the caller until hm_destroy.  Errors: HM_EINVAL (null out or cfg;
+ * d not 1..3; leaf_size < 0; r not 1..64; rank < 0 or > r; tol < 0 or NaN;
+ * with tol > 0, p not in 0..r-1; unknown precision; uniform_depth not 0..21),
+ * HM_ENOMEM.
  */
 hm_status hm_create(hm_ctx **out, const hm_config *cfg, void *stream);
 
@@ -162,12 +186,14 @@ hm_status hm_destroy(hm_ctx *ctx);
 
 /*
  * Section 3: cluster tree over n points (points_dev: device, n x d row-major
- * FP64, original order), neighbour and interaction lists of every cut.  The
- * points are copied into the context (permuted into Morton order); a second
- * call starts a new job on the same context.  Errors: HM_EINVAL (null ctx or
- * points, n < 1 or n > 2^30), HM_ENOMEM, HM_ECUDA.
+ * FP64, original order) with leaves of at most leaf_size points (the paper's
+ * m; 0 = hm_config.leaf_size), and the neighbour and interaction lists of
+ * every cut.  The points are copied into the context (permuted into Morton
+ * order); a second call starts a new job on the same context.  Errors:
+ * HM_EINVAL (null ctx or points, n < 1 or n > 2^30, leaf_size < 0, or both
+ * leaf sizes 0), HM_ENOMEM, HM_ECUDA.
  */
-hm_status hm_tree_build(hm_ctx *ctx, const double *points_dev, int64_t n);
+hm_status hm_tree_build(hm_ctx *ctx, const double *points_dev, int64_t n, int leaf_size);
 
 /*
  * Sections 4.1.2-4.1.3, Algorithm 2.3: build the constraint-incompatibility
@@ -195,20 +221,29 @@ hm_status hm_sample(hm_ctx *ctx, const hm_op *op, int level);
 
 /*
  * Algorithm 4.1: the whole compression (colour, sample, peel, bases, cores for
- * levels 2..L, then the leaf blocks).  Requires hm_tree_build; the factors
- * stay in the context for hm_apply / hm_relerr / hm_export.  Errors: HM_EINVAL
- * (null ctx or op, null callback or dense matrix, unknown kernel), HM_ESTATE
- * (no tree), HM_EOP (the callback failed; the context stays usable),
- * HM_ETIMEOUT (a bounded wait of the tensor-core sampler expired), HM_ENOTSUP
- * (r x k or r x columns beyond shared memory), HM_ENOMEM, HM_ECUDA.
+ * levels 2..L, then the leaf blocks).  Truncation of qr(Y, k) (Section 2.4):
+ *   tol > 0, rank == 0: k = #{|R_jj| > tol |R_11|}, at most r - p;
+ *   tol > 0, rank > 0:  the same, at most min(r - p, rank);
+ *   tol == 0, rank > 0: fixed rank k = rank (<= r);
+ *   both 0:             hm_config's tol and rank, by the same rules.
+ * k never exceeds min(|I_alpha|, |I_beta|).  Requires hm_tree_build; the
+ * factors stay in the context for hm_apply / hm_relerr / hm_export.  Errors:
+ * HM_EINVAL (null ctx or op, null callback or dense matrix, unknown kernel,
+ * tol < 0 or NaN, rank < 0 or > r, no tolerance and no rank, or with tol > 0
+ * p not in 0..r-1), HM_ESTATE (no tree), HM_EOP (the callback failed; the
+ * context stays usable), HM_ETIMEOUT (a bounded wait of the tensor-core
+ * sampler expired), HM_ENOTSUP (r x k or r x columns beyond shared memory),
+ * HM_ENOMEM, HM_ECUDA.
  */
-hm_status hm_compress(hm_ctx *ctx, const hm_op *op);
+hm_status hm_compress(hm_ctx *ctx, const hm_op *op, double tol, int rank);
 
 /*
  * Section 4.1.2 (level-truncated product over every level, plus the leaf
  * blocks): y = A~ x (trans = 0) or A~^* x (trans = 1) with the compressed
  * operator; x_dev, y_dev device, column-major n x nrhs (1 <= nrhs <= 64),
- * original order.  Errors: HM_EINVAL (null ctx or vectors, nrhs out of
+ * original order.  Asynchronous on the context's stream: y_dev is complete
+ * when that stream reaches this point.  Every factor is read once per block
+ * of 4 right-hand sides.  Errors: HM_EINVAL (null ctx or vectors, nrhs out of
  * range), HM_ESTATE (not compressed), HM_ENOMEM, HM_ECUDA.
  */
 hm_status hm_apply(hm_ctx *ctx, const double *x_dev, double *y_dev, int64_t nrhs, int trans);
@@ -270,8 +305,10 @@ hm_status hm_export(hm_ctx *ctx, int what, int level, void *host_buf, size_t *by
  * that loads the library holds until the process exits.  A request that needs
  * more returns HM_ENOTSUP (use hm_apply).  The first call on a device looks up
  * that array's address (cudaGetSymbolAddress), so it should come before any
- * stream capture.  All calls share the array: calls that overlap on the GPU
- * race.  Arguments, results and the other errors are those of hm_apply.
+ * stream capture.  The offsets it needs are computed by hm_compress; the call
+ * reads nothing back and is asynchronous on the context's stream, like
+ * hm_apply.  All calls share the array: calls that overlap on the GPU race.  Arguments, results and the other errors are those
+ * of hm_apply.
  */
 #define HM_APPLY_NOALLOC_SCRATCH_BYTES (64u << 20)
 hm_status hm_apply_noalloc(hm_ctx *ctx, const double *x_dev, double *y_dev, int64_t nrhs, int trans);

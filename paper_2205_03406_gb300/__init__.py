@@ -55,7 +55,10 @@ class hm_info(ctypes.Structure):
                 ("seconds_sample", ctypes.c_double), ("seconds_total", ctypes.c_double),
                 ("seconds_phase", ctypes.c_double * 8), ("act_rows", ctypes.c_int64 * 32),
                 ("kernel_launches", ctypes.c_int64), ("launches_total", ctypes.c_int64),
-                ("tc_kernel_evals", ctypes.c_int64)]
+                ("tc_kernel_evals", ctypes.c_int64), ("device_allocs", ctypes.c_int64),
+                ("bb_tc_levels", ctypes.c_int), ("bb_fp64_levels", ctypes.c_int), ("leaf_size", ctypes.c_int),
+                ("rank", ctypes.c_int), ("tol", ctypes.c_double), ("seconds_peel_update", ctypes.c_double),
+                ("peel_update_macs", ctypes.c_int64)]
 
 PHASES = ["colouring", "test matrices", "black box", "peel", "bases+cores", "leaf black box", "leaf peel+extract",
           "tensor-core kernel"]
@@ -70,10 +73,10 @@ def _load():
     sig = {
         "hm_create": [ctypes.POINTER(P), ctypes.POINTER(hm_config), P],
         "hm_destroy": [P],
-        "hm_tree_build": [P, P, I64],
+        "hm_tree_build": [P, P, I64, I],
         "hm_color": [P, I, ctypes.POINTER(I)],
         "hm_sample": [P, ctypes.POINTER(hm_op), I],
-        "hm_compress": [P, ctypes.POINTER(hm_op)],
+        "hm_compress": [P, ctypes.POINTER(hm_op), D, I],
         "hm_apply": [P, P, P, I64, I],
         "hm_apply_noalloc": [P, P, P, I64, I],
         "hm_relerr": [P, ctypes.POINTER(hm_op), I, ctypes.POINTER(D)],
@@ -121,8 +124,8 @@ def hm_destroy(ctx):
     return _lib.hm_destroy(ctx)
 
 
-def hm_tree_build(ctx, points_dev: int, n: int):
-    _check(ctx, _lib.hm_tree_build(ctx, ctypes.c_void_p(points_dev), n), "hm_tree_build")
+def hm_tree_build(ctx, points_dev: int, n: int, leaf_size: int = 0):
+    _check(ctx, _lib.hm_tree_build(ctx, ctypes.c_void_p(points_dev), n, leaf_size), "hm_tree_build")
 
 
 def hm_color(ctx, level: int) -> int:
@@ -135,8 +138,8 @@ def hm_sample(ctx, op: hm_op, level: int):
     _check(ctx, _lib.hm_sample(ctx, ctypes.byref(op), level), "hm_sample")
 
 
-def hm_compress(ctx, op: hm_op):
-    _check(ctx, _lib.hm_compress(ctx, ctypes.byref(op)), "hm_compress")
+def hm_compress(ctx, op: hm_op, tol: float = 0.0, rank: int = 0):
+    _check(ctx, _lib.hm_compress(ctx, ctypes.byref(op), tol, rank), "hm_compress")
 
 
 def hm_apply(ctx, x_dev: int, y_dev: int, nrhs: int, trans: int = 0):
@@ -166,6 +169,19 @@ def hm_export(ctx, what: int, level: int = 0) -> bytes:
     buf = ctypes.create_string_buffer(max(size.value, 1))
     _check(ctx, _lib.hm_export(ctx, what, level, buf, ctypes.byref(size)), "hm_export")
     return buf.raw[:size.value]
+
+
+def hm_export_into(ctx, what: int, level: int, host_ptr: int, nbytes: int) -> int:
+    """hm_export into caller memory (host_ptr, nbytes); returns the bytes written."""
+    size = ctypes.c_size_t(nbytes)
+    _check(ctx, _lib.hm_export(ctx, what, level, ctypes.c_void_p(host_ptr), ctypes.byref(size)), "hm_export")
+    return size.value
+
+
+def hm_export_size(ctx, what: int, level: int = 0) -> int:
+    size = ctypes.c_size_t(0)
+    _check(ctx, _lib.hm_export(ctx, what, level, None, ctypes.byref(size)), "hm_export")
+    return size.value
 
 
 def hm_last_error(ctx) -> str:
@@ -241,10 +257,11 @@ class Compressor:
         except Exception:
             pass
 
-    def tree_build(self, points):
+    def tree_build(self, points, leaf_size: int = 0):
+        """Cluster tree of the points (leaf_size 0: the settings' leaf size)."""
         pts = points.to(device="cuda", dtype=self.torch.float64).contiguous()
         self._points = pts
-        hm_tree_build(self.ctx, pts.data_ptr(), pts.shape[0])
+        hm_tree_build(self.ctx, pts.data_ptr(), pts.shape[0], leaf_size)
         return self
 
     def color(self, level: int) -> int:
@@ -253,8 +270,9 @@ class Compressor:
     def sample(self, op: hm_op, level: int):
         hm_sample(self.ctx, op, level)
 
-    def compress(self, op: hm_op):
-        hm_compress(self.ctx, op)
+    def compress(self, op: hm_op, tol: float = 0.0, rank: int = 0):
+        """Algorithm 4.1 (tol and rank both 0: the settings' tol and rank)."""
+        hm_compress(self.ctx, op, tol, rank)
         return hm_get_info(self.ctx)
 
     def apply(self, x, trans: int = 0):
@@ -287,3 +305,13 @@ class Compressor:
 
     def export(self, what: int, level: int = 0) -> bytes:
         return hm_export(self.ctx, what, level)
+
+    def export_into(self, what: int, level: int, out):
+        """hm_export into a contiguous host torch tensor (pinned memory makes the
+        copy fast); returns out viewed as raw bytes of the exported size."""
+        need = hm_export_size(self.ctx, what, level)
+        nbytes = out.numel() * out.element_size()
+        if not out.is_contiguous() or out.device.type != "cpu" or nbytes < need:
+            raise ValueError(f"export_into: need a contiguous host tensor of at least {need} bytes")
+        hm_export_into(self.ctx, what, level, out.data_ptr(), nbytes)
+        return need

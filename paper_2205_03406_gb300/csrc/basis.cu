@@ -840,7 +840,7 @@ Err bases_and_cores(hm_ctx *c, int level) {
     DBuf kY, kZ;
     HM_TRY(alloc(kY, np * sizeof(int)));
     HM_TRY(alloc(kZ, np * sizeof(int)));
-    const int cap = c->cfg.rank > 0 ? r : r - c->cfg.oversample;
+    const int cap = c->kcap;  // r (fixed rank), or r - p and the rank cap (tolerance)
     // HM_MIXED_BF16X6_F32: tiles up to qr32_rows rows by the FP32 shared-memory
     // kernel, tiles up to ts_max rows by the FP32 tall-skinny QR, larger ones
     // by the FP64 block kernel.  FP64: the warp kernel up to QR_WARP_ROWS rows,
@@ -887,7 +887,7 @@ Err bases_and_cores(hm_ctx *c, int level) {
         int *kk = side ? kZ.as<int>() : kY.as<int>();
         if (cu.max_rows > small_rows) {
             k_qr_tiles<<<(int)np, 256, 0, st>>>(g.pair_alpha.as<int>(), cu.int_idx.as<int>(), g.pair_color.as<int>(),
-                                                cu.ent.as<int>(), n, r, cap, c->cfg.rank, c->cfg.tol, T, kk,
+                                                cu.ent.as<int>(), n, r, cap, c->rank_fixed, c->tol, T, kk,
                                                 small_rows); ::hm::count_launch();
         }
         if (mixed) {
@@ -896,8 +896,8 @@ Err bases_and_cores(hm_ctx *c, int level) {
                     g.pair_alpha.as<int>(), g.pair_color.as<int>(), cu.ent.as<int>(), n, r, T, blk_tile.as<int64_t>(),
                     blk_row0.as<int>(), blk_rows.as<int>(), rstack.as<float>(), taus.as<float>()); ::hm::count_launch();
                 k_ts_top<<<(unsigned)np, 512, (size_t)nb_top * r * r * sizeof(float), st>>>(
-                    g.pair_alpha.as<int>(), cu.int_idx.as<int>(), cu.ent.as<int>(), np, r, cap, c->cfg.rank,
-                    c->cfg.tol, ts_off.as<int64_t>(), rstack.as<float>(), kk); ::hm::count_launch();
+                    g.pair_alpha.as<int>(), cu.int_idx.as<int>(), cu.ent.as<int>(), np, r, cap, c->rank_fixed,
+                    c->tol, ts_off.as<int64_t>(), rstack.as<float>(), kk); ::hm::count_launch();
                 k_ts_form<<<(unsigned)nblk, 512, 2 * ts_rows * r * sizeof(float), st>>>(
                     g.pair_alpha.as<int>(), g.pair_color.as<int>(), cu.ent.as<int>(), n, r, T, blk_tile.as<int64_t>(),
                     blk_row0.as<int>(), blk_rows.as<int>(), rstack.as<float>(), taus.as<float>(), kk); ::hm::count_launch();
@@ -905,17 +905,17 @@ Err bases_and_cores(hm_ctx *c, int level) {
             }
             // tiles up to 256 rows with 128 threads, taller ones with 512
             k_qr32<<<(int)np, 128, qr32_smem, st>>>(g.pair_alpha.as<int>(), cu.int_idx.as<int>(),
-                                                    g.pair_color.as<int>(), cu.ent.as<int>(), n, r, cap, c->cfg.rank,
-                                                    c->cfg.tol, T, kk, 0, std::min(256, qr32_rows)); ::hm::count_launch();
+                                                    g.pair_color.as<int>(), cu.ent.as<int>(), n, r, cap, c->rank_fixed,
+                                                    c->tol, T, kk, 0, std::min(256, qr32_rows)); ::hm::count_launch();
             if (cu.max_rows > 256 && qr32_rows > 256) {
                 k_qr32<<<(int)np, 512, qr32_smem, st>>>(g.pair_alpha.as<int>(), cu.int_idx.as<int>(),
                                                         g.pair_color.as<int>(), cu.ent.as<int>(), n, r, cap,
-                                                        c->cfg.rank, c->cfg.tol, T, kk, 256, qr32_rows); ::hm::count_launch();
+                                                        c->rank_fixed, c->tol, T, kk, 256, qr32_rows); ::hm::count_launch();
             }
         } else {
             k_qr_warp<<<ceil_div(np, 4), 128, 0, st>>>(g.pair_alpha.as<int>(), cu.int_idx.as<int>(),
                                                        g.pair_color.as<int>(), cu.ent.as<int>(), n, r, cap,
-                                                       c->cfg.rank, c->cfg.tol, T, kk, np); ::hm::count_launch();
+                                                       c->rank_fixed, c->tol, T, kk, np); ::hm::count_launch();
         }
     }
     HM_LAUNCH("qr_tiles");
@@ -945,7 +945,7 @@ Err bases_and_cores(hm_ctx *c, int level) {
                                     f.offU.as<int64_t>(), f.offV.as<int64_t>(), c->cur.Y.as<double>(),
                                     c->cur.Z.as<double>(), f.U.as<double>(), f.V.as<double>()); ::hm::count_launch();
     HM_LAUNCH("pack");
-    const int kc = std::max(1, c->cfg.rank > 0 ? std::min(r, c->cfg.rank) : std::min(r, cap));
+    const int kc = std::max(1, std::min(r, cap));
     // S1 = G_alpha^T U (Psi side) and S2 = G_beta^T V (Omega side)
     DBuf spart;
     HM_TRY(alloc(spart, 2 * part_elems * elem));

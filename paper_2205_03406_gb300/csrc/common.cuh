@@ -50,6 +50,11 @@ extern thread_local cudaStream_t g_alloc_stream;
 void count_launch();
 long long launches_so_far();
 
+// Device allocations made by this library since it was loaded (every
+// cudaMallocAsync of alloc() counts once).
+void count_alloc();
+long long allocs_so_far();
+
 // Host-side fault injection for the error-path tests: with the environment
 // variable HM_FAULT_ALLOC_AFTER=k set when the library is loaded, the device
 // allocation after k successful ones fails once with HM_ENOMEM (before any
@@ -92,6 +97,7 @@ inline Err alloc(DBuf &b, size_t bytes) {
     b.release();
     if (bytes == 0) bytes = 16;
     if (fault_alloc_now()) return fail(HM_ENOMEM, "injected allocation failure (HM_FAULT_ALLOC_AFTER)");
+    count_alloc();
     cudaError_t e = cudaMallocAsync(&b.p, bytes, g_alloc_stream);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -107,6 +113,25 @@ inline Err ensure(DBuf &b, size_t bytes) {
     if (b.p && b.bytes >= bytes) return ok();
     return alloc(b, bytes);
 }
+
+// Makes a context's device current for the duration of a call and restores
+// the caller's device afterwards (nothing happens when no device is visible).
+struct DeviceScope {
+    int prev = -1, want = -1;
+    explicit DeviceScope(int dev) : want(dev) {
+        if (want < 0 || cudaGetDevice(&prev) != cudaSuccess) {
+            cudaGetLastError();
+            prev = -1;
+            return;
+        }
+        if (prev != want) cudaSetDevice(want);
+    }
+    ~DeviceScope() {
+        if (prev >= 0 && prev != want) cudaSetDevice(prev);
+    }
+    DeviceScope(const DeviceScope &) = delete;
+    DeviceScope &operator=(const DeviceScope &) = delete;
+};
 
 inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 

@@ -301,21 +301,29 @@ Err sample_level(hm_ctx *c, const hm_op *op, int level, bool leaf) {
     HM_TRY(ensure(S.Y, bytes));
     if (!leaf) HM_TRY(ensure(S.Z, bytes));
     if (chi == 0) return ok();
-    if (op->kind == HM_OP_CALLBACK) return sample_callback(c, op, g, leaf, S.Y.as<double>(), S.Z.as<double>());
+    if (op->kind == HM_OP_CALLBACK) {
+        c->bb_fp64_levels++;
+        return sample_callback(c, op, g, leaf, S.Y.as<double>(), S.Z.as<double>());
+    }
     if (op->kind != HM_OP_KERNEL && op->kind != HM_OP_DENSE) return fail(HM_EINVAL, "unknown operator kind");
     const OpDev o = make_opdev(c, op);
     const Cut &cu = c->cuts[g.level];
     if (leaf && c->cfg.precision != HM_FP64 && op->kind == HM_OP_KERNEL)
-        return sample_leaf_mixed(c, op->kernel);
+        return sample_leaf_mixed(c, op->kernel);  // FP32 kernel values, FP64 sums
+    // from here on the black box runs in FP64 (or on tensor cores, counted there)
     if (leaf) {
+        c->bb_fp64_levels++;
         dim3 grid(ceil_div(n, 64), chi, ceil_div(cols, 64));
         k_sample_leaf64<<<grid, 256, 0, c->st>>>(o, g.act_ptr.as<int>(), g.act_box.as<int>(), cu.ent.as<int>(), cols,
                                                  S.Y.as<double>()); ::hm::count_launch();
         HM_LAUNCH("sample_leaf64");
         return ok();
     }
-    if (c->cfg.precision != HM_FP64 && op->kind == HM_OP_KERNEL && tc_supported(c))
+    if (c->cfg.precision != HM_FP64 && op->kind == HM_OP_KERNEL && tc_supported(c)) {
+        c->bb_tc_levels++;
         return sample_tc(c, level, op->kernel);
+    }
+    c->bb_fp64_levels++;
     const int64_t *rp = g.act_rows_ptr.as<int64_t>();
     const int *rows = g.act_rows.as<int>();
     if (op->kind == HM_OP_KERNEL) {

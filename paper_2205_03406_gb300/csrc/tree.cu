@@ -439,7 +439,7 @@ Err build_tree(hm_ctx *c, const double *points_dev, int64_t n) {
         HM_TRY(alloc(bo, n * sizeof(int)));
         HM_CUDA(cudaMemsetAsync(bo.p, 0, n * sizeof(int), st));
         box_of.push_back(std::move(bo));
-        k_level_leaf<<<1, 32, 0, st>>>(c->levels[0].box.as<int>(), 1, 0, c->cfg.leaf_size, c->cfg.uniform_depth); ::hm::count_launch();
+        k_level_leaf<<<1, 32, 0, st>>>(c->levels[0].box.as<int>(), 1, 0, c->leaf_size, c->cfg.uniform_depth); ::hm::count_launch();
         HM_LAUNCH("level_leaf");
     }
     int gid = 1;
@@ -466,7 +466,7 @@ Err build_tree(hm_ctx *c, const double *points_dev, int64_t n) {
                                           bo.as<int>()); ::hm::count_launch();
         HM_LAUNCH("level_fill");
         k_level_leaf<<<ceil_div(nb_next, 256), 256, 0, st>>>(nx.box.as<int>(), (int)nb_next, l + 1,
-                                                              c->cfg.leaf_size, c->cfg.uniform_depth); ::hm::count_launch();
+                                                              c->leaf_size, c->cfg.uniform_depth); ::hm::count_launch();
         HM_LAUNCH("level_leaf");
         c->level_off.push_back(gid);
         gid += (int)nb_next;

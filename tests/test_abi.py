@@ -50,8 +50,9 @@ def test_create_rejects_bad_configs_without_gpu():
     """Argument checks happen before any CUDA work."""
     import paper_2205_03406_gb300 as hm
     bad = [hm.Settings(d=4), hm.Settings(d=3, r=0, rank=1), hm.Settings(d=3, r=65, rank=1),
-           hm.Settings(d=3, rank=0, tol=0.0), hm.Settings(d=3, rank=5, tol=1e-6),
-           hm.Settings(d=3, r=8, rank=9), hm.Settings(d=3, rank=4, precision=7)]
+           hm.Settings(d=3, rank=-1), hm.Settings(d=3, tol=-1e-6), hm.Settings(d=3, tol=float("nan")),
+           hm.Settings(d=3, r=8, rank=9), hm.Settings(d=3, rank=4, precision=7),
+           hm.Settings(d=3, r=8, oversample=8, tol=1e-6), hm.Settings(d=3, leaf_size=-1, rank=4)]
     for s in bad:
         with pytest.raises(hm.HMError) as ei:
             hm.hm_create(s.to_c())
@@ -80,7 +81,7 @@ def test_call_order_and_argument_checks_without_gpu():
     assert L.hm_color(None, 2, None) == hm.HM_EINVAL
     assert L.hm_destroy(None) == hm.HM_OK
     for prec in (hm.HM_FP64, hm.HM_MIXED_BF16X6, hm.HM_MIXED_BF16X6_F32):
-        ctx = hm.hm_create(hm.Settings(d=3, leaf_size=16, r=8, rank=4, precision=prec).to_c())
+        ctx = hm.hm_create(hm.Settings(d=3, leaf_size=16, r=8, rank=4, oversample=4, precision=prec).to_c())
         try:
             nc = ctypes.c_int(0)
             op = hm.kernel_op(hm.HM_K_LAPLACE3D)
@@ -90,18 +91,24 @@ def test_call_order_and_argument_checks_without_gpu():
             # nothing is built yet
             assert L.hm_color(ctx, 2, ctypes.byref(nc)) == hm.HM_ESTATE
             assert L.hm_sample(ctx, ctypes.byref(op), 2) == hm.HM_ESTATE
-            assert L.hm_compress(ctx, ctypes.byref(op)) == hm.HM_ESTATE
+            assert L.hm_compress(ctx, ctypes.byref(op), 0.0, 0) == hm.HM_ESTATE
             assert L.hm_apply(ctx, ctypes.c_void_p(16), ctypes.c_void_p(16), 1, 0) == hm.HM_ESTATE
             assert L.hm_apply_noalloc(ctx, ctypes.c_void_p(16), ctypes.c_void_p(16), 1, 0) == hm.HM_ESTATE
             assert L.hm_relerr(ctx, ctypes.byref(op), 20, ctypes.byref(e)) == hm.HM_ESTATE
             assert L.hm_export(ctx, hm.HM_X_PERM, 0, None, ctypes.byref(size)) == hm.HM_ESTATE
             assert L.hm_get_info(ctx, ctypes.byref(info)) == hm.HM_OK
             # null pointers and bad sizes
-            assert L.hm_tree_build(ctx, None, 10) == hm.HM_EINVAL
+            assert L.hm_tree_build(ctx, None, 10, 0) == hm.HM_EINVAL
             assert "tree_build" in L.hm_last_error(ctx).decode()
-            assert L.hm_tree_build(ctx, ctypes.c_void_p(16), 0) == hm.HM_EINVAL
+            assert L.hm_tree_build(ctx, ctypes.c_void_p(16), 0, 0) == hm.HM_EINVAL
+            assert L.hm_tree_build(ctx, ctypes.c_void_p(16), 10, -1) == hm.HM_EINVAL
             assert L.hm_sample(ctx, None, 2) == hm.HM_EINVAL
-            assert L.hm_compress(ctx, None) == hm.HM_EINVAL
+            assert L.hm_compress(ctx, None, 0.0, 0) == hm.HM_EINVAL
+            # truncation arguments of hm_compress (checked before the call order)
+            for tol, rank in ((-1.0, 0), (float("nan"), 0), (0.0, -1), (0.0, 9), (1e-6, 9)):
+                assert L.hm_compress(ctx, ctypes.byref(op), tol, rank) == hm.HM_EINVAL, (tol, rank)
+            for tol, rank in ((1e-6, 0), (1e-6, 3), (0.0, 8)):
+                assert L.hm_compress(ctx, ctypes.byref(op), tol, rank) == hm.HM_ESTATE, (tol, rank)
             assert L.hm_get_info(ctx, None) == hm.HM_EINVAL
         finally:
             assert L.hm_destroy(ctx) == hm.HM_OK
@@ -120,7 +127,7 @@ def test_injected_allocation_failure_without_gpu(tmp_path):
         "import paper_2205_03406_gb300 as hm\n"
         "L = hm.lib()\n"
         "ctx = hm.hm_create(hm.Settings(d=3, leaf_size=16, r=8, rank=4).to_c())\n"
-        "st = L.hm_tree_build(ctx, ctypes.c_void_p(16), 10)\n"
+        "st = L.hm_tree_build(ctx, ctypes.c_void_p(16), 10, 0)\n"
         "msg = L.hm_last_error(ctx).decode()\n"
         "assert st == hm.HM_ENOMEM, st\n"
         "assert 'injected' in msg, msg\n"
