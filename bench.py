@@ -5,8 +5,9 @@ Workload: 200,000 points uniform in parameter space on a torus (R = 1,
 rho = 0.3), kernel 1/(4 pi |x - y|) with zero diagonal evaluated on the fly,
 adaptive octree with leaves of at most 64 points, relative truncation
 tolerance 1e-6 (r = 32 columns per colour, oversampling 10), black-box
-contraction in split-BF16 on the tensor cores, FP32 peel products, QR and
-core solves on FP64 samples and factors.
+contraction in split-BF16 on the tensor cores; peel products in double-float
+with the subtraction in FP64; pivoted QR, Gram products and core solves in
+FP64 (the default precision; --precision mixed-f32 and fp64 select the others).
 
 One step = the whole hot path on resident inputs: cluster tree and lists,
 colouring of every level, test matrices, black-box products, peeling, bases,
@@ -37,11 +38,16 @@ METRIC = "time-to-compress (s) and jobs/s at stated rel. error; p50/p99 latency"
 
 # precision modes: (hm_precision value, description, dtype key of the JSON line)
 PRECISIONS = {
+    "mixed": (1, "split-BF16x6 tensor-core black box; double-float (2 x FP32) peel products with the "
+                 "subtraction in FP64; FP64 pivoted QR, Gram products and core solves", "bf16x6-f32acc+df64+f64"),
     "mixed-f32": (2, "split-BF16x6 tensor-core black box; FP32 peel products, QR and core solves; "
                      "FP64 samples, factors and subtractions", "bf16x6-f32acc+f32+f64"),
-    "mixed": (1, "split-BF16x6 tensor-core black box; FP64 peel, QR and core solves", "bf16x6-f32acc+f64"),
     "fp64": (0, "FP64 throughout", "f64"),
 }
+# FP32 pipe of the GB300 (152 SMs x 128 lanes at the 2070 MHz maximum SM clock),
+# and the FP32 instructions of one double-float multiply-add (csrc/df.cuh)
+FP32_INSTR_PER_S = 152 * 128 * 2070e6
+DF_INSTR_PER_MAC = 12
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
 
 # dram bytes (read + write) of the tensor-core contraction kernel per evaluated
@@ -58,7 +64,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--n", type=int, default=200_000)
-    ap.add_argument("--precision", choices=list(PRECISIONS), default="mixed-f32")
+    ap.add_argument("--precision", choices=list(PRECISIONS), default="mixed")
+    ap.add_argument("--peaks", action="store_true",
+                    help="only measure cuBLAS DGEMM and SGEMM (no TF32) rates on this GPU and print them")
     ap.add_argument("--no-modes", action="store_true",
                     help="skip timing the other two precision modes beside the main line")
     ap.add_argument("--relerr-iters", type=int, default=20)
@@ -179,6 +187,47 @@ def roofline_tc(info, r: int):
             "traffic": traffic, "traffic_unit": "dram bytes per launch (ncu, scaled by evaluated entries)",
             "launches_per_step": launches, "seconds": round(t, 4), "bf16_flops": bf16_flops,
             "useful_fp64_equiv_flops": useful}
+
+
+def roofline_df(info):
+    """Double-float peel update: every multiply-add is 12 FP32 instructions, so
+    the kernel is bound by the FP32 pipe's issue rate; achieved and peak are in
+    FP64-equivalent flops (2 per multiply-add)."""
+    t = info.seconds_peel_update
+    flops = 2.0 * info.peel_update_macs
+    peak = 2.0 * FP32_INSTR_PER_S / DF_INSTR_PER_MAC / 1e12
+    achieved = flops / t / 1e12 if t > 0 else 0.0
+    return {"kernel": "k_peel_gemm_df (double-float peel update)", "bound": "alu",
+            "achieved": round(achieved, 3), "peak": round(peak, 3), "unit": "TFLOP/s (FP64-equivalent)",
+            "frac": round(achieved / peak, 4),
+            "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2070 MHz / 12 instructions per double-float "
+                           "multiply-add x 2 flops",
+            "traffic": None, "seconds": round(t, 4), "macs": int(info.peel_update_macs),
+            "launches_per_step": int(sum(1 for l in range(3, info.L + 1) if info.colors[l] > 0) * 2 +
+                                     (1 if info.colors[info.L + 1] > 0 else 0))}
+
+
+def measure_peaks():
+    """cuBLAS DGEMM (float64) and SGEMM (float32, TF32 off) rates on this GPU,
+    best of 3 after a warm-up, by CUDA events."""
+    import torch
+    torch.backends.cuda.matmul.allow_tf32 = False
+    out = {}
+    for name, dt, n in (("fp64_dgemm_tflops", torch.float64, 4096), ("fp32_sgemm_tflops", torch.float32, 8192)):
+        a = torch.randn(n, n, dtype=dt, device="cuda")
+        b = torch.randn(n, n, dtype=dt, device="cuda")
+        a @ b
+        torch.cuda.synchronize()
+        best = float("inf")
+        for _ in range(3):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            a @ b
+            e1.record()
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1) / 1e3)
+        out[name] = round(2.0 * n ** 3 / best / 1e12, 3)
+    return out
 
 
 def max_over_ranks(x: float, dist, device) -> float:
@@ -337,6 +386,13 @@ def run_ours(args):
         if dist is not None:
             dist.destroy_process_group()
         return
+    # the roofline of the kernel with the most device time in a step, the other beside it
+    roof_tc = roofline_tc(info, w.r)
+    roof_df = roofline_df(info) if info.seconds_peel_update > 0 else None
+    if roof_df is not None and roof_df["seconds"] > roof_tc["seconds"]:
+        roof_main, roof_second = roof_df, roof_tc
+    else:
+        roof_main, roof_second = roof_tc, roof_df
     per_step.sort()
     p50 = per_step[len(per_step) // 2]
     p99 = per_step[min(len(per_step) - 1, int(math.ceil(0.99 * len(per_step))) - 1)]
@@ -355,7 +411,7 @@ def run_ours(args):
         "matvec_cols": int(info.matvec_cols), "floats_per_dof": round(info.factor_floats / w.n, 1),
         "colors": [int(info.colors[l]) for l in range(2, info.L + 2)], "max_rank": int(info.max_rank),
         "phases_s": phases, "host_elapsed_s": round(elapsed_host, 3),
-        "roofline": roofline_tc(info, w.r),
+        "roofline": roof_main, "roofline_second": roof_second,
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
         "modes": modes,
     }
@@ -454,6 +510,9 @@ def run_reference(args):
 
 def main():
     args = parse()
+    if args.peaks:
+        print(json.dumps(measure_peaks()), flush=True)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -1,12 +1,24 @@
 // Apply of the compressed operator (Section 4.1.2 level-truncated product, the
 // apply timed in Section 5):  y = sum_l sum_(a,b) U B V^T x(I_b) + sum_near D x(I_b)
-// and the adjoint.  Vectors are row-major [n][nrhs] in sorted order.
+// and the adjoint.  Vectors are row-major [n][nrhs] in sorted order; the
+// right-hand sides are processed in blocks of APPLY_NB (grid dimension y).
 //
-//  stage 1: t_q = B_q (V_q^T x(I_b)) for every admissible pair of every level
-//           (adjoint: t_q = B_q^T (U_q^T x(I_a)));
-//  stage 2: one CTA per leaf owns its rows: y(I_alpha) = sum over levels j of
-//           U_q(rows of alpha) t_q for the pairs q of alpha's level-j ancestor,
-//           plus the neighbour blocks.  No atomics; deterministic.
+// Every factor is read once per block of right-hand sides, so the apply is
+// bound by HBM bandwidth (8 bytes per stored factor entry):
+//  stage 1 (k_ap1): one CTA per pair q of a level; its warps take the rows of
+//           the pair's column box (adjoint: row box) in turn, each lane one
+//           column of the factor (whole rows are read coalesced), the warps'
+//           sums are added in warp order and t_q = B_q s (adjoint B_q^T s);
+//  stage 2 (k_ap2): one CTA per APPLY_ROWS-row chunk of a box of the cut,
+//           thread i owning row i; for every pair of the box the chunk's rows
+//           of U_q (adjoint V) -- contiguous in the arena -- and t_q are
+//           copied into shared memory with cp.async while the previous pair
+//           multiplies; y(rows) += U_q(rows) t_q;
+//  near    (k_apnear): the same shape over the leaf cut's neighbour blocks
+//           D (adjoint D^T), in column chunks of APPLY_UC.
+// Each output row belongs to one CTA per launch and the levels run in order,
+// so the result is deterministic.  The metadata (t offsets, items) is built
+// once after the compression (build_apply_plan).
 #include "apply_kernels.cuh"
 
 #include <algorithm>
@@ -28,140 +40,326 @@ Err permute_rows(hm_ctx *c, const double *in, double *out, int nrhs, bool to_sor
     return ok();
 }
 
-// t_q (kout x nrhs) = B^(T) (F^T x(I_box))
-__global__ void k_apply_stage1(const int *pair_alpha, const int *pair_col, const int *ent, int64_t np,
-                               const int *kU, const int *kV, const int64_t *offU, const int64_t *offV,
-                               const int64_t *offB, const double *U, const double *V, const double *B,
-                               const double *x, int nrhs, int trans, const int64_t *toff, double *tq) {
-    extern __shared__ double s1[];  // kin x nrhs
+namespace {
+
+__device__ __forceinline__ void cp8(void *dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+}  // namespace
+
+// stage 1: s = F_q^T x(I_box) (F = V, box = column box; adjoint F = U, row
+// box), t_q = B_q s (adjoint B_q^T s), for the right-hand sides j0 .. j0+nb-1
+template <int NW>
+__global__ void __launch_bounds__(NW * 32) k_ap1(ApplyLevel L, const double *x, int nrhs, int trans, double *t) {
+    __shared__ double sp[NW][64][APPLY_NB];
+    __shared__ double ss[64][APPLY_NB];
     const int64_t q = blockIdx.x;
-    const int ku = kU[q], kv = kV[q];
-    if (ku == 0 || kv == 0) return;
+    const int j0 = blockIdx.y * APPLY_NB, nb = min(APPLY_NB, nrhs - j0);
+    const int ku = L.kU[q], kv = L.kV[q];
+    if (ku == 0 || kv == 0) return;  // no t_q: stage 2 skips the pair too
     const int kin = trans ? ku : kv, kout = trans ? kv : ku;
-    const int box = trans ? pair_alpha[q] : pair_col[q];
-    const int *e = ent + (int64_t)box * ENT_FIELDS;
+    const int box = trans ? L.pair_alpha[q] : L.int_idx[q];
+    const int *e = L.ent + (int64_t)box * ENT_FIELDS;
     const int s0 = e[3], m = e[4] - e[3];
-    const double *F = trans ? U + offU[q] : V + offV[q];
-    for (int o = threadIdx.x; o < kin * nrhs; o += blockDim.x) {
-        const int v = o / nrhs, j = o % nrhs;
-        double acc = 0.0;
-        for (int i = 0; i < m; ++i) acc = fma(F[(int64_t)i * kin + v], x[(int64_t)(s0 + i) * nrhs + j], acc);
-        s1[o] = acc;
+    const double *F = trans ? L.U + L.offU[q] : L.V + L.offV[q];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    double a0[APPLY_NB], a1[APPLY_NB];
+#pragma unroll
+    for (int j = 0; j < APPLY_NB; ++j) a0[j] = a1[j] = 0.0;
+#pragma unroll 4
+    for (int i = w; i < m; i += NW) {
+        const double *Fr = F + (int64_t)i * kin;
+        const double *xr = x + (int64_t)(s0 + i) * nrhs + j0;
+        double xv[APPLY_NB];
+#pragma unroll
+        for (int j = 0; j < APPLY_NB; ++j) xv[j] = j < nb ? xr[j] : 0.0;
+        if (lane < kin) {
+            const double f = Fr[lane];
+#pragma unroll
+            for (int j = 0; j < APPLY_NB; ++j) a0[j] = fma(f, xv[j], a0[j]);
+        }
+        if (lane + 32 < kin) {
+            const double f = Fr[lane + 32];
+#pragma unroll
+            for (int j = 0; j < APPLY_NB; ++j) a1[j] = fma(f, xv[j], a1[j]);
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < APPLY_NB; ++j) {
+        if (lane < kin) sp[w][lane][j] = a0[j];
+        if (lane + 32 < kin) sp[w][lane + 32][j] = a1[j];
     }
     __syncthreads();
-    const double *Bq = B + offB[q];
-    for (int o = threadIdx.x; o < kout * nrhs; o += blockDim.x) {
-        const int u = o / nrhs, j = o % nrhs;
+    for (int o = threadIdx.x; o < kin * APPLY_NB; o += NW * 32) {
+        const int v = o / APPLY_NB, j = o % APPLY_NB;
         double acc = 0.0;
-        for (int v = 0; v < kin; ++v) {
-            const double b = trans ? Bq[(int64_t)v * kout + u] : Bq[(int64_t)u * kin + v];
-            acc = fma(b, s1[v * nrhs + j], acc);
-        }
-        tq[toff[q] + o] = acc;
+        for (int ww = 0; ww < NW; ++ww) acc += sp[ww][v][j];
+        ss[v][j] = acc;
+    }
+    __syncthreads();
+    const double *Bq = L.B + L.offB[q];
+    double *tq = t + (trans ? L.toffV[q] : L.toffU[q]) * nrhs;
+    for (int o = threadIdx.x; o < kout * nb; o += NW * 32) {
+        const int u = o / nb, j = o % nb;
+        double acc = 0.0;
+        for (int v = 0; v < kin; ++v) acc = fma(trans ? Bq[(int64_t)v * kout + u] : Bq[(int64_t)u * kin + v], ss[v][j], acc);
+        tq[(int64_t)u * nrhs + j0 + j] = acc;
     }
 }
 
-__global__ void k_apply_stage2(const int *ent_leaf, int nleaf, const ApplyLevel *lv, int nlev, const int *near_ptr,
-                               const int *near_idx, const int *leaf_pairT, const int64_t *offD, const double *D,
-                               const double *x, int nrhs, int trans, double *y) {
-    const int a = blockIdx.x;
-    const int *ea = ent_leaf + (int64_t)a * ENT_FIELDS;
-    const int sa = ea[3], ma = ea[4] - ea[3];
-    for (int o = threadIdx.x; o < ma * nrhs; o += blockDim.x) {
-        const int i = o / nrhs, j = o % nrhs;
-        double acc = 0.0;
-        for (int l = 0; l < nlev; ++l) {
-            const ApplyLevel &L = lv[l];
-            const int anc = L.pt2ent[sa];
-            const int as = L.ent[(int64_t)anc * ENT_FIELDS + 3];
-            for (int t = L.int_ptr[anc]; t < L.int_ptr[anc + 1]; ++t) {
-                const int q = trans ? L.pairT[t] : t;
-                const int ku = L.kU[q], kv = L.kV[q];
-                if (ku == 0 || kv == 0) continue;
-                const int kk = trans ? kv : ku;
-                const double *F = trans ? L.V + L.offV[q] : L.U + L.offU[q];
-                const double *tv = L.tq + L.toff[q];
-                const double *Fr = F + (int64_t)(sa - as + i) * kk;
-                for (int u = 0; u < kk; ++u) acc = fma(Fr[u], tv[u * nrhs + j], acc);
+// stage 2: y(rows of the item) += sum over the box's pairs of F_q(rows) t_q,
+// F = U (adjoint V of the transposed pair); ld: shared-memory row stride (odd)
+__global__ void __launch_bounds__(APPLY_ROWS) k_ap2(ApplyLevel L, const int *items, const double *t, int nrhs,
+                                                     int trans, int ld, double *y) {
+    extern __shared__ __align__(16) double sm2[];
+    const int item = blockIdx.x;
+    const int j0 = blockIdx.y * APPLY_NB, nb = min(APPLY_NB, nrhs - j0);
+    const int box = items[2 * item], r0 = items[2 * item + 1];
+    const int *e = L.ent + (int64_t)box * ENT_FIELDS;
+    const int bs = e[3], rows = min(APPLY_ROWS, e[4] - e[3] - r0);
+    const int tid = threadIdx.x;
+    const int t0 = L.int_ptr[box], t1 = L.int_ptr[box + 1];
+    // stage b: F rows at sm2 + b APPLY_ROWS ld, t at sm2 + 2 APPLY_ROWS ld + b 64 APPLY_NB
+    double *const sT0 = sm2 + 2 * APPLY_ROWS * ld;
+    // stage pair tt into buffer b; returns its rank (0: skip)
+    auto issue = [&](int tt, int b) -> int {
+        const int q = trans ? L.pairT[tt] : tt;
+        const int ku = L.kU[q], kv = L.kV[q];
+        if (ku == 0 || kv == 0) {
+            cp_commit();  // keep one group per step
+            return 0;
+        }
+        const int k = trans ? kv : ku;
+        const double *F = (trans ? L.V + L.offV[q] : L.U + L.offU[q]) + (int64_t)r0 * k;
+        const double *tq = t + (trans ? L.toffV[q] : L.toffU[q]) * nrhs;
+        double *sF = sm2 + b * APPLY_ROWS * ld, *sT = sT0 + b * 64 * APPLY_NB;
+        for (int o = tid; o < rows * k; o += APPLY_ROWS) {
+            const int i = o / k, u = o - i * k;
+            cp8(&sF[i * ld + u], F + o);
+        }
+        for (int o = tid; o < k * nb; o += APPLY_ROWS) {
+            const int u = o / nb, j = o - u * nb;
+            cp8(&sT[u * APPLY_NB + j], tq + (int64_t)u * nrhs + j0 + j);
+        }
+        cp_commit();
+        return k;
+    };
+    double acc[APPLY_NB];
+#pragma unroll
+    for (int j = 0; j < APPLY_NB; ++j) acc[j] = 0.0;
+    int kcur = t0 < t1 ? issue(t0, 0) : 0;
+    for (int tt = t0; tt < t1; ++tt) {
+        const int s = tt - t0;
+        int knext = 0;
+        if (tt + 1 < t1) {
+            knext = issue(tt + 1, (s + 1) & 1);
+            cp_wait<1>();
+        } else {
+            cp_wait<0>();
+        }
+        __syncthreads();
+        if (tid < rows && kcur > 0) {
+            const double *f = sm2 + (s & 1) * APPLY_ROWS * ld + tid * ld, *tv = sT0 + (s & 1) * 64 * APPLY_NB;
+            for (int u = 0; u < kcur; ++u) {
+                const double fu = f[u];
+#pragma unroll
+                for (int j = 0; j < APPLY_NB; ++j) acc[j] = fma(fu, tv[u * APPLY_NB + j], acc[j]);
             }
         }
-        for (int t = near_ptr[a]; t < near_ptr[a + 1]; ++t) {
-            const int b = near_idx[t];
-            const int *eb = ent_leaf + (int64_t)b * ENT_FIELDS;
-            const int sb = eb[3], mb = eb[4] - eb[3];
+        __syncthreads();
+        kcur = knext;
+    }
+    if (tid < rows && t1 > t0)
+        for (int j = 0; j < nb; ++j) y[(int64_t)(bs + r0 + tid) * nrhs + j0 + j] += acc[j];
+}
+
+// near field: y(rows) += sum over neighbours b of D_ab(rows, :) x(I_b) (adjoint
+// D_ba(:, rows)^T x(I_b)), the neighbour's points in chunks of APPLY_UC
+__global__ void __launch_bounds__(APPLY_ROWS) k_apnear(const int *ent, const int *items, const int *near_ptr,
+                                                        const int *near_idx, const int *pairT, const int64_t *offD,
+                                                        const double *D, const double *x, int nrhs, int trans,
+                                                        double *y) {
+    __shared__ double sD[APPLY_UC][APPLY_ROWS + 1];  // (column, row) of the block chunk
+    __shared__ double sx[APPLY_UC][APPLY_NB];
+    const int item = blockIdx.x;
+    const int j0 = blockIdx.y * APPLY_NB, nb = min(APPLY_NB, nrhs - j0);
+    const int a = items[2 * item], r0 = items[2 * item + 1];
+    const int *ea = ent + (int64_t)a * ENT_FIELDS;
+    const int sa = ea[3], ma = ea[4] - ea[3], rows = min(APPLY_ROWS, ma - r0);
+    const int tid = threadIdx.x;
+    double acc[APPLY_NB];
+#pragma unroll
+    for (int j = 0; j < APPLY_NB; ++j) acc[j] = 0.0;
+    for (int tt = near_ptr[a]; tt < near_ptr[a + 1]; ++tt) {
+        const int b = near_idx[tt];
+        const int *eb = ent + (int64_t)b * ENT_FIELDS;
+        const int sb = eb[3], mb = eb[4] - eb[3];
+        // forward: D_ab is ma x mb row-major; adjoint: D_ba is mb x ma row-major
+        const double *Dp = D + offD[trans ? pairT[tt] : tt];
+        for (int u0 = 0; u0 < mb; u0 += APPLY_UC) {
+            const int uc = min(APPLY_UC, mb - u0);
+            __syncthreads();
             if (!trans) {
-                const double *Dp = D + offD[t];  // |I_a| x |I_b|
-                for (int u = 0; u < mb; ++u) acc = fma(Dp[(int64_t)i * mb + u], x[(int64_t)(sb + u) * nrhs + j], acc);
+                for (int o = tid; o < rows * uc; o += APPLY_ROWS) {
+                    const int i = o / uc, u = o - i * uc;
+                    sD[u][i] = Dp[(int64_t)(r0 + i) * mb + u0 + u];
+                }
             } else {
-                const double *Dp = D + offD[leaf_pairT[t]];  // block (b, a): |I_b| x |I_a|
-                for (int u = 0; u < mb; ++u) acc = fma(Dp[(int64_t)u * ma + i], x[(int64_t)(sb + u) * nrhs + j], acc);
+                for (int o = tid; o < uc * rows; o += APPLY_ROWS) {
+                    const int u = o / rows, i = o - u * rows;
+                    sD[u][i] = Dp[(int64_t)(u0 + u) * ma + r0 + i];
+                }
             }
+            for (int o = tid; o < uc * nb; o += APPLY_ROWS) {
+                const int u = o / nb, j = o - u * nb;
+                sx[u][j] = x[(int64_t)(sb + u0 + u) * nrhs + j0 + j];
+            }
+            __syncthreads();
+            if (tid < rows)
+                for (int u = 0; u < uc; ++u) {
+                    const double d = sD[u][tid];
+#pragma unroll
+                    for (int j = 0; j < APPLY_NB; ++j) acc[j] = fma(d, j < nb ? sx[u][j] : 0.0, acc[j]);
+                }
         }
-        y[(int64_t)(sa + i) * nrhs + j] = acc;
+    }
+    if (tid < rows)
+        for (int j = 0; j < nb; ++j) y[(int64_t)(sa + r0 + tid) * nrhs + j0 + j] += acc[j];
+}
+
+// --- metadata ---------------------------------------------------------------
+
+__global__ void k_toff_sizes(const int *kU, const int *kV, int64_t np, int trans, int64_t *sz) {
+    int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q < np) sz[q] = (kU[q] > 0 && kV[q] > 0) ? (int64_t)(trans ? kV[q] : kU[q]) : 0;
+}
+
+__global__ void k_ap_item_count(const int *ent, int nc, int64_t *cnt) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nc) return;
+    const int *e = ent + (int64_t)b * ENT_FIELDS;
+    cnt[b] = (e[4] - e[3] + APPLY_ROWS - 1) / APPLY_ROWS;
+}
+
+__global__ void k_ap_item_fill(const int64_t *off, int nc, int *items) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nc) return;
+    for (int64_t k = off[b]; k < off[b + 1]; ++k) {
+        items[2 * k] = b;
+        items[2 * k + 1] = (int)(k - off[b]) * APPLY_ROWS;
     }
 }
 
-__global__ void k_toff_sizes(const int *kU, const int *kV, int64_t np, int nrhs, int trans, int64_t *sz) {
-    int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (q < np) sz[q] = (int64_t)(trans ? kV[q] : kU[q]) * nrhs;
+Err build_apply_plan(hm_ctx *c) {
+    cudaStream_t st = c->st;
+    ApplyPlan &P = c->plan;
+    P = ApplyPlan();
+    const int nl = c->L + 1;
+    P.toffU.resize(nl);
+    P.toffV.resize(nl);
+    P.items.resize(nl);
+    P.nitems.assign(nl, 0);
+    P.maxk.assign(nl, 0);
+    for (int l = std::min(2, c->L); l <= c->L; ++l) {
+        const Cut &cu = c->cuts[l];
+        // items of cut l (the leaf cut's also serve the near field, whatever L is)
+        DBuf cnt, off;
+        HM_TRY(alloc(cnt, ((size_t)cu.nc + 1) * sizeof(int64_t)));
+        HM_TRY(alloc(off, ((size_t)cu.nc + 1) * sizeof(int64_t)));
+        k_ap_item_count<<<ceil_div(cu.nc, 256), 256, 0, st>>>(cu.ent.as<int>(), cu.nc, cnt.as<int64_t>()); ::hm::count_launch();
+        HM_LAUNCH("ap_item_count");
+        HM_TRY(scan_exclusive(cnt.as<int64_t>(), off.as<int64_t>(), cu.nc, st));
+        HM_TRY(read_scalar(P.nitems[l], off.as<int64_t>() + cu.nc, st));
+        if (P.nitems[l] >= (1ll << 31)) return fail(HM_ENOTSUP, "apply: too many row chunks in one cut");
+        HM_TRY(alloc(P.items[l], std::max<int64_t>(P.nitems[l], 1) * 2 * sizeof(int)));
+        k_ap_item_fill<<<ceil_div(cu.nc, 256), 256, 0, st>>>(off.as<int64_t>(), cu.nc, P.items[l].as<int>()); ::hm::count_launch();
+        HM_LAUNCH("ap_item_fill");
+        if (l < 2 || l >= (int)c->factors.size() || !c->factors[l].done || c->factors[l].n_pairs == 0) continue;
+        const Factors &f = c->factors[l];
+        const int64_t np = f.n_pairs;
+        P.maxk[l] = f.max_k;
+        for (int trans = 0; trans < 2; ++trans) {
+            DBuf &to = trans ? P.toffV[l] : P.toffU[l];
+            DBuf sz;
+            HM_TRY(alloc(sz, (np + 1) * sizeof(int64_t)));
+            HM_TRY(alloc(to, (np + 1) * sizeof(int64_t)));
+            k_toff_sizes<<<ceil_div(np, 256), 256, 0, st>>>(f.kU.as<int>(), f.kV.as<int>(), np, trans, sz.as<int64_t>()); ::hm::count_launch();
+            HM_LAUNCH("toff_sizes");
+            HM_TRY(scan_exclusive(sz.as<int64_t>(), to.as<int64_t>(), np, st));
+            int64_t tot = 0;
+            HM_TRY(read_scalar(tot, to.as<int64_t>() + np, st));
+            P.t_max = std::max(P.t_max, tot);
+        }
+    }
+    P.ready = true;
+    return ok();
 }
 
-Err apply_sorted(hm_ctx *c, const double *x, double *y, int nrhs, int trans) {
+// --- apply ------------------------------------------------------------------
+
+Err apply_sorted_into(hm_ctx *c, const double *x, double *y, int nrhs, int trans, double *t) {
     cudaStream_t st = c->st;
-    std::vector<ApplyLevel> lv;
-    std::vector<DBuf> tq(c->L + 1), toff(c->L + 1);
+    const ApplyPlan &P = c->plan;
+    if (!P.ready) return fail(HM_ESTATE, "apply: no apply plan (compress first)");
+    const unsigned nblk = (unsigned)ceil_div(nrhs, APPLY_NB);
+    HM_CUDA(cudaMemsetAsync(y, 0, (size_t)c->n * nrhs * sizeof(double), st));
     for (int l = 2; l <= c->L; ++l) {
         if (l >= (int)c->factors.size() || !c->factors[l].done || c->factors[l].n_pairs == 0) continue;
         const Factors &f = c->factors[l];
         const Coloring &g = c->colorings[l];
         const Cut &cu = c->cuts[l];
-        const int64_t np = f.n_pairs;
-        DBuf sz;
-        HM_TRY(alloc(sz, (np + 1) * sizeof(int64_t)));
-        HM_TRY(alloc(toff[l], (np + 1) * sizeof(int64_t)));
-        k_toff_sizes<<<ceil_div(np, 256), 256, 0, st>>>(f.kU.as<int>(), f.kV.as<int>(), np, nrhs, trans,
-                                                        sz.as<int64_t>()); ::hm::count_launch();
-        HM_TRY(scan_exclusive(sz.as<int64_t>(), toff[l].as<int64_t>(), np, st));
-        int64_t tot = 0;
-        HM_TRY(read_scalar(tot, toff[l].as<int64_t>() + np, st));
-        HM_TRY(alloc(tq[l], std::max<int64_t>(tot, 1) * sizeof(double)));
-        const size_t smem = (size_t)std::max(f.max_k, 1) * nrhs * sizeof(double);
-        if (smem > 200 * 1024) return fail(HM_ENOTSUP, "apply: too many right-hand sides");
-        HM_CUDA(cudaFuncSetAttribute(k_apply_stage1, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-        k_apply_stage1<<<(int)np, 128, smem, st>>>(g.pair_alpha.as<int>(), cu.int_idx.as<int>(), cu.ent.as<int>(), np,
-                                                   f.kU.as<int>(), f.kV.as<int>(), f.offU.as<int64_t>(),
-                                                   f.offV.as<int64_t>(), f.offB.as<int64_t>(), f.U.as<double>(),
-                                                   f.V.as<double>(), f.B.as<double>(), x, nrhs, trans,
-                                                   toff[l].as<int64_t>(), tq[l].as<double>()); ::hm::count_launch();
-        HM_LAUNCH("apply_stage1");
         ApplyLevel a;
-        a.pt2ent = cu.pt2ent.as<int>();
         a.ent = cu.ent.as<int>();
         a.int_ptr = cu.int_ptr.as<int>();
         a.int_idx = cu.int_idx.as<int>();
+        a.pair_alpha = g.pair_alpha.as<int>();
         a.pairT = g.pair_T.as<int>();
         a.kU = f.kU.as<int>();
         a.kV = f.kV.as<int>();
         a.offU = f.offU.as<int64_t>();
         a.offV = f.offV.as<int64_t>();
+        a.offB = f.offB.as<int64_t>();
         a.U = f.U.as<double>();
         a.V = f.V.as<double>();
-        a.toff = toff[l].as<int64_t>();
-        a.tq = tq[l].as<double>();
-        lv.push_back(a);
+        a.B = f.B.as<double>();
+        a.toffU = P.toffU[l].as<int64_t>();
+        a.toffV = P.toffV[l].as<int64_t>();
+        if (f.max_k > 64) return fail(HM_ENOTSUP, "apply: rank above 64");
+        // stage 1: 16 warps per pair where boxes are long, else 4
+        if (cu.max_rows > 1024) k_ap1<16><<<dim3((unsigned)f.n_pairs, nblk), 512, 0, st>>>(a, x, nrhs, trans, t);
+        else k_ap1<4><<<dim3((unsigned)f.n_pairs, nblk), 128, 0, st>>>(a, x, nrhs, trans, t);
+        ::hm::count_launch();
+        HM_LAUNCH("apply stage 1");
+        const int ld = std::max(1, P.maxk[l]) | 1;
+        const size_t smem = (2 * (size_t)APPLY_ROWS * ld + 2 * 64 * APPLY_NB) * sizeof(double);
+        HM_CUDA(cudaFuncSetAttribute(k_ap2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        if (P.nitems[l] > 0) {
+            k_ap2<<<dim3((unsigned)P.nitems[l], nblk), APPLY_ROWS, smem, st>>>(a, P.items[l].as<int>(), t, nrhs, trans,
+                                                                              ld, y);
+            ::hm::count_launch();
+            HM_LAUNCH("apply stage 2");
+        }
     }
-    DBuf lvd;
-    HM_TRY(alloc(lvd, std::max<size_t>(lv.size(), 1) * sizeof(ApplyLevel)));
-    if (!lv.empty())
-        HM_CUDA(cudaMemcpyAsync(lvd.p, lv.data(), lv.size() * sizeof(ApplyLevel), cudaMemcpyHostToDevice, st));
     const Cut &cl = c->cuts[c->L];
     const Coloring &gl = c->colorings[c->L + 1];
-    k_apply_stage2<<<cl.nc, 128, 0, st>>>(cl.ent.as<int>(), cl.nc, lvd.as<ApplyLevel>(), (int)lv.size(),
-                                          cl.near_ptr.as<int>(), cl.near_idx.as<int>(), gl.pair_T.as<int>(),
-                                          c->leaf.offD.as<int64_t>(), c->leaf.D.as<double>(), x, nrhs, trans, y); ::hm::count_launch();
-    HM_LAUNCH("apply_stage2");
-    HM_CUDA(cudaStreamSynchronize(st));
+    if (c->leaf.done && c->leaf.n_pairs > 0 && P.nitems[c->L] > 0) {
+        k_apnear<<<dim3((unsigned)P.nitems[c->L], nblk), APPLY_ROWS, 0, st>>>(
+            cl.ent.as<int>(), P.items[c->L].as<int>(), cl.near_ptr.as<int>(), cl.near_idx.as<int>(),
+            gl.pair_T.as<int>(), c->leaf.offD.as<int64_t>(), c->leaf.D.as<double>(), x, nrhs, trans, y);
+        ::hm::count_launch();
+        HM_LAUNCH("apply near field");
+    }
     return ok();
+}
+
+Err apply_sorted(hm_ctx *c, const double *x, double *y, int nrhs, int trans) {
+    HM_TRY(ensure(c->apply_t, (size_t)std::max<int64_t>(c->plan.t_max, 1) * nrhs * sizeof(double)));
+    return apply_sorted_into(c, x, y, nrhs, trans, c->apply_t.as<double>());
 }
 
 }  // namespace hm

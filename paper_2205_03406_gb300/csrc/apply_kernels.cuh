@@ -1,4 +1,4 @@
-// Kernels and level table of the apply (apply.cu), shared with the
+// Level table and entry point of the apply kernels (apply.cu), shared with the
 // allocation-free apply entry point (apply_noalloc.cu).
 #pragma once
 
@@ -6,22 +6,16 @@
 
 namespace hm {
 
-struct ApplyLevel {
-    const int *pt2ent, *ent, *int_ptr, *int_idx, *pairT;
-    const int *kU, *kV;
-    const int64_t *offU, *offV;
-    const double *U, *V;
-    const int64_t *toff;
-    const double *tq;
-};
+constexpr int APPLY_NB = 4;   // right-hand sides per CTA (grid dimension y)
+constexpr int APPLY_UC = 64;  // neighbour points per shared-memory chunk of the near field
 
-__global__ void k_apply_stage1(const int *pair_alpha, const int *pair_col, const int *ent, int64_t np,
-                               const int *kU, const int *kV, const int64_t *offU, const int64_t *offV,
-                               const int64_t *offB, const double *U, const double *V, const double *B,
-                               const double *x, int nrhs, int trans, const int64_t *toff, double *tq);
-__global__ void k_apply_stage2(const int *ent_leaf, int nleaf, const ApplyLevel *lv, int nlev, const int *near_ptr,
-                               const int *near_idx, const int *leaf_pairT, const int64_t *offD, const double *D,
-                               const double *x, int nrhs, int trans, double *y);
-__global__ void k_toff_sizes(const int *kU, const int *kV, int64_t np, int nrhs, int trans, int64_t *sz);
+// one admissible level as the apply kernels read it
+struct ApplyLevel {
+    const int *ent, *int_ptr, *int_idx, *pair_alpha, *pairT;
+    const int *kU, *kV;
+    const int64_t *offU, *offV, *offB;
+    const double *U, *V, *B;
+    const int64_t *toffU, *toffV;  // t offsets (units of one right-hand side), forward / adjoint
+};
 
 }  // namespace hm

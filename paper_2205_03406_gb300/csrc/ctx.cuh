@@ -73,6 +73,7 @@ struct Factors {
     DBuf offU, offV, offB;    // int64 element offsets
     DBuf U, V, B;
     DBuf U32, V32, B32;       // FP32 copies for the HM_MIXED_BF16X6_F32 peel (made on first use)
+    DBuf U2, V2, B2;          // double-float copies for the HM_MIXED_BF16X6 peel (made on first use)
     int64_t nU = 0, nV = 0, nB = 0;
     int max_k = 0;
 };
@@ -86,6 +87,21 @@ struct Leaf {
     int m_max = 0;
 };
 
+// Apply metadata, built once at the end of a compression so that an apply
+// needs no scan and no read back: per admissible level the offsets of every
+// pair's intermediate product t (prefix sums of k_U and of k_V, in units of
+// one right-hand side), and per cut the stage-2 items (box, first row) of at
+// most APPLY_ROWS rows each; the leaf cut's items also serve the near field.
+constexpr int APPLY_ROWS = 64;
+struct ApplyPlan {
+    bool ready = false;
+    std::vector<DBuf> toffU, toffV;   // int64 [np + 1], index l
+    std::vector<DBuf> items;          // int32 [nitems][2], index l (cut l)
+    std::vector<int64_t> nitems;
+    std::vector<int> maxk;            // largest k of level l
+    int64_t t_max = 0;                // largest sum of k over a level's pairs (both sides)
+};
+
 struct Samples {
     int level = -100;
     int chi = 0, cols = 0;    // colours, columns per colour
@@ -97,8 +113,19 @@ struct Samples {
 struct hm_ctx {
     hm_config cfg;
     cudaStream_t st = nullptr;
+    int dev = -1;             // the device current at hm_create (-1: none visible)
     std::string last_error;
     int stage = 0;            // 0 created, 1 tree built, 2 compressed
+
+    // settings of the current tree and compression (hm_tree_build's leaf size,
+    // hm_compress's truncation): fixed rank (0 in tolerance mode), tolerance
+    // (0 with a fixed rank), cap on k (r, or r - p and the rank cap with a
+    // tolerance), and the rank argument as given (0 = none)
+    int leaf_size = 0;
+    int rank_fixed = 0;
+    double tol = 0.0;
+    int kcap = 0;
+    int rank_arg = 0;
 
     // points
     int64_t n = 0;
@@ -131,9 +158,18 @@ struct hm_ctx {
     cudaStream_t color_st[2] = {nullptr, nullptr};
     hm::DBuf color_scan_tmp[2];
 
+    hm::ApplyPlan plan;
+    hm::DBuf apply_t;                 // hm_apply's intermediate products (grow-only)
+
     hm_info info;
     double t_sample = 0.0;
+    int bb_tc_levels = 0;     // levels of the last compression sampled on the tensor cores
+    int bb_fp64_levels = 0;   // levels sampled in FP64 (SIMT kernel, dense or callback operator)
     double t_tc = 0.0;        // device time of the tensor-core contraction kernels
+    // CUDA events around the peel update launches of the current compression,
+    // and their multiply-add counter (double-float mode)
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_update;
+    hm::DBuf peel_macs;
     int64_t tc_evals = 0;     // kernel entries the tensor-core sampler evaluated (padding excluded)
 };
 
@@ -157,10 +193,15 @@ bool tc_supported(const hm_ctx *c);
 Err peel_level(hm_ctx *c, int level, bool leaf);
 Err peel_level_mixed(hm_ctx *c, int level, bool leaf);  // FP32 products (HM_MIXED_BF16X6_F32)
 Err peel_level_fp64(hm_ctx *c, int level, bool leaf);   // the same structure in FP64
+Err peel_level_df(hm_ctx *c, int level, bool leaf);     // double-float products (HM_MIXED_BF16X6)
 // basis.cu
 Err bases_and_cores(hm_ctx *c, int level);
 Err extract_leaf(hm_ctx *c);
 // apply.cu
+Err build_apply_plan(hm_ctx *c);
+// y = A~ x (trans 0) or A~^* x for row-major sorted [n][nrhs] vectors; t holds
+// plan.t_max * nrhs doubles of scratch.  Asynchronous on c->st.
+Err apply_sorted_into(hm_ctx *c, const double *x_sorted, double *y_sorted, int nrhs, int trans, double *t);
 Err apply_sorted(hm_ctx *c, const double *x_sorted, double *y_sorted, int nrhs, int trans);
 Err permute_rows(hm_ctx *c, const double *in, double *out, int nrhs, bool to_sorted);
 

@@ -16,7 +16,10 @@
 namespace hm {
 thread_local cudaStream_t g_alloc_stream = nullptr;
 static std::atomic<long long> g_launches{0};
+static std::atomic<long long> g_allocs{0};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void count_alloc() { g_allocs.fetch_add(1, std::memory_order_relaxed); }
+long long allocs_so_far() { return g_allocs.load(std::memory_order_relaxed); }
 
 // allocations left before the injected failure; -1: injection off
 static std::atomic<long long> g_alloc_countdown{[] {
@@ -124,9 +127,8 @@ extern "C" {
 hm_status hm_create(hm_ctx **out, const hm_config *cfg, void *stream) {
     if (!out || !cfg) return HM_EINVAL;
     *out = nullptr;
-    if (cfg->d < 1 || cfg->d > 3 || cfg->leaf_size < 1 || cfg->r < 1 || cfg->r > 64) return HM_EINVAL;
-    if ((cfg->rank > 0) == (cfg->tol > 0.0) || cfg->rank > cfg->r || cfg->rank < 0 || !(cfg->tol >= 0.0))
-        return HM_EINVAL;
+    if (cfg->d < 1 || cfg->d > 3 || cfg->leaf_size < 0 || cfg->r < 1 || cfg->r > 64) return HM_EINVAL;
+    if (cfg->rank > cfg->r || cfg->rank < 0 || !(cfg->tol >= 0.0) || !(cfg->tol < INFINITY)) return HM_EINVAL;
     if (cfg->tol > 0.0 && (cfg->oversample < 0 || cfg->oversample >= cfg->r)) return HM_EINVAL;
     if (cfg->precision != HM_FP64 && cfg->precision != HM_MIXED_BF16X6 && cfg->precision != HM_MIXED_BF16X6_F32)
         return HM_EINVAL;
@@ -138,6 +140,7 @@ hm_status hm_create(hm_ctx **out, const hm_config *cfg, void *stream) {
     std::memset(&c->info, 0, sizeof(c->info));
     int dev = 0;
     if (cudaGetDevice(&dev) == cudaSuccess) {
+        c->dev = dev;
         cudaMemPool_t pool;
         if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
             uint64_t thr = UINT64_MAX;
@@ -152,6 +155,7 @@ hm_status hm_create(hm_ctx **out, const hm_config *cfg, void *stream) {
 hm_status hm_destroy(hm_ctx *c) {
     if (!c) return HM_OK;
     {
+        DeviceScope ds(c->dev);
         StreamScope ss(c->st);
         cudaStream_t st = c->st, cst0 = c->color_st[0], cst1 = c->color_st[1];
         delete c;
@@ -163,14 +167,19 @@ hm_status hm_destroy(hm_ctx *c) {
     return HM_OK;
 }
 
-hm_status hm_tree_build(hm_ctx *c, const double *points_dev, int64_t n) {
+hm_status hm_tree_build(hm_ctx *c, const double *points_dev, int64_t n, int leaf_size) {
     if (!c) return HM_EINVAL;
     if (!points_dev || n < 1 || n > (1ll << 30)) return bad(c, HM_EINVAL, "tree_build: bad points or n");
+    if (leaf_size < 0 || (leaf_size == 0 && c->cfg.leaf_size < 1))
+        return bad(c, HM_EINVAL, "tree_build: leaf_size < 0, or 0 with no leaf size in the configuration");
+    DeviceScope ds(c->dev);
     StreamScope ss(c->st);
+    c->leaf_size = leaf_size > 0 ? leaf_size : c->cfg.leaf_size;
     c->colorings.clear();
     c->factors.clear();
     c->kept.clear();
     c->leaf = Leaf();
+    c->plan = ApplyPlan();
     c->xdf.release();
     c->stage = 0;
     Err e = build_tree(c, points_dev, n);
@@ -186,6 +195,7 @@ hm_status hm_color(hm_ctx *c, int level, int *n_colors) {
     if (c->stage < 1) return bad(c, HM_ESTATE, "color: build the tree first");
     const bool leaf = level == HM_LEVEL_LEAF;
     if (!leaf && (level < 2 || level > c->L)) return bad(c, HM_EINVAL, "color: level out of range");
+    DeviceScope ds(c->dev);
     StreamScope ss(c->st);
     Err e = color_cut(c, level, leaf);
     if (e) return finish(c, e);
@@ -202,6 +212,7 @@ hm_status hm_sample(hm_ctx *c, const hm_op *op, int level) {
     if (!c->colorings[idx].done) return bad(c, HM_ESTATE, "sample: colour the level first");
     if (op->kind == HM_OP_CALLBACK && !op->apply) return bad(c, HM_EINVAL, "sample: null callback");
     if (op->kind == HM_OP_DENSE && !op->dense_dev) return bad(c, HM_EINVAL, "sample: null dense matrix");
+    DeviceScope ds(c->dev);
     StreamScope ss(c->st);
     Err e;
     if (!leaf) e = make_gaussians(c, level);
@@ -307,6 +318,14 @@ static Err compress_all(hm_ctx *c, const hm_op *op) {
     const long long launches0 = launches_so_far();
     c->t_tc = 0.0;
     c->tc_evals = 0;
+    c->bb_tc_levels = 0;
+    c->bb_fp64_levels = 0;
+    for (auto &e : c->ev_update) {
+        cudaEventDestroy(e.first);
+        cudaEventDestroy(e.second);
+    }
+    c->ev_update.clear();
+    if (c->peel_macs.p) HM_CUDA(cudaMemsetAsync(c->peel_macs.p, 0, sizeof(unsigned long long), c->st));
     // (phase, start event, end event) triples, read once at the end
     std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev;
     int cur_phase = -1;
@@ -365,6 +384,7 @@ static Err compress_all(hm_ctx *c, const hm_op *op) {
             if (!err) PHASE(6, extract_leaf(c));
         }
     }
+    if (!err) err = build_apply_plan(c);
 #undef PHASE
     if (cur_start) cudaEventDestroy(cur_start);
     cudaError_t ce = cudaStreamSynchronize(c->st);
@@ -376,6 +396,17 @@ static Err compress_all(hm_ctx *c, const hm_op *op) {
         cudaEventDestroy(e.second.first);
         cudaEventDestroy(e.second.second);
     }
+    double t_update = 0.0;
+    for (auto &e : c->ev_update) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, e.first, e.second) == cudaSuccess) t_update += ms * 1e-3;
+        cudaEventDestroy(e.first);
+        cudaEventDestroy(e.second);
+    }
+    c->ev_update.clear();
+    unsigned long long macs = 0;
+    if (!err && c->peel_macs.p && cudaMemcpy(&macs, c->peel_macs.p, sizeof(macs), cudaMemcpyDeviceToHost) != cudaSuccess)
+        macs = 0;
     cudaGetLastError();
     if (err) return err;
     const double ts = phase[2] + phase[5];
@@ -390,6 +421,12 @@ static Err compress_all(hm_ctx *c, const hm_op *op) {
     int64_t floats = 0;
     in.kernel_launches = launches_so_far() - launches0;
     in.tc_kernel_evals = c->tc_evals;
+    in.bb_tc_levels = c->bb_tc_levels;
+    in.bb_fp64_levels = c->bb_fp64_levels;
+    in.seconds_peel_update = t_update;
+    in.peel_update_macs = (int64_t)macs;
+    in.rank = c->rank_arg;
+    in.tol = c->tol;
     for (int l = 2; l <= c->L && l < 31; ++l) {
         in.act_rows[l] = c->colorings[l].n_act_rows;
         in.colors[l] = c->colorings[l].n_colors;
@@ -413,13 +450,27 @@ static Err compress_all(hm_ctx *c, const hm_op *op) {
     return ok();
 }
 
-hm_status hm_compress(hm_ctx *c, const hm_op *op) {
+hm_status hm_compress(hm_ctx *c, const hm_op *op, double tol, int rank) {
     if (!c || !op) return HM_EINVAL;
-    if (c->stage < 1) return bad(c, HM_ESTATE, "compress: build the tree first");
     if (op->kind == HM_OP_CALLBACK && !op->apply) return bad(c, HM_EINVAL, "compress: null callback");
     if (op->kind == HM_OP_DENSE && !op->dense_dev) return bad(c, HM_EINVAL, "compress: null dense matrix");
     if (op->kind == HM_OP_KERNEL && (op->kernel < HM_K_LOG || op->kernel > HM_K_EXP))
         return bad(c, HM_EINVAL, "compress: unknown kernel");
+    if (!(tol >= 0.0) || !(tol < INFINITY) || rank < 0) return bad(c, HM_EINVAL, "compress: tol < 0 or rank < 0");
+    if (tol == 0.0 && rank == 0) {  // the configuration's defaults
+        tol = c->cfg.tol;
+        rank = c->cfg.rank;
+    }
+    const int r = c->cfg.r, p = c->cfg.oversample;
+    if (tol == 0.0 && rank == 0) return bad(c, HM_EINVAL, "compress: neither a tolerance nor a rank");
+    if (rank > r) return bad(c, HM_EINVAL, "compress: rank > r");
+    if (tol > 0.0 && (p < 0 || p >= r)) return bad(c, HM_EINVAL, "compress: oversampling p not in 0..r-1");
+    if (c->stage < 1) return bad(c, HM_ESTATE, "compress: build the tree first");
+    c->tol = tol;
+    c->rank_arg = rank;
+    c->rank_fixed = tol > 0.0 ? 0 : rank;
+    c->kcap = tol > 0.0 ? (rank > 0 ? std::min(r - p, rank) : r - p) : r;
+    DeviceScope ds(c->dev);
     StreamScope ss(c->st);
     c->stage = 1;
     c->kept.clear();
@@ -433,6 +484,7 @@ hm_status hm_apply(hm_ctx *c, const double *x, double *y, int64_t nrhs, int tran
     if (!c) return HM_EINVAL;
     if (c->stage < 2) return bad(c, HM_ESTATE, "apply: compress first");
     if (!x || !y || nrhs < 1 || nrhs > 64) return bad(c, HM_EINVAL, "apply: bad vectors");
+    DeviceScope ds(c->dev);
     StreamScope ss(c->st);
     DBuf xs, ys;
     Err e = alloc(xs, c->n * nrhs * sizeof(double));
@@ -440,10 +492,6 @@ hm_status hm_apply(hm_ctx *c, const double *x, double *y, int64_t nrhs, int tran
     if (!e) e = permute_rows(c, x, xs.as<double>(), (int)nrhs, true);
     if (!e) e = apply_sorted(c, xs.as<double>(), ys.as<double>(), (int)nrhs, trans ? 1 : 0);
     if (!e) e = permute_rows(c, ys.as<double>(), y, (int)nrhs, false);
-    if (!e) {
-        cudaError_t ce = cudaStreamSynchronize(c->st);
-        if (ce != cudaSuccess) e = fail(HM_ECUDA, cudaGetErrorString(ce));
-    }
     return finish(c, e);
 }
 
@@ -451,6 +499,7 @@ hm_status hm_relerr(hm_ctx *c, const hm_op *op, int iters, double *err) {
     if (!c || !op || !err) return HM_EINVAL;
     if (c->stage < 2) return bad(c, HM_ESTATE, "relerr: compress first");
     if (iters < 1) return bad(c, HM_EINVAL, "relerr: iters < 1");
+    DeviceScope ds(c->dev);
     StreamScope ss(c->st);
     const int64_t n = c->n;
     DBuf x, ax, hx, w, z1, z2, sq, t1, t2;
@@ -504,6 +553,8 @@ hm_status hm_get_info(hm_ctx *c, hm_info *out) {
     if (!c || !out) return HM_EINVAL;
     *out = c->info;
     out->launches_total = launches_so_far();
+    out->device_allocs = allocs_so_far();
+    out->leaf_size = c->leaf_size;
     if (c->stage >= 1) {
         out->n = c->n;
         out->L = c->L;
@@ -517,6 +568,7 @@ hm_status hm_get_info(hm_ctx *c, hm_info *out) {
 hm_status hm_export(hm_ctx *c, int what, int level, void *host_buf, size_t *bytes) {
     if (!c || !bytes) return HM_EINVAL;
     if (c->stage < 1) return bad(c, HM_ESTATE, "export: build the tree first");
+    DeviceScope ds(c->dev);
     StreamScope ss(c->st);
     const bool leaf = level == HM_LEVEL_LEAF;
     const int cl = leaf ? c->L : level;

@@ -175,8 +175,11 @@ Err peel_level(hm_ctx *c, int level, bool leaf) {
     const int cols = g.m_cols;
     // up to 64 columns per colour: T = B W once per (coarse pair, colour) and a
     // register-tiled update (peel_mixed.cu), in FP32 or FP64; wider leaves: below
-    if (cols <= 64)
-        return c->cfg.precision == HM_MIXED_BF16X6_F32 ? peel_level_mixed(c, level, leaf) : peel_level_fp64(c, level, leaf);
+    if (cols <= 64) {
+        if (c->cfg.precision == HM_MIXED_BF16X6_F32) return peel_level_mixed(c, level, leaf);
+        if (c->cfg.precision == HM_MIXED_BF16X6) return peel_level_df(c, level, leaf);
+        return peel_level_fp64(c, level, leaf);
+    }
     const int jmax = leaf ? c->L : level - 1;
     const Cut &cl = c->cuts[l];
     cudaStream_t st = c->st;

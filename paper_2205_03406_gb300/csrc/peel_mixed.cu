@@ -14,7 +14,19 @@
 // combinations a level needs are found through the (ancestor box A at level
 // j, colour c) combinations of the tiles: the slots of T for (A, c) are
 // contiguous, one per entry of A's interaction list, in list order.
+//
+// HM_MIXED_BF16X6 runs the same three products in double-float arithmetic
+// (df.cuh: two FP32 words, about 48 significant bits, on the FP32 pipe, whose
+// rate on this GPU is about 60 times the FP64 rate) from double-float copies of
+// the factors and Gaussians, and subtracts the result from the FP64 samples in
+// FP64.  Its update kernel (k_peel_gemm_df) reads compacted records of the live
+// T slots (written by k_peel_T) and stages the next slot's F and T rows in
+// shared memory with cp.async while the current one multiplies.  HM_FP64 keeps
+// FP64 products (k_peel_gemm64).
 #include "ctx.cuh"
+#include "df.cuh"
+
+#include <type_traits>
 
 namespace hm {
 
@@ -26,6 +38,19 @@ __global__ void k_to_f32(const double *in, float *out, int64_t n) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i < n) out[i] = (float)in[i];
 }
+
+__global__ void k_to_df(const double *in, dfloat *out, int64_t n) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) out[i] = df_from(in[i]);
+}
+
+// a live T slot of (ancestor A, colour c) for the double-float update: the
+// pair's factor offset in its arena, the slot, and the rank of the factor
+struct PeelRec {
+    int64_t foff;
+    int slot;
+    int kout;
+};
 
 // size of the X block of each coarse pair: k x cols per level-l box inside its box
 __global__ void k_xsize(const int *pair_alpha, const int *pair_col, int64_t np, const int *entj, const int *pt2ent_l,
@@ -63,7 +88,7 @@ __global__ void k_peel_xr(const int *pair_alpha, const int *pair_col, const int 
                 acc = (t < len) ? Fq[(int64_t)(s0 - bstart + t) * k + v] : R(0);
             } else {
                 for (int i = 0; i < len; ++i)
-                    acc = fma(Fq[(int64_t)(s0 - bstart + i) * k + v], G[(int64_t)(s0 + i) * cols + t], acc);
+                    acc = mac(Fq[(int64_t)(s0 - bstart + i) * k + v], G[(int64_t)(s0 + i) * cols + t], acc);
             }
             xg[o] = acc;
         }
@@ -105,10 +130,12 @@ __global__ void k_anc_mark(const int *tile_alpha, const int *tile_color, int64_t
 // One warp per (A, c) combination of level j; for every entry t of A's
 // interaction list: W = sum of X_{q,gamma} over the gammas of colour c in the
 // other box, T[slot] = B W (Y side, B is kout x kin) or B^T W (Z side).
+// With rec != nullptr (double-float mode) it also writes the live slots of
+// each (A, c), in list order, as records rec[base[e] ..] and their count cnt[e].
 template <typename R>
 __global__ void __launch_bounds__(WARPS * 32) k_peel_T(CoarseT<R> C, int64_t ncomb, int chi, int side, int cols,
                                                      int kcap, const int *pt2ent_l, const int *act_ptr,
-                                                     const int *act_box) {
+                                                     const int *act_box, PeelRec *rec, int *cnt) {
     extern __shared__ __align__(16) unsigned char sm_raw[];
     R *sm = reinterpret_cast<R *>(sm_raw);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -120,6 +147,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_peel_T(CoarseT<R> C, int64_t nco
     R *W = sm + (size_t)warp * kcap * cols;
     const int a0 = act_ptr[c], a1 = act_ptr[c + 1];
     const int t0 = C.int_ptr[A];
+    int nlive = 0;
     for (int t = t0; t < C.int_ptr[A + 1]; ++t) {
         const int64_t slot = s0 + (t - t0);
         const int q = side ? C.pairT[t] : t;
@@ -135,7 +163,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_peel_T(CoarseT<R> C, int64_t nco
                 const R *Xq = C.X + C.xoff[q];
                 for (int o = lane; o < kin * cols; o += 32) {
                     R sacc = R(0);
-                    for (int g = lo; g < hi; ++g) sacc += Xq[(int64_t)(act_box[g] - kb) * kin * cols + o];
+                    for (int g = lo; g < hi; ++g) sacc = add(sacc, Xq[(int64_t)(act_box[g] - kb) * kin * cols + o]);
                     W[o] = sacc;
                 }
                 __syncwarp();
@@ -145,14 +173,20 @@ __global__ void __launch_bounds__(WARPS * 32) k_peel_T(CoarseT<R> C, int64_t nco
                     const int u = o / cols, col = o % cols;
                     R sacc = R(0);
                     for (int v = 0; v < kin; ++v)
-                        sacc = fma(side ? Bq[v * kout + u] : Bq[u * kin + v], W[v * cols + col], sacc);
+                        sacc = mac(side ? Bq[v * kout + u] : Bq[u * kin + v], W[v * cols + col], sacc);
                     To[o] = sacc;
                 }
                 __syncwarp();
             }
         }
-        if (lane == 0) C.live[slot] = (kin > 0 && kout > 0 && lo < hi) ? 1 : 0;
+        const bool live = kin > 0 && kout > 0 && lo < hi;  // the same in every lane
+        if (lane == 0) {
+            C.live[slot] = live ? 1 : 0;
+            if (rec && live) rec[s0 + nlive] = PeelRec{side ? C.offV[q] : C.offU[q], (int)slot, kout};
+        }
+        nlive += live ? 1 : 0;
     }
+    if (rec && lane == 0) cnt[e] = nlive;
 }
 
 // work items of the update: chunks of gr rows of every tile
@@ -341,6 +375,149 @@ __global__ void __launch_bounds__(128) k_peel_gemm64(const CoarseT<double> *cl, 
     }
 }
 
+// ---------------------------------------------------------------------------
+// Double-float update (HM_MIXED_BF16X6).  One CTA of 128 threads per 32-row
+// chunk of a tile (alpha, c): the steps are the live T slots of the chunk's
+// ancestors at every coarse level (the records k_peel_T compacted), each a
+// product F'(rows, 0:kout) T (kout x cols).  Step s + 1's F rows (transposed)
+// and T are copied into the other shared-memory stage with cp.async while step
+// s multiplies; thread (rg, cg) owns rows 4 rg .. 4 rg + 3 and columns
+// cg CW .. cg CW + CW - 1 (CW = MAXC / 16) in double-float accumulators, and
+// the FP64 tile -= hi + lo at the end.  macs (optional) receives the
+// multiply-adds of the valid rows and columns.
+// ---------------------------------------------------------------------------
+
+struct CoarseDF {
+    const int *ent, *pt2ent;
+    const int64_t *base;   // [nc_j * chi + 1]: first record of (A, c)
+    const int *cnt;        // [nc_j * chi]: live records of (A, c)
+    const PeelRec *rec;
+    const dfloat *F;       // U (Y side) or V (Z side) arena
+    const dfloat *T;       // [slots][kcap][cols]
+};
+
+constexpr int DF_MAXLV = MAX_LEVELS;
+
+__device__ __forceinline__ void cp_async8(void *dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+template <int MAXC>
+__global__ void __launch_bounds__(128) k_peel_gemm_df(const CoarseDF *cl, int ncl, int chi, const int *tile_alpha,
+                                                      const int *tile_color, const int *entl, const int64_t *item_tile,
+                                                      const int *item_row, int64_t nitems, int cols, int kcap,
+                                                      int64_t n, double *OUT, unsigned long long *macs) {
+    constexpr int CW = MAXC / 16;
+    constexpr int LDF = GEMM64_LDF;
+    extern __shared__ __align__(16) unsigned char smdf_raw[];
+    dfloat *Fs = reinterpret_cast<dfloat *>(smdf_raw);  // [2][kcap][LDF]: F' transposed
+    dfloat *Ts = Fs + 2 * kcap * LDF;                    // [2][kcap][MAXC]
+    __shared__ int lv_first[DF_MAXLV + 1], lv_n[DF_MAXLV], lv_rowoff[DF_MAXLV];
+    __shared__ int64_t lv_s0[DF_MAXLV];
+    const int64_t item = blockIdx.x;
+    if (item >= nitems) return;
+    const int tid = threadIdx.x, rg = tid >> 4, cg = tid & 15;
+    const int64_t p = item_tile[item];
+    const int alpha = tile_alpha[p], c = tile_color[p];
+    const int *ea = entl + (int64_t)alpha * ENT_FIELDS;
+    const int sa = ea[3] + item_row[item];
+    const int rows = min(GEMM64_ROWS, ea[4] - sa);
+    if (tid < ncl) {  // ancestor of the chunk at coarse level tid: its records
+        const CoarseDF &C = cl[tid];
+        const int A = C.pt2ent[sa];
+        const int64_t e = (int64_t)A * chi + c;
+        lv_s0[tid] = C.base[e];
+        lv_n[tid] = C.cnt[e];
+        lv_rowoff[tid] = sa - C.ent[(int64_t)A * ENT_FIELDS + 3];
+    }
+    __syncthreads();
+    if (tid == 0) {
+        lv_first[0] = 0;
+        for (int l = 0; l < ncl; ++l) lv_first[l + 1] = lv_first[l] + lv_n[l];
+    }
+    __syncthreads();
+    const int S = lv_first[ncl];
+    // stage the F rows and T of step s into buffer b; returns the step's rank
+    auto issue = [&](int s, int b) -> int {
+        int lv = 0;
+        while (s >= lv_first[lv + 1]) ++lv;
+        const CoarseDF &C = cl[lv];
+        const PeelRec rc = C.rec[lv_s0[lv] + (s - lv_first[lv])];
+        const int kout = rc.kout;
+        const dfloat *F = C.F + rc.foff + (int64_t)lv_rowoff[lv] * kout;
+        const dfloat *T = C.T + (int64_t)rc.slot * kcap * cols;
+        dfloat *fs = Fs + b * kcap * LDF, *ts = Ts + b * kcap * MAXC;
+        for (int o = tid; o < GEMM64_ROWS * kout; o += 128) {
+            const int row = o / kout, u = o - row * kout;
+            if (row < rows) cp_async8(&fs[u * LDF + row], F + o);
+            else fs[u * LDF + row] = dfloat(0.0f, 0.0f);
+        }
+        for (int o = tid; o < kout * MAXC; o += 128) {
+            const int u = o / MAXC, col = o - u * MAXC;
+            if (col < cols) cp_async8(&ts[o], T + (int64_t)u * cols + col);
+            else ts[o] = dfloat(0.0f, 0.0f);
+        }
+        cp_async_commit();
+        return kout;
+    };
+    dfloat acc[4][CW];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < CW; ++j) acc[i][j] = dfloat(0.0f, 0.0f);
+    unsigned long long nmac = 0;
+    int kcur = S > 0 ? issue(0, 0) : 0;
+    for (int s = 0; s < S; ++s) {
+        int knext = 0;
+        if (s + 1 < S) {
+            knext = issue(s + 1, (s + 1) & 1);  // that stage was last read in step s - 1
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
+        __syncthreads();
+        const dfloat *fs = Fs + (s & 1) * kcap * LDF, *ts = Ts + (s & 1) * kcap * MAXC;
+        for (int u = 0; u < kcur; ++u) {
+            const float4 f01 = *reinterpret_cast<const float4 *>(&fs[u * LDF + rg * 4]);
+            const float4 f23 = *reinterpret_cast<const float4 *>(&fs[u * LDF + rg * 4 + 2]);
+            const dfloat fv[4] = {dfloat(f01.x, f01.y), dfloat(f01.z, f01.w), dfloat(f23.x, f23.y),
+                                  dfloat(f23.z, f23.w)};
+            dfloat tv[CW];
+#pragma unroll
+            for (int j2 = 0; j2 < CW / 2; ++j2) {
+                const float4 x = *reinterpret_cast<const float4 *>(&ts[u * MAXC + cg * CW + 2 * j2]);
+                tv[2 * j2] = dfloat(x.x, x.y);
+                tv[2 * j2 + 1] = dfloat(x.z, x.w);
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < CW; ++j) acc[i][j] = df_fma(fv[i], tv[j], acc[i][j]);
+        }
+        nmac += (unsigned long long)rows * kcur * cols;
+        __syncthreads();  // stage s & 1 is refilled in step s + 1
+        kcur = knext;
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int row = rg * 4 + i;
+        if (row >= rows) continue;
+        double *out = OUT + ((int64_t)c * n + sa + row) * cols;
+#pragma unroll
+        for (int j = 0; j < CW; ++j) {
+            const int col = cg * CW + j;
+            if (col < cols) out[col] -= df_to(acc[i][j]);
+        }
+    }
+    if (macs && tid == 0 && nmac) atomicAdd(macs, nmac);
+}
+
 }  // namespace pm
 
 static Err f32_copy(DBuf &dst, const DBuf &src, int64_t count, cudaStream_t st) {
@@ -359,6 +536,56 @@ static Err factors_f32(Factors &f, cudaStream_t st) {
     HM_TRY(f32_copy(f.U32, f.U, f.nU, st));
     HM_TRY(f32_copy(f.V32, f.V, f.nV, st));
     HM_TRY(f32_copy(f.B32, f.B, f.nB, st));
+    return ok();
+}
+
+static Err df_copy(DBuf &dst, const DBuf &src, int64_t count, cudaStream_t st) {
+    HM_TRY(alloc(dst, std::max<int64_t>(count, 1) * sizeof(dfloat)));
+    if (count > 0) {
+        pm::k_to_df<<<ceil_div(count, 256), 256, 0, st>>>(src.as<double>(), dst.as<dfloat>(), count);
+        count_launch();
+        HM_LAUNCH("to_df");
+    }
+    return ok();
+}
+
+// double-float copies of a level's factors, made once when a finer level first peels it
+static Err factors_df(Factors &f, cudaStream_t st) {
+    if (f.U2.p) return ok();
+    HM_TRY(df_copy(f.U2, f.U, f.nU, st));
+    HM_TRY(df_copy(f.V2, f.V, f.nV, st));
+    HM_TRY(df_copy(f.B2, f.B, f.nB, st));
+    return ok();
+}
+
+// the double-float update of one side, timed by CUDA events (hm_info.seconds_peel_update)
+static Err launch_update_df(hm_ctx *c, const pm::CoarseDF *tab, int ntab, int chi, const Coloring &g, const Cut &cl,
+                            const DBuf &item_tile, const DBuf &item_row, int64_t nitems, int cols, int r, double *OUT) {
+    cudaStream_t st = c->st;
+    const int maxc = cols <= 32 ? 32 : 64;
+    const size_t smem = 2 * (size_t)r * (pm::GEMM64_LDF + maxc) * sizeof(dfloat);
+    if (smem > 220 * 1024) return fail(HM_ENOTSUP, "peel: r x columns per colour too large");
+    HM_TRY(ensure(c->peel_macs, sizeof(unsigned long long)));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    HM_CUDA(cudaEventCreate(&e0));
+    HM_CUDA(cudaEventCreate(&e1));
+    c->ev_update.push_back({e0, e1});
+    HM_CUDA(cudaEventRecord(e0, st));
+    auto *macs = c->peel_macs.as<unsigned long long>();
+    if (maxc == 32) {
+        HM_CUDA(cudaFuncSetAttribute(pm::k_peel_gemm_df<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        pm::k_peel_gemm_df<32><<<(unsigned)nitems, 128, smem, st>>>(
+            tab, ntab, chi, g.pair_alpha.as<int>(), g.pair_color.as<int>(), cl.ent.as<int>(), item_tile.as<int64_t>(),
+            item_row.as<int>(), nitems, cols, r, c->n, OUT, macs);
+    } else {
+        HM_CUDA(cudaFuncSetAttribute(pm::k_peel_gemm_df<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        pm::k_peel_gemm_df<64><<<(unsigned)nitems, 128, smem, st>>>(
+            tab, ntab, chi, g.pair_alpha.as<int>(), g.pair_color.as<int>(), cl.ent.as<int>(), item_tile.as<int64_t>(),
+            item_row.as<int>(), nitems, cols, r, c->n, OUT, macs);
+    }
+    count_launch();
+    HM_LAUNCH("peel_gemm_df");
+    HM_CUDA(cudaEventRecord(e1, st));
     return ok();
 }
 
@@ -432,8 +659,24 @@ template <> struct PeelData<double> {
     static constexpr int rows = pm::GEMM64_ROWS;
 };
 
+template <> struct PeelData<dfloat> {
+    static Err factors(Factors &f, cudaStream_t st) { return factors_df(f, st); }
+    static const dfloat *U(const Factors &f) { return f.U2.as<dfloat>(); }
+    static const dfloat *V(const Factors &f) { return f.V2.as<dfloat>(); }
+    static const dfloat *B(const Factors &f) { return f.B2.as<dfloat>(); }
+    static Err gauss(hm_ctx *c, DBuf *G2, const dfloat **G) {
+        HM_TRY(df_copy(G2[0], c->GO, c->n * c->cfg.r, c->st));
+        HM_TRY(df_copy(G2[1], c->GP, c->n * c->cfg.r, c->st));
+        G[0] = G2[0].as<dfloat>();
+        G[1] = G2[1].as<dfloat>();
+        return ok();
+    }
+    static constexpr int rows = pm::GEMM64_ROWS;
+};
+
 template <typename R> static Err peel_level_t(hm_ctx *c, int level, bool leaf) {
     using PD = PeelData<R>;
+    constexpr bool kDF = std::is_same<R, dfloat>::value;  // compacted records + double-float update
     const int l = leaf ? c->L : level;
     const int idx = leaf ? c->L + 1 : level;
     const Coloring &g = c->colorings[idx];
@@ -494,7 +737,8 @@ template <typename R> static Err peel_level_t(hm_ctx *c, int level, bool leaf) {
 
     for (int side = 0; side < (leaf ? 1 : 2); ++side) {
         std::vector<pm::CoarseT<R>> tab;
-        std::vector<DBuf> keep;  // X, offsets, T and live flags of every coarse level
+        std::vector<pm::CoarseDF> dtab;
+        std::vector<DBuf> keep;  // X, offsets, T, live flags and records of every coarse level
         for (size_t i = 0; i < js.size(); ++i) {
             const int j = js[i];
             Factors &f = c->factors[j];
@@ -545,14 +789,35 @@ template <typename R> static Err peel_level_t(hm_ctx *c, int level, bool leaf) {
             co.base = bases[i].as<int64_t>();
             co.T = T.as<R>();
             co.live = live.as<unsigned char>();
+            const int64_t ncomb = (int64_t)cj.nc * chi;
+            DBuf recb, cntb;
+            if (kDF) {
+                if (nslots[i] >= (1ll << 31)) return fail(HM_ENOTSUP, "peel: more than 2^31 T slots in one level");
+                HM_TRY(alloc(recb, std::max<int64_t>(nslots[i], 1) * sizeof(pm::PeelRec)));
+                HM_TRY(alloc(cntb, std::max<int64_t>(ncomb, 1) * sizeof(int)));
+                HM_CUDA(cudaMemsetAsync(cntb.p, 0, std::max<int64_t>(ncomb, 1) * sizeof(int), st));
+            }
             if (nslots[i] > 0) {
-                const int64_t ncomb = (int64_t)cj.nc * chi;
                 const size_t smem = (size_t)pm::WARPS * r * cols * sizeof(R);
                 HM_CUDA(cudaFuncSetAttribute(pm::k_peel_T<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
                 pm::k_peel_T<R><<<ceil_div(ncomb, pm::WARPS), pm::WARPS * 32, smem, st>>>(
-                    co, ncomb, chi, side, cols, r, cl.pt2ent.as<int>(), g.act_ptr.as<int>(), g.act_box.as<int>());
+                    co, ncomb, chi, side, cols, r, cl.pt2ent.as<int>(), g.act_ptr.as<int>(), g.act_box.as<int>(),
+                    kDF ? recb.as<pm::PeelRec>() : nullptr, kDF ? cntb.as<int>() : nullptr);
                 count_launch();
                 HM_LAUNCH("peel_T");
+            }
+            if (kDF) {
+                pm::CoarseDF d;
+                d.ent = cj.ent.as<int>();
+                d.pt2ent = cj.pt2ent.as<int>();
+                d.base = bases[i].as<int64_t>();
+                d.cnt = cntb.as<int>();
+                d.rec = recb.as<pm::PeelRec>();
+                d.F = reinterpret_cast<const dfloat *>(side ? PD::V(f) : PD::U(f));
+                d.T = reinterpret_cast<const dfloat *>(T.template as<R>());
+                dtab.push_back(d);
+                keep.push_back(std::move(recb));
+                keep.push_back(std::move(cntb));
             }
             tab.push_back(co);
             keep.push_back(std::move(X));
@@ -560,17 +825,29 @@ template <typename R> static Err peel_level_t(hm_ctx *c, int level, bool leaf) {
             keep.push_back(std::move(T));
             keep.push_back(std::move(live));
         }
-        DBuf tabd;
-        HM_TRY(alloc(tabd, tab.size() * sizeof(pm::CoarseT<R>)));
-        HM_CUDA(cudaMemcpyAsync(tabd.p, tab.data(), tab.size() * sizeof(pm::CoarseT<R>), cudaMemcpyHostToDevice, st));
         double *OUT = side ? c->cur.Z.as<double>() : c->cur.Y.as<double>();
-        if (nitems > 0) HM_TRY(launch_update(tabd.as<pm::CoarseT<R>>(), (int)tab.size(), side, chi, g, cl, item_tile,
-                                             item_row, nitems, cols, r, n, OUT, st));
+        DBuf tabd;
+        if constexpr (kDF) {
+            HM_TRY(alloc(tabd, dtab.size() * sizeof(pm::CoarseDF)));
+            HM_CUDA(cudaMemcpyAsync(tabd.p, dtab.data(), dtab.size() * sizeof(pm::CoarseDF), cudaMemcpyHostToDevice,
+                                    st));
+            if (nitems > 0)
+                HM_TRY(launch_update_df(c, tabd.as<pm::CoarseDF>(), (int)dtab.size(), chi, g, cl, item_tile, item_row,
+                                        nitems, cols, r, OUT));
+        } else {
+            HM_TRY(alloc(tabd, tab.size() * sizeof(pm::CoarseT<R>)));
+            HM_CUDA(cudaMemcpyAsync(tabd.p, tab.data(), tab.size() * sizeof(pm::CoarseT<R>), cudaMemcpyHostToDevice,
+                                    st));
+            if (nitems > 0)
+                HM_TRY(launch_update(tabd.as<pm::CoarseT<R>>(), (int)tab.size(), side, chi, g, cl, item_tile,
+                                     item_row, nitems, cols, r, n, OUT, st));
+        }
     }
     return ok();
 }
 
 Err peel_level_mixed(hm_ctx *c, int level, bool leaf) { return peel_level_t<float>(c, level, leaf); }
 Err peel_level_fp64(hm_ctx *c, int level, bool leaf) { return peel_level_t<double>(c, level, leaf); }
+Err peel_level_df(hm_ctx *c, int level, bool leaf) { return peel_level_t<dfloat>(c, level, leaf); }
 
 }  // namespace hm

@@ -32,7 +32,9 @@
 
 #include <cuda_bf16.h>
 
+#include <atomic>
 #include <cmath>
+#include <cstdlib>
 
 namespace hm {
 
@@ -45,7 +47,8 @@ constexpr int PWARPS = NPROD / 32;
 constexpr int NTHREADS = NPROD + 64;  // + MMA warp (16) + TMA warp (17)
 constexpr int A_PIECE = TM * 128;        // bytes of one A piece (16 KB)
 constexpr int COORD_BYTES = KC * 32;     // 64 entries x 8 floats
-constexpr unsigned long long WAIT_NS = 4000000000ull;  // 4 s per wait
+constexpr unsigned long long WAIT_NS = 4000000000ull;  // 4 s per wait (Params.wait_ns)
+constexpr unsigned long long STALL_WAIT_NS = 1000000ull;  // 1 ms in an injected stall
 
 __host__ __device__ constexpr int b_bytes(int r) { return 3 * 2 * r * 128; }
 __host__ __device__ constexpr int chunk_bytes(int r) { return b_bytes(r) + COORD_BYTES; }
@@ -89,17 +92,17 @@ __device__ __forceinline__ bool mbar_try(uint64_t *bar, uint32_t parity) {
     return ok != 0;
 }
 
-// Bounded wait: false (and *status set) when the phase does not complete in
-// time or another thread has already given up.
+// Bounded wait: false (and *status set) when the phase does not complete
+// within limit_ns or another thread has already given up.
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *status,
-                                          bool abortable = true) {
+                                          unsigned long long limit_ns, bool abortable = true) {
     if (mbar_try(bar, parity)) return true;
     const unsigned long long t0 = gtime();
     for (uint32_t it = 1;; ++it) {
         if (mbar_try(bar, parity)) return true;
         if ((it & 1023) == 0) {
             if (abortable && *status) return false;
-            if (gtime() - t0 > WAIT_NS) {
+            if (gtime() - t0 > limit_ns) {
                 *status = 1;
                 return false;
             }
@@ -244,6 +247,9 @@ struct Params {
     const int64_t *out_ptr;    // per colour (chi + 1)
     const int64_t *item_base;
     const int *item_color;
+    unsigned long long wait_ns;  // limit of every mbarrier wait
+    int withhold;              // fault injection: the TMA warp issues no copy, so the
+                               // pipeline's waits run out (set by the host only)
 };
 
 constexpr int SEG = 2;      // chunks accumulated in tensor memory before promotion
@@ -346,7 +352,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_sample_tc(Params P) {
         auto promote = [&](int sg) -> bool {
             const int set = sg & 1;
             // tcgen05.ld is warp-collective: the whole warp goes on or stops together
-            const bool done = mbar_wait(&seg_done[set], (uint32_t)(sg >> 1) & 1, status, false);
+            const bool done = mbar_wait(&seg_done[set], (uint32_t)(sg >> 1) & 1, status, P.wait_ns, false);
             if (!__all_sync(0xffffffffu, done)) return false;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint32_t base = trow + (uint32_t)(set * 6 * r);
@@ -380,7 +386,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_sample_tc(Params P) {
             const int s = q & 1;
             const uint32_t u = (uint32_t)(q >> 1);
             if (q + 1 < nchunks) cnext = reinterpret_cast<const float *>(gpack + (size_t)(q + 1) * CB + b_bytes(r))[tid];
-            if (ok && q >= 2) ok = mbar_wait(&empty[s], (u - 1) & 1, status);
+            if (ok && q >= 2) ok = mbar_wait(&empty[s], (u - 1) & 1, status, P.wait_ns);
             ok = __all_sync(0xffffffffu, ok);
             if (ok) {
                 unsigned char *st = smem + s * SB;
@@ -461,9 +467,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_sample_tc(Params P) {
         // ------------------------------------------------------------ TMA issuer
         if (lane == 0) {
             int issued = 0;
-            for (int q = 0; q < nchunks && ok; ++q) {
+            for (int q = 0; q < nchunks && ok && !P.withhold; ++q) {
                 const int s = q & 1;
-                if (q >= 2) ok = mbar_wait(&empty[s], ((uint32_t)(q >> 1) - 1) & 1, status);
+                if (q >= 2) ok = mbar_wait(&empty[s], ((uint32_t)(q >> 1) - 1) & 1, status, P.wait_ns);
                 if (!ok) break;
                 mbar_expect_tx(&full_b[s], b_bytes(r));
                 bulk_g2s(smem + s * SB + 3 * A_PIECE, gpack + (size_t)q * CB, b_bytes(r), &full_b[s]);
@@ -471,7 +477,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_sample_tc(Params P) {
             }
             // never leave a bulk copy in flight: wait for the last two issued
             for (int k = (issued > 2 ? issued - 2 : 0); k < issued; ++k)
-                mbar_wait(&full_b[k & 1], (uint32_t)(k >> 1) & 1, status, false);
+                mbar_wait(&full_b[k & 1], (uint32_t)(k >> 1) & 1, status, P.wait_ns, false);
         }
     } else if (lane == 0) {
         // ------------------------------------------------------------ MMA issuer
@@ -482,8 +488,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_sample_tc(Params P) {
             const int sg = q / SEG, set = sg & 1;
             const bool first = (q % SEG) == 0;
             // the accumulator set is free once the producers promoted segment sg - 2
-            if (first && sg >= 2) ok = mbar_wait(&set_free[set], (uint32_t)((sg >> 1) - 1) & 1, status);
-            if (ok) ok = mbar_wait(&full_a[s], u & 1, status) && mbar_wait(&full_b[s], u & 1, status);
+            if (first && sg >= 2) ok = mbar_wait(&set_free[set], (uint32_t)((sg >> 1) - 1) & 1, status, P.wait_ns);
+            if (ok) ok = mbar_wait(&full_a[s], u & 1, status, P.wait_ns) && mbar_wait(&full_b[s], u & 1, status, P.wait_ns);
             if (!ok) break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint32_t sa = smem_u32(smem + s * SB);
@@ -504,7 +510,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_sample_tc(Params P) {
         }
         // every MMA of this CTA has completed before tensor memory is freed
         mma_commit(&accum);
-        mbar_wait(&accum, 0, status, false);
+        mbar_wait(&accum, 0, status, P.wait_ns, false);
     }
     __syncwarp();
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -658,6 +664,19 @@ static Err make_xdf(hm_ctx *c) {
     return ok();
 }
 
+// Fault injection for the failure-detection tests: with HM_FAULT_TC_STALL_AFTER=k
+// in the environment when the library is loaded, the tensor-core sampler
+// launch after k normal ones withholds its copies and waits at most 1 ms, so
+// that its waits expire and the call returns HM_ETIMEOUT; it fires once.
+static std::atomic<long long> g_tc_stall_countdown{[] {
+    const char *s = getenv("HM_FAULT_TC_STALL_AFTER");
+    return s && *s ? atoll(s) : -1ll;
+}()};
+static bool tc_stall_now() {
+    if (g_tc_stall_countdown.load(std::memory_order_relaxed) < 0) return false;
+    return g_tc_stall_countdown.fetch_sub(1, std::memory_order_relaxed) == 0;
+}
+
 bool tc_supported(const hm_ctx *c) {
     const int r = c->cfg.r;
     return r % 8 == 0 && r >= 8 && r <= 40;
@@ -719,6 +738,8 @@ Err sample_tc(hm_ctx *c, int level, int kernel) {
     P.out_ptr = g.out_rows_ptr.as<int64_t>();
     P.item_base = ibased.as<int64_t>();
     P.item_color = icold.as<int>();
+    P.withhold = tc_stall_now() ? 1 : 0;
+    P.wait_ns = P.withhold ? STALL_WAIT_NS : WAIT_NS;
     const int smem = 2 * stage_bytes(r) + 1024;
     const unsigned grid = (unsigned)icol.size();
     cudaEvent_t e0, e1;

@@ -97,3 +97,21 @@ def oracle_op(w: W.Workload, t):
     if w.dense is not None:
         return h1.DenseOp(w.dense[t.perm][:, t.perm])
     return h1.KernelOp(w.points[t.perm], w.kernel)
+
+
+def check_structure(comp, t):
+    """Permutation, boxes of every level, cuts, neighbour and interaction lists:
+    bit-exact against the oracle's tree."""
+    m = hm()
+    assert np.array_equal(i32(comp.export(m.HM_X_PERM)), t.perm)
+    assert comp.info().L == t.L
+    for l in range(t.L + 1):
+        bx = i32(comp.export(m.HM_X_LEVEL_BOXES, l)).reshape(-1, 8)
+        ref = np.array([[b.start, b.end, *(list(b.anchor) + [0] * (3 - t.d)), b.parent, int(b.leaf), b.gid]
+                        for b in t.levels[l]])
+        assert np.array_equal(bx, ref), f"level {l} boxes"
+        cut = i32(comp.export(m.HM_X_CUT, l)).reshape(-1, 2)
+        assert np.array_equal(cut, np.array(t.cuts[l])), f"cut {l}"
+        nc = len(t.cuts[l])
+        assert csr(comp.export(m.HM_X_NEAR, l), nc) == t.near[l], f"near {l}"
+        assert csr(comp.export(m.HM_X_INTER, l), nc) == t.inter[l], f"inter {l}"

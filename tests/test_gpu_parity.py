@@ -12,7 +12,7 @@ import hm_workloads as W
 from oracle import h1 as oh1
 from oracle import tree as ot
 
-from gpu_helpers import csr, f64, factors, hm, i32, oracle_op, run_gpu, samples
+from gpu_helpers import check_structure, f64, factors, hm, i32, oracle_op, run_gpu, samples
 
 pytestmark = pytest.mark.gpu
 
@@ -31,22 +31,6 @@ def small_workloads():
         "cube_exp": W.Workload("cube_exp", np.random.default_rng(4).random((2500, 3)), W.K_EXP, leaf_size=48,
                                r=16, tol=1e-9, seed=3),
     }
-
-
-def check_structure(comp, t, levels=True):
-    m = hm()
-    assert np.array_equal(i32(comp.export(m.HM_X_PERM)), t.perm)
-    assert comp.info().L == t.L
-    for l in range(t.L + 1):
-        bx = i32(comp.export(m.HM_X_LEVEL_BOXES, l)).reshape(-1, 8)
-        ref = np.array([[b.start, b.end, *(list(b.anchor) + [0] * (3 - t.d)), b.parent, int(b.leaf), b.gid]
-                        for b in t.levels[l]])
-        assert np.array_equal(bx, ref), f"level {l} boxes"
-        cut = i32(comp.export(m.HM_X_CUT, l)).reshape(-1, 2)
-        assert np.array_equal(cut, np.array(t.cuts[l])), f"cut {l}"
-        nc = len(t.cuts[l])
-        assert csr(comp.export(m.HM_X_NEAR, l), nc) == t.near[l], f"near {l}"
-        assert csr(comp.export(m.HM_X_INTER, l), nc) == t.inter[l], f"inter {l}"
 
 
 @pytest.mark.parametrize("name", list(small_workloads()))

@@ -23,9 +23,15 @@ def test_apply_noalloc_matches_apply_on_two_calls():
     comp, _ = run_gpu(w, keep=False)
     X = torch.from_numpy(np.random.default_rng(0).standard_normal((w.n, 2))).cuda()
     for trans in (0, 1):
+        a0 = comp.info().device_allocs
         ref = comp.apply(X, trans)
+        assert comp.info().device_allocs > a0  # hm_apply allocates its scratch
         for _ in range(2):  # the scratch array keeps the previous call's contents
+            # hm_info.device_allocs counts every device allocation the library
+            # makes; the binding's output tensor comes from torch, outside it
+            a0 = comp.info().device_allocs
             got = comp.apply_noalloc(X, trans)
+            assert comp.info().device_allocs == a0, "hm_apply_noalloc allocated device memory"
             assert torch.linalg.norm(got - ref) <= 1e-10 * torch.linalg.norm(ref)
     # a request larger than the scratch array is refused with a clear error
     big = torch.zeros((w.n, 64), dtype=torch.float64, device="cuda")
