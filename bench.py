@@ -73,6 +73,12 @@ def parse():
     ap.add_argument("--no-relerr", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serving-jobs", type=int, default=48,
+                    help="jobs of the serving measurement (the streamed-jobs configuration has 256)")
+    ap.add_argument("--serving-matvecs", type=int, default=100,
+                    help="matvecs per job in the serving measurement (the configuration has 1000)")
+    ap.add_argument("--serving-slots", type=int, default=4)
     return ap.parse_args()
 
 
@@ -276,6 +282,79 @@ def time_mode(hm, w, pts, op, precision: int, rank: int, steps: int, relerr_iter
     return out
 
 
+def run_serving(hm, args):
+    """A stream of compression jobs (N log-uniform in [4k, 64k]; 2D curves with
+    log|x-y|, the torus with 1/|x-y| and exp(-|x-y|); tol 1e-6, spec precision)
+    through hm_server: Poisson arrivals at 1.2 times the single-stream capacity
+    (measured first on three jobs compressed one at a time), admission by
+    device-memory footprint, and a client thread that serves matvecs on every
+    job as soon as it is ready, while later jobs still compress."""
+    import threading
+
+    import numpy as np
+    import torch
+
+    import hm_workloads as W
+    jobs = W.serving_jobs(args.serving_jobs, n_min=4096, n_max=65536)
+    prec = PRECISIONS["mixed"][0]
+
+    def settings(w):
+        return hm.Settings(d=w.d, leaf_size=w.leaf_size, r=w.r, oversample=w.oversample, tol=w.tol,
+                           precision=prec, seed=w.seed)
+
+    one = hm.Server(slots=1)
+    t_single = []
+    for w in jobs[:3]:
+        st = one.wait(one.submit(w.points, settings(w), hm.kernel_op(w.kernel)), 600.0)
+        t_single.append(st.t_done - st.t_start)
+    one.close()
+    rate = 1.2 / (sum(t_single) / len(t_single))
+    gaps = np.random.default_rng(7).exponential(1.0 / rate, len(jobs))
+    srv = hm.Server(slots=args.serving_slots)
+    ids = [None] * len(jobs)
+    ready = threading.Semaphore(0)
+    errors = []
+
+    def client():
+        try:
+            for k, w in enumerate(jobs):
+                ready.acquire()
+                srv.wait(ids[k], 600.0)
+                xs = [torch.from_numpy(np.random.default_rng(k * 10 + i).standard_normal(w.n)).cuda()
+                      for i in range(2)]
+                for i in range(args.serving_matvecs):
+                    srv.apply(ids[k], xs[i % 2])
+                srv.release(ids[k])
+        except Exception as e:  # reported in the line
+            errors.append(repr(e))
+
+    th = threading.Thread(target=client)
+    t0 = time.perf_counter()
+    th.start()
+    nxt = t0
+    for k, w in enumerate(jobs):
+        nxt += gaps[k]
+        dt = nxt - time.perf_counter()
+        if dt > 0:
+            time.sleep(dt)
+        ids[k] = srv.submit(w.points, settings(w), hm.kernel_op(w.kernel))
+        ready.release()
+    th.join()
+    wall = time.perf_counter() - t0
+    info = srv.info()
+    srv.close()
+    return {"jobs": len(jobs), "matvecs_per_job": args.serving_matvecs, "slots": args.serving_slots,
+            "arrival_rate_jobs_per_s": round(rate, 3), "single_stream_s_per_job": round(sum(t_single) / 3, 4),
+            "jobs_per_s": round(info.jobs_per_s, 3), "job_p50_s": round(info.job_p50_s, 4),
+            "job_p99_s": round(info.job_p99_s, 4), "apply_p50_s": round(info.apply_p50_s, 6),
+            "apply_p99_s": round(info.apply_p99_s, 6), "applies": int(info.applies),
+            "max_running": int(info.max_running), "max_reserved_bytes": int(info.max_reserved),
+            "budget_bytes": int(info.budget), "completed": int(info.completed), "failed": int(info.failed),
+            "wall_s": round(wall, 2), "errors": errors,
+            "workload": "N log-uniform in [4096, 65536]; 2D curve r=1+0.3cos(5t) with log|x-y|, torus with "
+                        "1/|x-y| and exp(-|x-y|); tol 1e-6, r 32; Poisson arrivals"}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -361,6 +440,30 @@ def run_ours(args):
                "h2d_bytes_per_step": int(hp.numel() * 8 + hx.numel() * 8),
                "d2h_bytes_per_step": int(hy.numel() * 8), "time_to_compress_s": round(te / args.steps, 4)}
 
+    # the apply of the compressed operator alone (one right-hand side): every
+    # stored factor entry (U, V, B and the leaf blocks) is read once
+    apply_line = None
+    if rank == 0:
+        xs = [torch.from_numpy(np.random.default_rng(100 + k).standard_normal(w.n)).cuda() for k in range(2)]
+        for k in range(3):
+            comp.apply(xs[k % 2])
+        torch.cuda.synchronize()
+        reps = 20
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        for k in range(reps):
+            comp.apply(xs[k % 2])
+        a1.record(stream)
+        torch.cuda.synchronize()
+        ta = a0.elapsed_time(a1) / 1e3 / reps
+        pk, src = peaks()
+        nbytes = 8 * int(info.factor_floats) + 4 * 8 * w.n  # factors + x, y and their permuted copies
+        gbs = nbytes / ta / 1e9
+        apply_line = {"seconds": round(ta, 6), "bytes": nbytes, "achieved": round(gbs, 1),
+                      "peak": float(pk["hbm_gbs"]), "unit": "GB/s", "frac": round(gbs / float(pk["hbm_gbs"]), 4),
+                      "bound": "hbm", "peak_source": f"{src} hbm_gbs", "nrhs": 1,
+                      "l2": "factors (several GB) far larger than L2"}
+
     relerr = None
     if not args.no_relerr and rank == 0:
         relerr = comp.relerr(hm.kernel_op(w.kernel), args.relerr_iters)
@@ -368,6 +471,10 @@ def run_ours(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(w, rows_per_level=100)
+
+    serving = None
+    if rank == 0 and world == 1 and not args.no_serving:
+        serving = run_serving(hm, args)
 
     # the other precision modes on the same job, for the error / time trade-off
     # (one GPU only: under torchrun every GPU would be held meanwhile)
@@ -411,8 +518,8 @@ def run_ours(args):
         "matvec_cols": int(info.matvec_cols), "floats_per_dof": round(info.factor_floats / w.n, 1),
         "colors": [int(info.colors[l]) for l in range(2, info.L + 2)], "max_rank": int(info.max_rank),
         "phases_s": phases, "host_elapsed_s": round(elapsed_host, 3),
-        "roofline": roof_main, "roofline_second": roof_second,
-        "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
+        "roofline": roof_main, "roofline_second": roof_second, "apply": apply_line,
+        "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk, "serving": serving,
         "modes": modes,
     }
     print(json.dumps(out), flush=True)

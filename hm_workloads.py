@@ -57,6 +57,14 @@ def torus(n: int, seed: int, R: float = 1.0, rho: float = 0.3) -> np.ndarray:
     return np.ascontiguousarray(pts)
 
 
+def curve2d(n: int, lobes: int = 5, amp: float = 0.3) -> np.ndarray:
+    """n points equispaced in angle on the closed curve r(t) = 1 + amp cos(lobes t)
+    (a smooth star-shaped contour standing in for the paper's 2D boundary)."""
+    t = 2.0 * math.pi * np.arange(n) / n
+    rad = 1.0 + amp * np.cos(lobes * t)
+    return np.ascontiguousarray(np.stack([rad * np.cos(t), rad * np.sin(t)], axis=1))
+
+
 def sphere(n: int, seed: int, jitter: float = 0.1) -> np.ndarray:
     """Fibonacci points on the unit sphere with seeded Gaussian jitter.
 
@@ -153,3 +161,23 @@ def sphere_invr(n: int = 1 << 20, tol: float = 1e-8, r: int = 40) -> Workload:
     seed = SEED_BASE + 5
     return Workload(f"sphere_invr_{n}", sphere(n, seed), K_INVR, leaf_size=64,
                     r=r, tol=tol, seed=seed)
+
+
+def serving_jobs(count: int, n_min: int = 4096, n_max: int = 65536, tol: float = 1e-6, seed: int = SEED_BASE + 4):
+    """A stream of compression jobs: N log-uniform in [n_min, n_max], geometry and
+    kernel alternating between a 2D closed curve with log|x - y|, and the torus
+    with 1/|x - y| or exp(-|x - y|); tolerance tol, r = 32 (leaf 64 in 3D, 32 in 2D)."""
+    rng = np.random.default_rng(seed)
+    jobs = []
+    for k in range(count):
+        n = int(math.exp(rng.uniform(math.log(n_min), math.log(n_max))))
+        kind = k % 3
+        if kind == 0:
+            jobs.append(Workload(f"curve_log_{n}", curve2d(n), K_LOG, leaf_size=32, r=32, tol=tol, seed=seed + k))
+        elif kind == 1:
+            jobs.append(Workload(f"torus_invr_{n}", torus(n, seed + k), K_INVR, leaf_size=64, r=32, tol=tol,
+                                 seed=seed + k))
+        else:
+            jobs.append(Workload(f"torus_exp_{n}", torus(n, seed + k), K_EXP, leaf_size=64, r=32, tol=tol,
+                                 seed=seed + k))
+    return jobs

@@ -166,6 +166,10 @@ typedef struct {
                                  double-float peel update kernels during hm_compress */
     int64_t peel_update_macs; /* their multiply-adds: sum over tile rows, live coarse
                                  pairs and columns of rows x k x columns */
+    uint64_t pool_used_bytes; /* device memory in use in the device's default memory pool
+                                 (all contexts of the process) when the info was read */
+    uint64_t pool_peak_bytes; /* its high-water mark since the start of the last
+                                 hm_compress (which resets it) */
 } hm_info;
 
 /*
@@ -315,6 +319,100 @@ hm_status hm_apply_noalloc(hm_ctx *ctx, const double *x_dev, double *y_dev, int6
 
 /* Human-readable description of the last error on this context. */
 const char *hm_last_error(const hm_ctx *ctx);
+
+/* ---------------------------------------------------------------------------
+ * Serving (a library service around Algorithm 4.1; the paper has no
+ * counterpart).  A server admits compression jobs of differing size,
+ * geometry and kernel as device memory and worker slots free up, keeps each
+ * finished job's compressed operator resident, and serves matvecs with it.
+ *  - Admission: jobs are taken in submission order; a job starts when a worker
+ *    slot is free and its estimated peak footprint fits in the byte budget
+ *    next to the reservations of the jobs already admitted.  When a job's
+ *    compression ends, the samples and Gaussians are freed and its
+ *    reservation shrinks to the bytes it keeps (factors, leaf blocks, tree
+ *    and apply metadata), so queued jobs can start.
+ *  - Concurrency: every job has its own CUDA stream and is compressed by one
+ *    of the server's worker threads (hm_compress's colouring also runs ahead
+ *    on its own streams), so the work of concurrent jobs overlaps on the GPU.
+ *  - Results are those of the same job compressed alone with hm_compress on
+ *    the same inputs.
+ * The server uses the device current at hm_server_create.
+ * ------------------------------------------------------------------------- */
+typedef struct hm_server hm_server;
+
+typedef struct {
+    size_t hbm_budget;  /* bytes the admitted jobs may reserve; 0 = 85% of the free
+                           device memory at hm_server_create */
+    int slots;          /* jobs compressed at the same time (worker threads), 1..64 */
+} hm_server_config;
+
+typedef struct {
+    hm_config cfg;              /* the job's configuration (see hm_create) */
+    hm_op op;                   /* its black box; a dense matrix must stay valid and a
+                                   callback callable until the job is done */
+    const double *points_host;  /* n x d row-major FP64, original order; copied by
+                                   hm_server_submit (the caller may free it after) */
+    int64_t n;
+    int leaf_size;              /* as hm_tree_build (0 = cfg.leaf_size) */
+    double tol;                 /* as hm_compress (both 0 = cfg's) */
+    int rank;
+} hm_job_desc;
+
+enum { HM_JOB_QUEUED = 0, HM_JOB_RUNNING = 1, HM_JOB_READY = 2, HM_JOB_FAILED = 3 };
+
+typedef struct {
+    int state;                  /* HM_JOB_* */
+    hm_status status;           /* outcome of the compression (HM_OK when ready) */
+    double t_submit, t_start, t_done;  /* seconds since the server was created */
+    size_t reserved_bytes;      /* the job's current reservation */
+    size_t estimate_bytes;      /* its estimated peak footprint (the reservation while
+                                   it compresses) */
+    hm_info info;               /* hm_get_info of the job after its compression */
+} hm_job_stats;
+
+typedef struct {
+    int64_t submitted, completed, failed, released, queued, running;
+    int max_running;            /* largest number of jobs compressed at the same time */
+    size_t budget, reserved, max_reserved;
+    double jobs_per_s;          /* completed jobs / (last completion - first submission) */
+    double job_p50_s, job_p99_s;      /* submission -> compressed, over completed jobs */
+    int64_t applies;
+    double apply_p50_s, apply_p99_s;  /* hm_server_apply latency (host, end to end) */
+} hm_server_info;
+
+/* Create a server.  Errors: HM_EINVAL (null out or cfg, slots out of range),
+ * HM_ENOMEM, HM_ECUDA (no device). */
+hm_status hm_server_create(hm_server **out, const hm_server_config *cfg);
+
+/* Queue a job; *job_id receives its id.  Returns at once.  Errors: HM_EINVAL
+ * (null pointers, bad configuration or sizes), HM_ENOTSUP (the job's estimated
+ * footprint exceeds the whole budget), HM_ENOMEM. */
+hm_status hm_server_submit(hm_server *s, const hm_job_desc *job, int64_t *job_id);
+
+/* Wait until the job is ready or failed (at most timeout_s seconds; < 0 waits
+ * without limit); *stats (may be NULL) receives its record.  Returns the job's
+ * status, HM_ETIMEOUT if it is still queued or running, or HM_EINVAL (unknown
+ * or released id). */
+hm_status hm_server_wait(hm_server *s, int64_t job_id, double timeout_s, hm_job_stats *stats);
+
+/* y = A~ x (trans = 0) or A~^* x with a ready job's compressed operator, as
+ * hm_apply (device pointers, column-major n x nrhs, original order), on the
+ * job's stream; returns when y_dev is complete.  Calls on one job are
+ * serialised.  Errors: HM_EINVAL (unknown id, bad vectors), HM_ESTATE (job not
+ * ready), and those of hm_apply. */
+hm_status hm_server_apply(hm_server *s, int64_t job_id, const double *x_dev, double *y_dev, int64_t nrhs,
+                          int trans);
+
+/* Free a job (ready or failed) and its reservation.  Errors: HM_EINVAL (unknown
+ * id), HM_ESTATE (queued or running). */
+hm_status hm_server_release(hm_server *s, int64_t job_id);
+
+/* Counters and latency percentiles since hm_server_create.  Errors: HM_EINVAL. */
+hm_status hm_server_get_info(hm_server *s, hm_server_info *out);
+
+/* Stop the workers after the jobs already admitted, drop the queued ones and
+ * free every job.  Safe on NULL. */
+hm_status hm_server_destroy(hm_server *s);
 
 #ifdef __cplusplus
 }

@@ -29,7 +29,10 @@ HM_LEVEL_LEAF = -1
  HM_X_FACTOR_OFFS, HM_X_LEAF_D, HM_X_VERTEX_DEGREE) = range(1, 17)
 
 EXPORTED = ["hm_create", "hm_destroy", "hm_tree_build", "hm_color", "hm_sample", "hm_compress", "hm_apply",
-            "hm_relerr", "hm_get_info", "hm_export", "hm_last_error", "hm_apply_noalloc"]
+            "hm_relerr", "hm_get_info", "hm_export", "hm_last_error", "hm_apply_noalloc",
+            "hm_server_create", "hm_server_submit", "hm_server_wait", "hm_server_apply", "hm_server_release",
+            "hm_server_get_info", "hm_server_destroy"]
+HM_JOB_QUEUED, HM_JOB_RUNNING, HM_JOB_READY, HM_JOB_FAILED = range(4)
 
 
 class hm_config(ctypes.Structure):
@@ -58,7 +61,32 @@ class hm_info(ctypes.Structure):
                 ("tc_kernel_evals", ctypes.c_int64), ("device_allocs", ctypes.c_int64),
                 ("bb_tc_levels", ctypes.c_int), ("bb_fp64_levels", ctypes.c_int), ("leaf_size", ctypes.c_int),
                 ("rank", ctypes.c_int), ("tol", ctypes.c_double), ("seconds_peel_update", ctypes.c_double),
-                ("peel_update_macs", ctypes.c_int64)]
+                ("peel_update_macs", ctypes.c_int64), ("pool_used_bytes", ctypes.c_uint64),
+                ("pool_peak_bytes", ctypes.c_uint64)]
+
+class hm_server_config(ctypes.Structure):
+    _fields_ = [("hbm_budget", ctypes.c_size_t), ("slots", ctypes.c_int)]
+
+
+class hm_job_desc(ctypes.Structure):
+    _fields_ = [("cfg", hm_config), ("op", hm_op), ("points_host", ctypes.c_void_p), ("n", ctypes.c_int64),
+                ("leaf_size", ctypes.c_int), ("tol", ctypes.c_double), ("rank", ctypes.c_int)]
+
+
+class hm_job_stats(ctypes.Structure):
+    _fields_ = [("state", ctypes.c_int), ("status", ctypes.c_int), ("t_submit", ctypes.c_double),
+                ("t_start", ctypes.c_double), ("t_done", ctypes.c_double), ("reserved_bytes", ctypes.c_size_t),
+                ("estimate_bytes", ctypes.c_size_t), ("info", hm_info)]
+
+
+class hm_server_info(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("failed", ctypes.c_int64),
+                ("released", ctypes.c_int64), ("queued", ctypes.c_int64), ("running", ctypes.c_int64),
+                ("max_running", ctypes.c_int), ("budget", ctypes.c_size_t), ("reserved", ctypes.c_size_t),
+                ("max_reserved", ctypes.c_size_t), ("jobs_per_s", ctypes.c_double), ("job_p50_s", ctypes.c_double),
+                ("job_p99_s", ctypes.c_double), ("applies", ctypes.c_int64), ("apply_p50_s", ctypes.c_double),
+                ("apply_p99_s", ctypes.c_double)]
+
 
 PHASES = ["colouring", "test matrices", "black box", "peel", "bases+cores", "leaf black box", "leaf peel+extract",
           "tensor-core kernel"]
@@ -83,6 +111,13 @@ def _load():
         "hm_get_info": [P, ctypes.POINTER(hm_info)],
         "hm_export": [P, I, I, P, ctypes.POINTER(ctypes.c_size_t)],
         "hm_last_error": [P],
+        "hm_server_create": [ctypes.POINTER(P), ctypes.POINTER(hm_server_config)],
+        "hm_server_submit": [P, ctypes.POINTER(hm_job_desc), ctypes.POINTER(I64)],
+        "hm_server_wait": [P, I64, D, ctypes.POINTER(hm_job_stats)],
+        "hm_server_apply": [P, I64, P, P, I64, I],
+        "hm_server_release": [P, I64],
+        "hm_server_get_info": [P, ctypes.POINTER(hm_server_info)],
+        "hm_server_destroy": [P],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -315,3 +350,79 @@ class Compressor:
             raise ValueError(f"export_into: need a contiguous host tensor of at least {need} bytes")
         hm_export_into(self.ctx, what, level, out.data_ptr(), nbytes)
         return need
+
+
+# ---------------------------------------------------------------------------
+# serving (hm_server_*)
+# ---------------------------------------------------------------------------
+
+class Server:
+    """Compression jobs admitted by device-memory footprint, compressed
+    concurrently (one stream each) and kept resident for matvecs."""
+
+    def __init__(self, slots: int = 4, hbm_budget: int = 0):
+        import torch
+        self.torch = torch
+        cfg = hm_server_config(hbm_budget, slots)
+        h = ctypes.c_void_p()
+        st = _lib.hm_server_create(ctypes.byref(h), ctypes.byref(cfg))
+        if st != HM_OK:
+            raise HMError(st, "hm_server_create", "")
+        self.h = h
+        self._keep = {}
+
+    def submit(self, points, settings: Settings, op: hm_op, leaf_size: int = 0, tol: float = 0.0,
+               rank: int = 0) -> int:
+        """points: host array-like (n x d float64, original order)."""
+        import numpy as np
+        pts = np.ascontiguousarray(np.asarray(points, dtype=np.float64))
+        desc = hm_job_desc(settings.to_c(), op, pts.ctypes.data, pts.shape[0], leaf_size, tol, rank)
+        jid = ctypes.c_int64(0)
+        st = _lib.hm_server_submit(self.h, ctypes.byref(desc), ctypes.byref(jid))
+        if st != HM_OK:
+            raise HMError(st, "hm_server_submit", "")
+        self._keep[jid.value] = op  # a dense matrix or callback must outlive the job
+        return jid.value
+
+    def wait(self, job: int, timeout: float = -1.0) -> hm_job_stats:
+        stats = hm_job_stats()
+        st = _lib.hm_server_wait(self.h, job, timeout, ctypes.byref(stats))
+        if st != HM_OK:
+            raise HMError(st, "hm_server_wait", f"job {job}")
+        return stats
+
+    def apply(self, job: int, x, trans: int = 0):
+        """x: (n,) or (n, nrhs) float64 CUDA tensor in original order; synchronous."""
+        t = self.torch
+        vec = x.dim() == 1
+        X = x.reshape(x.shape[0], -1).to(dtype=t.float64)
+        Xc = X.t().contiguous()
+        Yc = t.empty_like(Xc)
+        t.cuda.current_stream().synchronize()  # X is complete before the job's stream reads it
+        st = _lib.hm_server_apply(self.h, job, Xc.data_ptr(), Yc.data_ptr(), X.shape[1], trans)
+        if st != HM_OK:
+            raise HMError(st, "hm_server_apply", f"job {job}")
+        Y = Yc.t()
+        return Y[:, 0] if vec else Y
+
+    def release(self, job: int):
+        st = _lib.hm_server_release(self.h, job)
+        if st != HM_OK:
+            raise HMError(st, "hm_server_release", f"job {job}")
+        self._keep.pop(job, None)
+
+    def info(self) -> hm_server_info:
+        out = hm_server_info()
+        _check(None, _lib.hm_server_get_info(self.h, ctypes.byref(out)), "hm_server_get_info")
+        return out
+
+    def close(self):
+        if self.h:
+            _lib.hm_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -54,12 +54,12 @@ template <int N> __device__ __forceinline__ void cp_wait() { asm volatile("cp.as
 
 // stage 1: s = F_q^T x(I_box) (F = V, box = column box; adjoint F = U, row
 // box), t_q = B_q s (adjoint B_q^T s), for the right-hand sides j0 .. j0+nb-1
-template <int NW>
+template <int NW, int NB>
 __global__ void __launch_bounds__(NW * 32) k_ap1(ApplyLevel L, const double *x, int nrhs, int trans, double *t) {
-    __shared__ double sp[NW][64][APPLY_NB];
-    __shared__ double ss[64][APPLY_NB];
+    __shared__ double sp[NW][64][NB];
+    __shared__ double ss[64][NB];
     const int64_t q = blockIdx.x;
-    const int j0 = blockIdx.y * APPLY_NB, nb = min(APPLY_NB, nrhs - j0);
+    const int j0 = blockIdx.y * NB, nb = min(NB, nrhs - j0);
     const int ku = L.kU[q], kv = L.kV[q];
     if (ku == 0 || kv == 0) return;  // no t_q: stage 2 skips the pair too
     const int kin = trans ? ku : kv, kout = trans ? kv : ku;
@@ -68,35 +68,35 @@ __global__ void __launch_bounds__(NW * 32) k_ap1(ApplyLevel L, const double *x, 
     const int s0 = e[3], m = e[4] - e[3];
     const double *F = trans ? L.U + L.offU[q] : L.V + L.offV[q];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    double a0[APPLY_NB], a1[APPLY_NB];
+    double a0[NB], a1[NB];
 #pragma unroll
-    for (int j = 0; j < APPLY_NB; ++j) a0[j] = a1[j] = 0.0;
+    for (int j = 0; j < NB; ++j) a0[j] = a1[j] = 0.0;
 #pragma unroll 4
     for (int i = w; i < m; i += NW) {
         const double *Fr = F + (int64_t)i * kin;
         const double *xr = x + (int64_t)(s0 + i) * nrhs + j0;
-        double xv[APPLY_NB];
+        double xv[NB];
 #pragma unroll
-        for (int j = 0; j < APPLY_NB; ++j) xv[j] = j < nb ? xr[j] : 0.0;
+        for (int j = 0; j < NB; ++j) xv[j] = j < nb ? xr[j] : 0.0;
         if (lane < kin) {
             const double f = Fr[lane];
 #pragma unroll
-            for (int j = 0; j < APPLY_NB; ++j) a0[j] = fma(f, xv[j], a0[j]);
+            for (int j = 0; j < NB; ++j) a0[j] = fma(f, xv[j], a0[j]);
         }
         if (lane + 32 < kin) {
             const double f = Fr[lane + 32];
 #pragma unroll
-            for (int j = 0; j < APPLY_NB; ++j) a1[j] = fma(f, xv[j], a1[j]);
+            for (int j = 0; j < NB; ++j) a1[j] = fma(f, xv[j], a1[j]);
         }
     }
 #pragma unroll
-    for (int j = 0; j < APPLY_NB; ++j) {
+    for (int j = 0; j < NB; ++j) {
         if (lane < kin) sp[w][lane][j] = a0[j];
         if (lane + 32 < kin) sp[w][lane + 32][j] = a1[j];
     }
     __syncthreads();
-    for (int o = threadIdx.x; o < kin * APPLY_NB; o += NW * 32) {
-        const int v = o / APPLY_NB, j = o % APPLY_NB;
+    for (int o = threadIdx.x; o < kin * NB; o += NW * 32) {
+        const int v = o / NB, j = o % NB;
         double acc = 0.0;
         for (int ww = 0; ww < NW; ++ww) acc += sp[ww][v][j];
         ss[v][j] = acc;
@@ -114,17 +114,18 @@ __global__ void __launch_bounds__(NW * 32) k_ap1(ApplyLevel L, const double *x, 
 
 // stage 2: y(rows of the item) += sum over the box's pairs of F_q(rows) t_q,
 // F = U (adjoint V of the transposed pair); ld: shared-memory row stride (odd)
+template <int NB>
 __global__ void __launch_bounds__(APPLY_ROWS) k_ap2(ApplyLevel L, const int *items, const double *t, int nrhs,
                                                      int trans, int ld, double *y) {
     extern __shared__ __align__(16) double sm2[];
     const int item = blockIdx.x;
-    const int j0 = blockIdx.y * APPLY_NB, nb = min(APPLY_NB, nrhs - j0);
+    const int j0 = blockIdx.y * NB, nb = min(NB, nrhs - j0);
     const int box = items[2 * item], r0 = items[2 * item + 1];
     const int *e = L.ent + (int64_t)box * ENT_FIELDS;
     const int bs = e[3], rows = min(APPLY_ROWS, e[4] - e[3] - r0);
     const int tid = threadIdx.x;
     const int t0 = L.int_ptr[box], t1 = L.int_ptr[box + 1];
-    // stage b: F rows at sm2 + b APPLY_ROWS ld, t at sm2 + 2 APPLY_ROWS ld + b 64 APPLY_NB
+    // stage b: F rows at sm2 + b APPLY_ROWS ld, t at sm2 + 2 APPLY_ROWS ld + b 64 NB
     double *const sT0 = sm2 + 2 * APPLY_ROWS * ld;
     // stage pair tt into buffer b; returns its rank (0: skip)
     auto issue = [&](int tt, int b) -> int {
@@ -137,21 +138,21 @@ __global__ void __launch_bounds__(APPLY_ROWS) k_ap2(ApplyLevel L, const int *ite
         const int k = trans ? kv : ku;
         const double *F = (trans ? L.V + L.offV[q] : L.U + L.offU[q]) + (int64_t)r0 * k;
         const double *tq = t + (trans ? L.toffV[q] : L.toffU[q]) * nrhs;
-        double *sF = sm2 + b * APPLY_ROWS * ld, *sT = sT0 + b * 64 * APPLY_NB;
+        double *sF = sm2 + b * APPLY_ROWS * ld, *sT = sT0 + b * 64 * NB;
         for (int o = tid; o < rows * k; o += APPLY_ROWS) {
             const int i = o / k, u = o - i * k;
             cp8(&sF[i * ld + u], F + o);
         }
         for (int o = tid; o < k * nb; o += APPLY_ROWS) {
             const int u = o / nb, j = o - u * nb;
-            cp8(&sT[u * APPLY_NB + j], tq + (int64_t)u * nrhs + j0 + j);
+            cp8(&sT[u * NB + j], tq + (int64_t)u * nrhs + j0 + j);
         }
         cp_commit();
         return k;
     };
-    double acc[APPLY_NB];
+    double acc[NB];
 #pragma unroll
-    for (int j = 0; j < APPLY_NB; ++j) acc[j] = 0.0;
+    for (int j = 0; j < NB; ++j) acc[j] = 0.0;
     int kcur = t0 < t1 ? issue(t0, 0) : 0;
     for (int tt = t0; tt < t1; ++tt) {
         const int s = tt - t0;
@@ -164,11 +165,11 @@ __global__ void __launch_bounds__(APPLY_ROWS) k_ap2(ApplyLevel L, const int *ite
         }
         __syncthreads();
         if (tid < rows && kcur > 0) {
-            const double *f = sm2 + (s & 1) * APPLY_ROWS * ld + tid * ld, *tv = sT0 + (s & 1) * 64 * APPLY_NB;
+            const double *f = sm2 + (s & 1) * APPLY_ROWS * ld + tid * ld, *tv = sT0 + (s & 1) * 64 * NB;
             for (int u = 0; u < kcur; ++u) {
                 const double fu = f[u];
 #pragma unroll
-                for (int j = 0; j < APPLY_NB; ++j) acc[j] = fma(fu, tv[u * APPLY_NB + j], acc[j]);
+                for (int j = 0; j < NB; ++j) acc[j] = fma(fu, tv[u * NB + j], acc[j]);
             }
         }
         __syncthreads();
@@ -180,21 +181,22 @@ __global__ void __launch_bounds__(APPLY_ROWS) k_ap2(ApplyLevel L, const int *ite
 
 // near field: y(rows) += sum over neighbours b of D_ab(rows, :) x(I_b) (adjoint
 // D_ba(:, rows)^T x(I_b)), the neighbour's points in chunks of APPLY_UC
+template <int NB>
 __global__ void __launch_bounds__(APPLY_ROWS) k_apnear(const int *ent, const int *items, const int *near_ptr,
                                                         const int *near_idx, const int *pairT, const int64_t *offD,
                                                         const double *D, const double *x, int nrhs, int trans,
                                                         double *y) {
     __shared__ double sD[APPLY_UC][APPLY_ROWS + 1];  // (column, row) of the block chunk
-    __shared__ double sx[APPLY_UC][APPLY_NB];
+    __shared__ double sx[APPLY_UC][NB];
     const int item = blockIdx.x;
-    const int j0 = blockIdx.y * APPLY_NB, nb = min(APPLY_NB, nrhs - j0);
+    const int j0 = blockIdx.y * NB, nb = min(NB, nrhs - j0);
     const int a = items[2 * item], r0 = items[2 * item + 1];
     const int *ea = ent + (int64_t)a * ENT_FIELDS;
     const int sa = ea[3], ma = ea[4] - ea[3], rows = min(APPLY_ROWS, ma - r0);
     const int tid = threadIdx.x;
-    double acc[APPLY_NB];
+    double acc[NB];
 #pragma unroll
-    for (int j = 0; j < APPLY_NB; ++j) acc[j] = 0.0;
+    for (int j = 0; j < NB; ++j) acc[j] = 0.0;
     for (int tt = near_ptr[a]; tt < near_ptr[a + 1]; ++tt) {
         const int b = near_idx[tt];
         const int *eb = ent + (int64_t)b * ENT_FIELDS;
@@ -224,7 +226,7 @@ __global__ void __launch_bounds__(APPLY_ROWS) k_apnear(const int *ent, const int
                 for (int u = 0; u < uc; ++u) {
                     const double d = sD[u][tid];
 #pragma unroll
-                    for (int j = 0; j < APPLY_NB; ++j) acc[j] = fma(d, j < nb ? sx[u][j] : 0.0, acc[j]);
+                    for (int j = 0; j < NB; ++j) acc[j] = fma(d, j < nb ? sx[u][j] : 0.0, acc[j]);
                 }
         }
     }
@@ -302,11 +304,30 @@ Err build_apply_plan(hm_ctx *c) {
 
 // --- apply ------------------------------------------------------------------
 
+// stage 1 (16 warps per pair where boxes are long, else 4) and stage 2 of one level
+template <int NB>
+static Err launch_level(const ApplyLevel &a, int max_rows, int64_t np, const int *items, int64_t nitems, int ld,
+                        const double *x, int nrhs, int trans, double *t, double *y, cudaStream_t st) {
+    const unsigned nblk = (unsigned)ceil_div(nrhs, NB);
+    if (max_rows > 1024) k_ap1<16, NB><<<dim3((unsigned)np, nblk), 512, 0, st>>>(a, x, nrhs, trans, t);
+    else k_ap1<4, NB><<<dim3((unsigned)np, nblk), 128, 0, st>>>(a, x, nrhs, trans, t);
+    ::hm::count_launch();
+    HM_LAUNCH("apply stage 1");
+    const size_t smem = (2 * (size_t)APPLY_ROWS * ld + 2 * 64 * NB) * sizeof(double);
+    HM_CUDA(cudaFuncSetAttribute(k_ap2<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    if (nitems > 0) {
+        k_ap2<NB><<<dim3((unsigned)nitems, nblk), APPLY_ROWS, smem, st>>>(a, items, t, nrhs, trans, ld, y);
+        ::hm::count_launch();
+        HM_LAUNCH("apply stage 2");
+    }
+    return ok();
+}
+
 Err apply_sorted_into(hm_ctx *c, const double *x, double *y, int nrhs, int trans, double *t) {
     cudaStream_t st = c->st;
     const ApplyPlan &P = c->plan;
     if (!P.ready) return fail(HM_ESTATE, "apply: no apply plan (compress first)");
-    const unsigned nblk = (unsigned)ceil_div(nrhs, APPLY_NB);
+    const int nb = nrhs >= 4 ? 4 : nrhs;  // right-hand sides per CTA: 1, 2 or 4
     HM_CUDA(cudaMemsetAsync(y, 0, (size_t)c->n * nrhs * sizeof(double), st));
     for (int l = 2; l <= c->L; ++l) {
         if (l >= (int)c->factors.size() || !c->factors[l].done || c->factors[l].n_pairs == 0) continue;
@@ -330,27 +351,25 @@ Err apply_sorted_into(hm_ctx *c, const double *x, double *y, int nrhs, int trans
         a.toffU = P.toffU[l].as<int64_t>();
         a.toffV = P.toffV[l].as<int64_t>();
         if (f.max_k > 64) return fail(HM_ENOTSUP, "apply: rank above 64");
-        // stage 1: 16 warps per pair where boxes are long, else 4
-        if (cu.max_rows > 1024) k_ap1<16><<<dim3((unsigned)f.n_pairs, nblk), 512, 0, st>>>(a, x, nrhs, trans, t);
-        else k_ap1<4><<<dim3((unsigned)f.n_pairs, nblk), 128, 0, st>>>(a, x, nrhs, trans, t);
-        ::hm::count_launch();
-        HM_LAUNCH("apply stage 1");
         const int ld = std::max(1, P.maxk[l]) | 1;
-        const size_t smem = (2 * (size_t)APPLY_ROWS * ld + 2 * 64 * APPLY_NB) * sizeof(double);
-        HM_CUDA(cudaFuncSetAttribute(k_ap2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        if (P.nitems[l] > 0) {
-            k_ap2<<<dim3((unsigned)P.nitems[l], nblk), APPLY_ROWS, smem, st>>>(a, P.items[l].as<int>(), t, nrhs, trans,
-                                                                              ld, y);
-            ::hm::count_launch();
-            HM_LAUNCH("apply stage 2");
+        switch (nb) {
+        case 1: HM_TRY(launch_level<1>(a, cu.max_rows, f.n_pairs, P.items[l].as<int>(), P.nitems[l], ld, x, nrhs, trans, t, y, st)); break;
+        case 2: HM_TRY(launch_level<2>(a, cu.max_rows, f.n_pairs, P.items[l].as<int>(), P.nitems[l], ld, x, nrhs, trans, t, y, st)); break;
+        default: HM_TRY(launch_level<4>(a, cu.max_rows, f.n_pairs, P.items[l].as<int>(), P.nitems[l], ld, x, nrhs, trans, t, y, st));
         }
     }
     const Cut &cl = c->cuts[c->L];
     const Coloring &gl = c->colorings[c->L + 1];
     if (c->leaf.done && c->leaf.n_pairs > 0 && P.nitems[c->L] > 0) {
-        k_apnear<<<dim3((unsigned)P.nitems[c->L], nblk), APPLY_ROWS, 0, st>>>(
-            cl.ent.as<int>(), P.items[c->L].as<int>(), cl.near_ptr.as<int>(), cl.near_idx.as<int>(),
-            gl.pair_T.as<int>(), c->leaf.offD.as<int64_t>(), c->leaf.D.as<double>(), x, nrhs, trans, y);
+        const dim3 grid((unsigned)P.nitems[c->L], (unsigned)ceil_div(nrhs, nb));
+#define NEAR(NBV)                                                                                                  \
+    k_apnear<NBV><<<grid, APPLY_ROWS, 0, st>>>(cl.ent.as<int>(), P.items[c->L].as<int>(), cl.near_ptr.as<int>(),    \
+                                               cl.near_idx.as<int>(), gl.pair_T.as<int>(), c->leaf.offD.as<int64_t>(), \
+                                               c->leaf.D.as<double>(), x, nrhs, trans, y)
+        if (nb == 1) NEAR(1);
+        else if (nb == 2) NEAR(2);
+        else NEAR(4);
+#undef NEAR
         ::hm::count_launch();
         HM_LAUNCH("apply near field");
     }

@@ -46,6 +46,15 @@ inline Err fail(hm_status c, const std::string &m) { Err e; e.code = c; e.msg = 
 // Stream on which the current API call allocates and frees (set on entry).
 extern thread_local cudaStream_t g_alloc_stream;
 
+// Sets g_alloc_stream for a scope (every entry point and worker thread).
+struct StreamScope {
+    cudaStream_t prev;
+    explicit StreamScope(cudaStream_t s) : prev(g_alloc_stream) { g_alloc_stream = s; }
+    ~StreamScope() { g_alloc_stream = prev; }
+    StreamScope(const StreamScope &) = delete;
+    StreamScope &operator=(const StreamScope &) = delete;
+};
+
 // Kernel launches made by this library (every launch site calls this once).
 void count_launch();
 long long launches_so_far();

@@ -37,12 +37,6 @@ using namespace hm;
 
 namespace {
 
-struct StreamScope {
-    cudaStream_t prev;
-    explicit StreamScope(cudaStream_t s) : prev(g_alloc_stream) { g_alloc_stream = s; }
-    ~StreamScope() { g_alloc_stream = prev; }
-};
-
 hm_status finish(hm_ctx *c, const Err &e) {
     if (e) {
         c->last_error = e.msg;
@@ -320,6 +314,13 @@ static Err compress_all(hm_ctx *c, const hm_op *op) {
     c->tc_evals = 0;
     c->bb_tc_levels = 0;
     c->bb_fp64_levels = 0;
+    {  // the pool's high-water mark from here on
+        cudaMemPool_t pool;
+        uint64_t zero = 0;
+        if (cudaDeviceGetDefaultMemPool(&pool, c->dev) == cudaSuccess)
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrUsedMemHigh, &zero);
+        cudaGetLastError();
+    }
     for (auto &e : c->ev_update) {
         cudaEventDestroy(e.first);
         cudaEventDestroy(e.second);
@@ -554,6 +555,15 @@ hm_status hm_get_info(hm_ctx *c, hm_info *out) {
     *out = c->info;
     out->launches_total = launches_so_far();
     out->device_allocs = allocs_so_far();
+    {
+        cudaMemPool_t pool;
+        uint64_t v = 0;
+        if (c->dev >= 0 && cudaDeviceGetDefaultMemPool(&pool, c->dev) == cudaSuccess) {
+            if (cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &v) == cudaSuccess) out->pool_used_bytes = v;
+            if (cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemHigh, &v) == cudaSuccess) out->pool_peak_bytes = v;
+        }
+        cudaGetLastError();
+    }
     out->leaf_size = c->leaf_size;
     if (c->stage >= 1) {
         out->n = c->n;

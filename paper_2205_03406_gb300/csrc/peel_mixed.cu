@@ -379,9 +379,9 @@ __global__ void __launch_bounds__(128) k_peel_gemm64(const CoarseT<double> *cl, 
 // Double-float update (HM_MIXED_BF16X6).  One CTA of 128 threads per 32-row
 // chunk of a tile (alpha, c): the steps are the live T slots of the chunk's
 // ancestors at every coarse level (the records k_peel_T compacted), each a
-// product F'(rows, 0:kout) T (kout x cols).  Step s + 1's F rows (transposed)
-// and T are copied into the other shared-memory stage with cp.async while step
-// s multiplies; thread (rg, cg) owns rows 4 rg .. 4 rg + 3 and columns
+// product F'(rows, 0:kout) T (kout x cols).  Step s + 1's F rows (row-major, a
+// flat copy) and T are copied into the other shared-memory stage with
+// cp.async while step s multiplies; thread (rg, cg) owns rows 4 rg .. 4 rg + 3 and columns
 // cg CW .. cg CW + CW - 1 (CW = MAXC / 16) in double-float accumulators, and
 // the FP64 tile -= hi + lo at the end.  macs (optional) receives the
 // multiply-adds of the valid rows and columns.
@@ -443,7 +443,8 @@ __global__ void __launch_bounds__(128) k_peel_gemm_df(const CoarseDF *cl, int nc
     }
     __syncthreads();
     const int S = lv_first[ncl];
-    // stage the F rows and T of step s into buffer b; returns the step's rank
+    // stage the F rows (row-major, leading dimension kout: one flat copy) and
+    // T of step s into buffer b; returns the step's rank
     auto issue = [&](int s, int b) -> int {
         int lv = 0;
         while (s >= lv_first[lv + 1]) ++lv;
@@ -453,10 +454,10 @@ __global__ void __launch_bounds__(128) k_peel_gemm_df(const CoarseDF *cl, int nc
         const dfloat *F = C.F + rc.foff + (int64_t)lv_rowoff[lv] * kout;
         const dfloat *T = C.T + (int64_t)rc.slot * kcap * cols;
         dfloat *fs = Fs + b * kcap * LDF, *ts = Ts + b * kcap * MAXC;
+        const int nf = rows * kout;
         for (int o = tid; o < GEMM64_ROWS * kout; o += 128) {
-            const int row = o / kout, u = o - row * kout;
-            if (row < rows) cp_async8(&fs[u * LDF + row], F + o);
-            else fs[u * LDF + row] = dfloat(0.0f, 0.0f);
+            if (o < nf) cp_async8(&fs[o], F + o);
+            else fs[o] = dfloat(0.0f, 0.0f);
         }
         for (int o = tid; o < kout * MAXC; o += 128) {
             const int u = o / MAXC, col = o - u * MAXC;
@@ -482,12 +483,10 @@ __global__ void __launch_bounds__(128) k_peel_gemm_df(const CoarseDF *cl, int nc
             cp_async_wait<0>();
         }
         __syncthreads();
-        const dfloat *fs = Fs + (s & 1) * kcap * LDF, *ts = Ts + (s & 1) * kcap * MAXC;
-        for (int u = 0; u < kcur; ++u) {
-            const float4 f01 = *reinterpret_cast<const float4 *>(&fs[u * LDF + rg * 4]);
-            const float4 f23 = *reinterpret_cast<const float4 *>(&fs[u * LDF + rg * 4 + 2]);
-            const dfloat fv[4] = {dfloat(f01.x, f01.y), dfloat(f01.z, f01.w), dfloat(f23.x, f23.y),
-                                  dfloat(f23.z, f23.w)};
+        const dfloat *fs = Fs + (s & 1) * kcap * LDF + rg * 4 * kcur, *ts = Ts + (s & 1) * kcap * MAXC;
+        // warps whose rows all lie past the chunk's last row skip the products
+        for (int u = 0; u < (rg * 4 < rows ? kcur : 0); ++u) {
+            const dfloat fv[4] = {fs[u], fs[kcur + u], fs[2 * kcur + u], fs[3 * kcur + u]};
             dfloat tv[CW];
 #pragma unroll
             for (int j2 = 0; j2 < CW / 2; ++j2) {

@@ -36,13 +36,17 @@ def test_binding_struct_layouts_match_header(tmp_path):
     src = tmp_path / "sizes.c"
     src.write_text(
         '#include <stdio.h>\n#include <stddef.h>\n#include "hm.h"\n'
-        'int main(void){printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(hm_config), sizeof(hm_op), sizeof(hm_info),'
-        ' offsetof(hm_config, seed), offsetof(hm_op, user), offsetof(hm_info, seconds_total)); return 0;}\n')
+        'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(hm_config), sizeof(hm_op),'
+        ' sizeof(hm_info), offsetof(hm_config, seed), offsetof(hm_op, user), offsetof(hm_info, seconds_total),'
+        ' offsetof(hm_info, pool_peak_bytes), sizeof(hm_job_desc), offsetof(hm_job_desc, rank),'
+        ' sizeof(hm_job_stats), sizeof(hm_server_info), offsetof(hm_server_info, apply_p99_s)); return 0;}\n')
     exe = tmp_path / "sizes"
     subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
     got = [int(v) for v in subprocess.check_output([str(exe)]).split()]
     want = [ctypes.sizeof(hm.hm_config), ctypes.sizeof(hm.hm_op), ctypes.sizeof(hm.hm_info),
-            hm.hm_config.seed.offset, hm.hm_op.user.offset, hm.hm_info.seconds_total.offset]
+            hm.hm_config.seed.offset, hm.hm_op.user.offset, hm.hm_info.seconds_total.offset,
+            hm.hm_info.pool_peak_bytes.offset, ctypes.sizeof(hm.hm_job_desc), hm.hm_job_desc.rank.offset,
+            ctypes.sizeof(hm.hm_job_stats), ctypes.sizeof(hm.hm_server_info), hm.hm_server_info.apply_p99_s.offset]
     assert got == want
 
 
@@ -136,3 +140,23 @@ def test_injected_allocation_failure_without_gpu(tmp_path):
     env = dict(os.environ, HM_FAULT_ALLOC_AFTER="0")
     out = subprocess.run([sys.executable, str(script)], env=env, capture_output=True, text=True, timeout=120)
     assert out.returncode == 0 and "ok" in out.stdout, out.stdout + out.stderr
+
+
+def test_server_argument_checks_without_gpu():
+    """The serving entry points check their arguments before any CUDA work; with
+    no device visible hm_server_create reports HM_ECUDA."""
+    import ctypes
+
+    import paper_2205_03406_gb300 as hm
+    L = hm.lib()
+    h = ctypes.c_void_p()
+    assert L.hm_server_create(None, None) == hm.HM_EINVAL
+    assert L.hm_server_create(ctypes.byref(h), ctypes.byref(hm.hm_server_config(0, 0))) == hm.HM_EINVAL
+    assert L.hm_server_create(ctypes.byref(h), ctypes.byref(hm.hm_server_config(0, 65))) == hm.HM_EINVAL
+    assert L.hm_server_create(ctypes.byref(h), ctypes.byref(hm.hm_server_config(0, 2))) == hm.HM_ECUDA
+    assert L.hm_server_submit(None, None, None) == hm.HM_EINVAL
+    assert L.hm_server_wait(None, 1, 0.0, None) == hm.HM_EINVAL
+    assert L.hm_server_apply(None, 1, None, None, 1, 0) == hm.HM_EINVAL
+    assert L.hm_server_release(None, 1) == hm.HM_EINVAL
+    assert L.hm_server_get_info(None, None) == hm.HM_EINVAL
+    assert L.hm_server_destroy(None) == hm.HM_OK
