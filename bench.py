@@ -79,6 +79,9 @@ def parse():
     ap.add_argument("--serving-matvecs", type=int, default=100,
                     help="matvecs per job in the serving measurement (the configuration has 1000)")
     ap.add_argument("--serving-slots", type=int, default=4)
+    ap.add_argument("--oracle-series", type=str, default=None,
+                    help="comma-separated torus sizes: time the full CPU oracle compression at each (and the "
+                         "2048-point 1D dense configuration, best of 3), print one JSON line, exit")
     return ap.parse_args()
 
 
@@ -583,6 +586,35 @@ class OracleSample:
                 "seconds_estimate": round(est, 2)}
 
 
+def oracle_series(sizes):
+    """The full CPU oracle (tree, colourings, samples, peel, bases, cores, leaf
+    blocks) timed end to end on the torus job at the given sizes, and on the
+    2048-point 1D dense log-kernel configuration (best of 3)."""
+    import hm_workloads as W
+    from oracle import h1 as oh1
+    from oracle import tree as ot
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    out = {"kind": "oracle", "cores": cores, "torus": [], "line1d_dense_2048": None}
+    w = W.line1d_dense()
+    best = float("inf")
+    for _ in range(3):
+        t0 = time.perf_counter()
+        t = ot.build_tree(w.points, w.leaf_size, w.uniform_depth)
+        oh1.compress(t, oh1.DenseOp(w.dense[t.perm][:, t.perm]), w.r, rank=w.rank, seed=w.seed)
+        best = min(best, time.perf_counter() - t0)
+    out["line1d_dense_2048"] = {"seconds_best_of_3": round(best, 3)}
+    for n in sizes:
+        w = W.torus_laplace(n=n, tol=1e-6, r=32)
+        t0 = time.perf_counter()
+        t = ot.build_tree(w.points, w.leaf_size)
+        H = oh1.compress(t, oh1.KernelOp(w.points[t.perm], w.kernel), w.r, tol=w.tol, seed=w.seed,
+                         oversample=w.oversample)
+        out["torus"].append({"n": n, "levels": t.L, "seconds": round(time.perf_counter() - t0, 2),
+                             "matvec_cols": H.matvec_cols, "floats_per_dof": round(H.floats() / n, 1)})
+        print(json.dumps(out), flush=True)
+    return out
+
+
 def cpu_baseline(w, rows_per_level: int = 100):
     return OracleSample(w).sample(rows_per_level)
 
@@ -619,6 +651,9 @@ def main():
     args = parse()
     if args.peaks:
         print(json.dumps(measure_peaks()), flush=True)
+        return
+    if args.oracle_series:
+        print(json.dumps(oracle_series([int(v) for v in args.oracle_series.split(",")])), flush=True)
         return
     if args.impl == "reference":
         run_reference(args)

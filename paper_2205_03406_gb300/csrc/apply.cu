@@ -42,6 +42,8 @@ Err permute_rows(hm_ctx *c, const double *in, double *out, int nrhs, bool to_sor
 
 namespace {
 
+constexpr int AP1_BATCH = 8;  // rows a stage-1 warp reads before it multiplies
+
 __device__ __forceinline__ void cp8(void *dst, const void *src) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
                  "l"(src)
@@ -53,7 +55,11 @@ template <int N> __device__ __forceinline__ void cp_wait() { asm volatile("cp.as
 }  // namespace
 
 // stage 1: s = F_q^T x(I_box) (F = V, box = column box; adjoint F = U, row
-// box), t_q = B_q s (adjoint B_q^T s), for the right-hand sides j0 .. j0+nb-1
+// box), t_q = B_q s (adjoint B_q^T s), for the right-hand sides j0 .. j0+nb-1.
+// Lanes are packed so that FP64 issue slots do useful work: with kp the
+// smallest of 8, 16, 32, 64 not below kin, lane l takes column l % kp of rows
+// l / kp (mod 32 / kp) of each group of rows (kp = 64: columns l and l + 32);
+// AP1_BATCH groups are read before the products, so their loads overlap.
 template <int NW, int NB>
 __global__ void __launch_bounds__(NW * 32) k_ap1(ApplyLevel L, const double *x, int nrhs, int trans, double *t) {
     __shared__ double sp[NW][64][NB];
@@ -68,38 +74,51 @@ __global__ void __launch_bounds__(NW * 32) k_ap1(ApplyLevel L, const double *x, 
     const int s0 = e[3], m = e[4] - e[3];
     const double *F = trans ? L.U + L.offU[q] : L.V + L.offV[q];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int kp = kin <= 8 ? 8 : (kin <= 16 ? 16 : (kin <= 32 ? 32 : 64));
+    const int rpi = kp >= 32 ? 1 : 32 / kp;            // rows per warp instruction
+    const int v = kp == 64 ? lane : lane % kp, rsub = kp >= 32 ? 0 : lane / kp;
+    const bool c0 = v < kin, c1 = kp == 64 && lane + 32 < kin;
     double a0[NB], a1[NB];
 #pragma unroll
     for (int j = 0; j < NB; ++j) a0[j] = a1[j] = 0.0;
-#pragma unroll 4
-    for (int i = w; i < m; i += NW) {
-        const double *Fr = F + (int64_t)i * kin;
-        const double *xr = x + (int64_t)(s0 + i) * nrhs + j0;
-        double xv[NB];
+    const int step = rpi * NW;  // rows per pass of all warps
+    for (int g0 = w * rpi; g0 < m; g0 += AP1_BATCH * step) {
+        double f0[AP1_BATCH], f1[AP1_BATCH], xv[AP1_BATCH][NB];
 #pragma unroll
-        for (int j = 0; j < NB; ++j) xv[j] = j < nb ? xr[j] : 0.0;
-        if (lane < kin) {
-            const double f = Fr[lane];
+        for (int b = 0; b < AP1_BATCH; ++b) {
+            const int i = g0 + b * step + rsub;
+            const bool in = i < m;
+            const double *Fr = F + (int64_t)i * kin;
+            f0[b] = (in && c0) ? Fr[v] : 0.0;
+            f1[b] = (in && c1) ? Fr[lane + 32] : 0.0;
 #pragma unroll
-            for (int j = 0; j < NB; ++j) a0[j] = fma(f, xv[j], a0[j]);
+            for (int j = 0; j < NB; ++j) xv[b][j] = (in && j < nb) ? x[(int64_t)(s0 + i) * nrhs + j0 + j] : 0.0;
         }
-        if (lane + 32 < kin) {
-            const double f = Fr[lane + 32];
 #pragma unroll
-            for (int j = 0; j < NB; ++j) a1[j] = fma(f, xv[j], a1[j]);
-        }
+        for (int b = 0; b < AP1_BATCH; ++b)
+#pragma unroll
+            for (int j = 0; j < NB; ++j) a0[j] = fma(f0[b], xv[b][j], a0[j]);
+        if (kp == 64)
+#pragma unroll
+            for (int b = 0; b < AP1_BATCH; ++b)
+#pragma unroll
+                for (int j = 0; j < NB; ++j) a1[j] = fma(f1[b], xv[b][j], a1[j]);
     }
+    // lanes holding the same column (rsub = 0 .. rpi-1) are added in rsub order
+#pragma unroll
+    for (int j = 0; j < NB; ++j)
+        for (int o = kp; o < 32; o <<= 1) a0[j] += __shfl_down_sync(0xffffffffu, a0[j], o);
 #pragma unroll
     for (int j = 0; j < NB; ++j) {
-        if (lane < kin) sp[w][lane][j] = a0[j];
-        if (lane + 32 < kin) sp[w][lane + 32][j] = a1[j];
+        if (rsub == 0 && c0) sp[w][v][j] = a0[j];
+        if (c1) sp[w][lane + 32][j] = a1[j];
     }
     __syncthreads();
     for (int o = threadIdx.x; o < kin * NB; o += NW * 32) {
-        const int v = o / NB, j = o % NB;
+        const int vv = o / NB, j = o % NB;
         double acc = 0.0;
-        for (int ww = 0; ww < NW; ++ww) acc += sp[ww][v][j];
-        ss[v][j] = acc;
+        for (int ww = 0; ww < NW; ++ww) acc += sp[ww][vv][j];
+        ss[vv][j] = acc;
     }
     __syncthreads();
     const double *Bq = L.B + L.offB[q];
@@ -107,47 +126,86 @@ __global__ void __launch_bounds__(NW * 32) k_ap1(ApplyLevel L, const double *x, 
     for (int o = threadIdx.x; o < kout * nb; o += NW * 32) {
         const int u = o / nb, j = o % nb;
         double acc = 0.0;
-        for (int v = 0; v < kin; ++v) acc = fma(trans ? Bq[(int64_t)v * kout + u] : Bq[(int64_t)u * kin + v], ss[v][j], acc);
+        for (int vv = 0; vv < kin; ++vv)
+            acc = fma(trans ? Bq[(int64_t)vv * kout + u] : Bq[(int64_t)u * kin + vv], ss[vv][j], acc);
         tq[(int64_t)u * nrhs + j0 + j] = acc;
     }
 }
 
-// stage 2: y(rows of the item) += sum over the box's pairs of F_q(rows) t_q,
-// F = U (adjoint V of the transposed pair); ld: shared-memory row stride (odd)
-template <int NB>
-__global__ void __launch_bounds__(APPLY_ROWS) k_ap2(ApplyLevel L, const int *items, const double *t, int nrhs,
-                                                     int trans, int ld, double *y) {
+// Sources of stage 2: for entry tt of a box's list, the rank k of the block
+// (0: skip), its rows r0.. (row-major, leading dimension k) and its t (k x
+// nrhs, leading dimension nrhs).
+struct FactorRows {  // admissible pairs of a level: U_q t_q (adjoint V_q of the transposed pair)
+    ApplyLevel L;
+    const double *t;
+    int trans;
+    __device__ int first(int box) const { return L.int_ptr[box]; }
+    __device__ int last(int box) const { return L.int_ptr[box + 1]; }
+    __device__ int rank(int tt) const {
+        const int q = trans ? L.pairT[tt] : tt;
+        return (L.kU[q] == 0 || L.kV[q] == 0) ? 0 : (trans ? L.kV[q] : L.kU[q]);
+    }
+    __device__ const double *rows(int tt, int r0, int k) const {
+        const int q = trans ? L.pairT[tt] : tt;
+        return (trans ? L.V + L.offV[q] : L.U + L.offU[q]) + (int64_t)r0 * k;
+    }
+    __device__ const double *tvec(int tt, int nrhs) const {
+        const int q = trans ? L.pairT[tt] : tt;
+        return t + (trans ? L.toffV[q] : L.toffU[q]) * nrhs;
+    }
+};
+struct NearRows {  // leaf neighbour blocks, forward: D_ab x(I_b)
+    const int *ent, *near_ptr, *near_idx;
+    const int64_t *offD;
+    const double *D, *x;
+    __device__ int first(int box) const { return near_ptr[box]; }
+    __device__ int last(int box) const { return near_ptr[box + 1]; }
+    __device__ int rank(int tt) const {
+        const int *eb = ent + (int64_t)near_idx[tt] * ENT_FIELDS;
+        return eb[4] - eb[3];
+    }
+    __device__ const double *rows(int tt, int r0, int k) const { return D + offD[tt] + (int64_t)r0 * k; }
+    __device__ const double *tvec(int tt, int nrhs) const {
+        return x + (int64_t)ent[(int64_t)near_idx[tt] * ENT_FIELDS + 3] * nrhs;
+    }
+};
+
+// stage 2: y(rows of the item) += sum over the box's list of F(rows) t, the
+// next entry's rows and t copied into the other shared-memory stage with
+// cp.async while the current one multiplies.  ld: row stride in shared memory
+// (odd, >= every k); every k <= 64.  A chunk of at most 16 (32) rows gives
+// each row 4 (2) threads, which take every 4th (2nd) column and are added by
+// shuffles, so that FP64 issue slots do useful work on short boxes.
+template <int NB, class Src>
+__global__ void __launch_bounds__(APPLY_ROWS) k_ap2(Src S, const int *ent, const int *items, int nrhs, int ld,
+                                                     double *y) {
     extern __shared__ __align__(16) double sm2[];
     const int item = blockIdx.x;
     const int j0 = blockIdx.y * NB, nb = min(NB, nrhs - j0);
     const int box = items[2 * item], r0 = items[2 * item + 1];
-    const int *e = L.ent + (int64_t)box * ENT_FIELDS;
+    const int *e = ent + (int64_t)box * ENT_FIELDS;
     const int bs = e[3], rows = min(APPLY_ROWS, e[4] - e[3] - r0);
     const int tid = threadIdx.x;
-    const int t0 = L.int_ptr[box], t1 = L.int_ptr[box + 1];
-    // stage b: F rows at sm2 + b APPLY_ROWS ld, t at sm2 + 2 APPLY_ROWS ld + b 64 NB
+    const int spr = rows <= 16 ? 4 : (rows <= 32 ? 2 : 1);  // threads per row
+    const int row = tid / spr, part = tid % spr;
+    const int t0 = S.first(box), t1 = S.last(box);
+    // stage b: rows at sm2 + b APPLY_ROWS ld, t at sm2 + 2 APPLY_ROWS ld + b 64 NB
     double *const sT0 = sm2 + 2 * APPLY_ROWS * ld;
-    // stage pair tt into buffer b; returns its rank (0: skip)
     auto issue = [&](int tt, int b) -> int {
-        const int q = trans ? L.pairT[tt] : tt;
-        const int ku = L.kU[q], kv = L.kV[q];
-        if (ku == 0 || kv == 0) {
-            cp_commit();  // keep one group per step
-            return 0;
+        const int k = S.rank(tt);
+        if (k > 0) {
+            const double *F = S.rows(tt, r0, k), *tq = S.tvec(tt, nrhs);
+            double *sF = sm2 + b * APPLY_ROWS * ld, *sT = sT0 + b * 64 * NB;
+            for (int o = tid; o < rows * k; o += APPLY_ROWS) {
+                const int i = o / k, u = o - i * k;
+                cp8(&sF[i * ld + u], F + o);
+            }
+            for (int o = tid; o < k * nb; o += APPLY_ROWS) {
+                const int u = o / nb, j = o - u * nb;
+                cp8(&sT[u * NB + j], tq + (int64_t)u * nrhs + j0 + j);
+            }
         }
-        const int k = trans ? kv : ku;
-        const double *F = (trans ? L.V + L.offV[q] : L.U + L.offU[q]) + (int64_t)r0 * k;
-        const double *tq = t + (trans ? L.toffV[q] : L.toffU[q]) * nrhs;
-        double *sF = sm2 + b * APPLY_ROWS * ld, *sT = sT0 + b * 64 * NB;
-        for (int o = tid; o < rows * k; o += APPLY_ROWS) {
-            const int i = o / k, u = o - i * k;
-            cp8(&sF[i * ld + u], F + o);
-        }
-        for (int o = tid; o < k * nb; o += APPLY_ROWS) {
-            const int u = o / nb, j = o - u * nb;
-            cp8(&sT[u * NB + j], tq + (int64_t)u * nrhs + j0 + j);
-        }
-        cp_commit();
+        cp_commit();  // one group per entry, empty or not
         return k;
     };
     double acc[NB];
@@ -164,19 +222,22 @@ __global__ void __launch_bounds__(APPLY_ROWS) k_ap2(ApplyLevel L, const int *ite
             cp_wait<0>();
         }
         __syncthreads();
-        if (tid < rows && kcur > 0) {
-            const double *f = sm2 + (s & 1) * APPLY_ROWS * ld + tid * ld, *tv = sT0 + (s & 1) * 64 * NB;
-            for (int u = 0; u < kcur; ++u) {
+        if (row < rows && kcur > 0) {
+            const double *f = sm2 + (s & 1) * APPLY_ROWS * ld + row * ld, *tv = sT0 + (s & 1) * 64 * NB;
+            for (int u = part; u < kcur; u += spr) {
                 const double fu = f[u];
 #pragma unroll
-                for (int j = 0; j < NB; ++j) acc[j] = fma(fu, tv[u * NB + j], acc[j]);
+                for (int j = 0; j < NB; ++j) acc[j] = fma(fu, j < nb ? tv[u * NB + j] : 0.0, acc[j]);
             }
         }
         __syncthreads();
         kcur = knext;
     }
-    if (tid < rows && t1 > t0)
-        for (int j = 0; j < nb; ++j) y[(int64_t)(bs + r0 + tid) * nrhs + j0 + j] += acc[j];
+#pragma unroll
+    for (int j = 0; j < NB; ++j)
+        for (int o = 1; o < spr; o <<= 1) acc[j] += __shfl_down_sync(0xffffffffu, acc[j], o);
+    if (part == 0 && row < rows && t1 > t0)
+        for (int j = 0; j < nb; ++j) y[(int64_t)(bs + r0 + row) * nrhs + j0 + j] += acc[j];
 }
 
 // near field: y(rows) += sum over neighbours b of D_ab(rows, :) x(I_b) (adjoint
@@ -314,9 +375,10 @@ static Err launch_level(const ApplyLevel &a, int max_rows, int64_t np, const int
     ::hm::count_launch();
     HM_LAUNCH("apply stage 1");
     const size_t smem = (2 * (size_t)APPLY_ROWS * ld + 2 * 64 * NB) * sizeof(double);
-    HM_CUDA(cudaFuncSetAttribute(k_ap2<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    HM_CUDA(cudaFuncSetAttribute(k_ap2<NB, FactorRows>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     if (nitems > 0) {
-        k_ap2<NB><<<dim3((unsigned)nitems, nblk), APPLY_ROWS, smem, st>>>(a, items, t, nrhs, trans, ld, y);
+        FactorRows src{a, t, trans};
+        k_ap2<NB, FactorRows><<<dim3((unsigned)nitems, nblk), APPLY_ROWS, smem, st>>>(src, a.ent, items, nrhs, ld, y);
         ::hm::count_launch();
         HM_LAUNCH("apply stage 2");
     }
@@ -362,14 +424,32 @@ Err apply_sorted_into(hm_ctx *c, const double *x, double *y, int nrhs, int trans
     const Coloring &gl = c->colorings[c->L + 1];
     if (c->leaf.done && c->leaf.n_pairs > 0 && P.nitems[c->L] > 0) {
         const dim3 grid((unsigned)P.nitems[c->L], (unsigned)ceil_div(nrhs, nb));
+        const int m_max = c->leaf.m_max;
+        if (!trans && m_max <= 64) {  // forward: the rows of D_ab are contiguous, like a factor's
+            NearRows src{cl.ent.as<int>(), cl.near_ptr.as<int>(), cl.near_idx.as<int>(), c->leaf.offD.as<int64_t>(),
+                         c->leaf.D.as<double>(), x};
+            const int ld = std::max(1, m_max) | 1;
+#define NEARF(NBV)                                                                                                 \
+    do {                                                                                                           \
+        const size_t smem = (2 * (size_t)APPLY_ROWS * ld + 2 * 64 * NBV) * sizeof(double);                         \
+        HM_CUDA(cudaFuncSetAttribute(k_ap2<NBV, NearRows>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)); \
+        k_ap2<NBV, NearRows><<<grid, APPLY_ROWS, smem, st>>>(src, cl.ent.as<int>(), P.items[c->L].as<int>(), nrhs,  \
+                                                             ld, y);                                              \
+    } while (0)
+            if (nb == 1) NEARF(1);
+            else if (nb == 2) NEARF(2);
+            else NEARF(4);
+#undef NEARF
+        } else {  // adjoint (columns of D_ba) or leaves above 64 points
 #define NEAR(NBV)                                                                                                  \
     k_apnear<NBV><<<grid, APPLY_ROWS, 0, st>>>(cl.ent.as<int>(), P.items[c->L].as<int>(), cl.near_ptr.as<int>(),    \
                                                cl.near_idx.as<int>(), gl.pair_T.as<int>(), c->leaf.offD.as<int64_t>(), \
                                                c->leaf.D.as<double>(), x, nrhs, trans, y)
-        if (nb == 1) NEAR(1);
-        else if (nb == 2) NEAR(2);
-        else NEAR(4);
+            if (nb == 1) NEAR(1);
+            else if (nb == 2) NEAR(2);
+            else NEAR(4);
 #undef NEAR
+        }
         ::hm::count_launch();
         HM_LAUNCH("apply near field");
     }

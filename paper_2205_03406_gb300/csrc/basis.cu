@@ -349,20 +349,21 @@ __global__ void __launch_bounds__(128) k_qr_warp(const int *tile_alpha, const in
 
 // sum over the rows i >= i0 of a(i, j) b(i, j') for the thread's column, added
 // over the row groups: the result for column t (t < r) is returned to thread t
-__device__ __forceinline__ void col_dots(const float *qa, int m, int r, int i0, int ca, int cb_lo, int cb_hi,
-                                         bool square, float (*red)[64], float *out) {
+template <typename T>
+__device__ __forceinline__ void col_dots(const T *qa, int m, int r, int i0, int ca, int cb_lo, int cb_hi,
+                                         bool square, T (*red)[64], T *out) {
     const int t = threadIdx.x, RP = r <= 32 ? 32 : 64, NG = (int)blockDim.x / RP, cj = t % RP, grp = t / RP;
-    float a = 0.0f;
+    T a = T(0);
     if (cj >= cb_lo && cj < cb_hi) {
         if (square)
-            for (int i = i0 + grp; i < m; i += NG) a = fmaf(qa[i * r + cj], qa[i * r + cj], a);
+            for (int i = i0 + grp; i < m; i += NG) a = fma(qa[i * r + cj], qa[i * r + cj], a);
         else
-            for (int i = i0 + grp; i < m; i += NG) a = fmaf(qa[i * r + ca], qa[i * r + cj], a);
+            for (int i = i0 + grp; i < m; i += NG) a = fma(qa[i * r + ca], qa[i * r + cj], a);
     }
     red[grp][cj] = a;
     __syncthreads();
     if (t < r) {
-        float v = 0.0f;
+        T v = T(0);
         for (int g = 0; g < NG; ++g) v += red[g][t];
         out[t] = v;
     }
@@ -370,12 +371,13 @@ __device__ __forceinline__ void col_dots(const float *qa, int m, int r, int i0, 
 }
 
 // A(i, j) -= tau v_i w_j for i >= s, j in (s, jhi); v_s = 1, v_i = A(i, s) below
-__device__ __forceinline__ void reflect(float *qa, int m, int r, int s, int jhi, float ts, const float *wv) {
+template <typename T>
+__device__ __forceinline__ void reflect(T *qa, int m, int r, int s, int jhi, T ts, const T *wv) {
     const int t = threadIdx.x, RP = r <= 32 ? 32 : 64, NG = (int)blockDim.x / RP, cj = t % RP, grp = t / RP;
     if (cj > s && cj < jhi) {
-        const float w = ts * wv[cj];
+        const T w = ts * wv[cj];
         for (int i = s + grp; i < m; i += NG) {
-            const float vi = (i == s) ? 1.0f : qa[i * r + s];
+            const T vi = (i == s) ? T(1) : qa[i * r + s];
             qa[i * r + cj] -= vi * w;
         }
     }
@@ -385,35 +387,36 @@ __device__ __forceinline__ void reflect(float *qa, int m, int r, int s, int jhi,
 // Column-pivoted Householder QR of the m x r shared tile qa (ld r), at most
 // kmax steps, stopping by the rank or tolerance rule; on return columns
 // 0..k-1 hold Q_k with R_jj >= 0, and every thread returns k.
-__device__ int qr32_pivoted(float *qa, int m, int r, int kmax, int rank, double tol) {
-    __shared__ float red[16][64], nrm[64], wv[64], tau[64], beta[64];
-    __shared__ float sh_sc;
+template <typename T>
+__device__ int qr_pivoted_smem(T *qa, int m, int r, int kmax, int rank, double tol) {
+    __shared__ T red[16][64], nrm[64], wv[64], tau[64], beta[64];
+    __shared__ T sh_sc;
     __shared__ int sh_piv, sh_stop;
     const int t = threadIdx.x;
-    float n0 = 0.0f;
+    T n0 = T(0);
     int k = 0;
     for (int s = 0; s < kmax; ++s) {
         col_dots(qa, m, r, s, 0, s, r, true, red, nrm);  // exact norms of the trailing columns
         if (t == 0) {
-            float best = -1.0f;
+            T best = T(-1);
             int piv = s;
             for (int j = s; j < r; ++j)
                 if (nrm[j] > best) {  // largest norm, lowest column on ties
                     best = nrm[j];
                     piv = j;
                 }
-            const float nv = sqrtf(best);
+            const T nv = sqrt(best);
             if (s == 0) n0 = nv;
-            const int stop = rank > 0 ? (s >= rank) : (!(n0 > 0.0f) || !((double)nv > tol * (double)n0));
+            const int stop = rank > 0 ? (s >= rank) : (!(n0 > T(0)) || !((double)nv > tol * (double)n0));
             sh_stop = stop;
             sh_piv = piv;
             if (!stop) {
-                const float x0 = qa[s * r + piv];
-                float tt = 0.0f, b = 0.0f, sc = 0.0f;
-                if (nv > 0.0f) {
-                    b = -copysignf(nv, x0);
+                const T x0 = qa[s * r + piv];
+                T tt = T(0), b = T(0), sc = T(0);
+                if (nv > T(0)) {
+                    b = -copysign(nv, x0);
                     tt = (b - x0) / b;
-                    sc = 1.0f / (x0 - b);
+                    sc = T(1) / (x0 - b);
                 }
                 tau[s] = tt;
                 beta[s] = b;
@@ -423,17 +426,17 @@ __device__ int qr32_pivoted(float *qa, int m, int r, int kmax, int rank, double 
         __syncthreads();
         if (sh_stop) break;
         const int piv = sh_piv;
-        const float sc = sh_sc, ts = tau[s], bs = beta[s];
+        const T sc = sh_sc, ts = tau[s], bs = beta[s];
         // swap columns s and piv, scale the reflector, set R_ss
         for (int i = t; i < m; i += blockDim.x) {
-            float vs = qa[i * r + s];
+            T vs = qa[i * r + s];
             if (piv != s) {
-                const float vp = qa[i * r + piv];
+                const T vp = qa[i * r + piv];
                 qa[i * r + piv] = vs;
                 vs = vp;
             }
             if (i > s) vs *= sc;
-            else if (i == s && bs != 0.0f) vs = bs;
+            else if (i == s && bs != T(0)) vs = bs;
             qa[i * r + s] = vs;
         }
         __syncthreads();
@@ -446,7 +449,7 @@ __device__ int qr32_pivoted(float *qa, int m, int r, int kmax, int rank, double 
     }
     // explicit Q_k, backward accumulation of the reflectors
     for (int j = k - 1; j >= 0; --j) {
-        const float tj = tau[j];
+        const T tj = tau[j];
         if (j < k - 1) {
             col_dots(qa, m, r, j + 1, j, j + 1, k, false, red, wv);
             if (t > j && t < k) wv[t] += qa[j * r + t];
@@ -454,9 +457,9 @@ __device__ int qr32_pivoted(float *qa, int m, int r, int kmax, int rank, double 
             reflect(qa, m, r, j, k, tj, wv);
         }
         for (int i = t; i < m; i += blockDim.x) {
-            float v;
-            if (i < j) v = 0.0f;
-            else if (i == j) v = 1.0f - tj;
+            T v;
+            if (i < j) v = T(0);
+            else if (i == j) v = T(1) - tj;
             else v = -tj * qa[i * r + j];
             qa[i * r + j] = v;
         }
@@ -464,17 +467,19 @@ __device__ int qr32_pivoted(float *qa, int m, int r, int kmax, int rank, double 
     }
     for (int o = t; o < m * k; o += blockDim.x) {  // R_jj >= 0
         const int j = o % k;
-        if (beta[j] < 0.0f) qa[(o / k) * r + j] = -qa[(o / k) * r + j];
+        if (beta[j] < T(0)) qa[(o / k) * r + j] = -qa[(o / k) * r + j];
     }
     __syncthreads();
     return k;
 }
 
 // One CTA per tile of min_rows < m <= max_rows rows; Q_k back to the FP64 tile.
-__global__ void __launch_bounds__(512) k_qr32(const int *tile_alpha, const int *tile_beta, const int *tile_color,
+template <typename T>
+__global__ void __launch_bounds__(512) k_qr_smem(const int *tile_alpha, const int *tile_beta, const int *tile_color,
                                               const int *ent, int64_t n, int r, int cap, int rank, double tol,
                                               double *Ybase, int *kout, int min_rows, int max_rows) {
-    extern __shared__ float qa[];  // m x r, leading dimension r
+    extern __shared__ __align__(16) unsigned char qa_raw[];
+    T *qa = reinterpret_cast<T *>(qa_raw);  // m x r, leading dimension r
     const int64_t p = blockIdx.x;
     const int *e = ent + (int64_t)tile_alpha[p] * ENT_FIELDS;
     const int m = e[4] - e[3];
@@ -482,9 +487,9 @@ __global__ void __launch_bounds__(512) k_qr32(const int *tile_alpha, const int *
     double *Ag = Ybase + ((int64_t)tile_color[p] * n + e[3]) * r;
     const int *eb = ent + (int64_t)tile_beta[p] * ENT_FIELDS;
     const int kmax = min(min(m, eb[4] - eb[3]), min(r, cap));
-    for (int o = threadIdx.x; o < m * r; o += blockDim.x) qa[o] = (float)Ag[o];
+    for (int o = threadIdx.x; o < m * r; o += blockDim.x) qa[o] = (T)Ag[o];
     __syncthreads();
-    const int k = qr32_pivoted(qa, m, r, kmax, rank, tol);
+    const int k = qr_pivoted_smem<T>(qa, m, r, kmax, rank, tol);
     for (int o = threadIdx.x; o < m * k; o += blockDim.x) Ag[(int64_t)(o / k) * r + o % k] = (double)qa[(o / k) * r + o % k];
     if (threadIdx.x == 0) kout[p] = k;
 }
@@ -582,7 +587,7 @@ __global__ void __launch_bounds__(512) k_ts_top(const int *tile_alpha, const int
     float *S = Rstack + off[p] * r * r;
     for (int o = threadIdx.x; o < ms * r; o += blockDim.x) qa[o] = S[o];
     __syncthreads();
-    const int k = qr32_pivoted(qa, ms, r, kmax, rank, tol);
+    const int k = qr_pivoted_smem<float>(qa, ms, r, kmax, rank, tol);
     for (int o = threadIdx.x; o < ms * r; o += blockDim.x) S[o] = qa[o];
     if (threadIdx.x == 0) kout[p] = k;
 }
@@ -843,15 +848,21 @@ Err bases_and_cores(hm_ctx *c, int level) {
     const int cap = c->kcap;  // r (fixed rank), or r - p and the rank cap (tolerance)
     // HM_MIXED_BF16X6_F32: tiles up to qr32_rows rows by the FP32 shared-memory
     // kernel, tiles up to ts_max rows by the FP32 tall-skinny QR, larger ones
-    // by the FP64 block kernel.  FP64: the warp kernel up to QR_WARP_ROWS rows,
-    // the block kernel beyond.
+    // by the FP64 block kernel.  FP64 modes: the warp kernel up to QR_WARP_ROWS
+    // rows, the FP64 shared-memory kernel up to qr64_rows (200 KB of tile), the
+    // block kernel beyond.
     const bool mixed = c->cfg.precision == HM_MIXED_BF16X6_F32;
     const int qr32_rows = mixed ? std::min(QR32_MAX_ROWS, (200 * 1024) / (4 * r)) : 0;
+    const int qr64_rows = mixed ? 0 : (200 * 1024) / (8 * r);
     const int ts_rows = (200 * 1024) / (8 * r) / 32 * 32;       // rows per tall-skinny block
     const int ts_max = mixed ? (200 * 1024) / (4 * r * r) * ts_rows : 0;
-    const int small_rows = mixed ? std::max(qr32_rows, ts_max) : QR_WARP_ROWS;
+    const int small_rows = mixed ? std::max(qr32_rows, ts_max) : std::max(QR_WARP_ROWS, qr64_rows);
     const size_t qr32_smem = (size_t)std::max(1, std::min(qr32_rows, cu.max_rows)) * r * sizeof(float);
-    if (mixed) HM_CUDA(cudaFuncSetAttribute(k_qr32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)qr32_smem));
+    const size_t qr64_smem = (size_t)std::max(1, std::min(qr64_rows, cu.max_rows)) * r * sizeof(double);
+    if (mixed)
+        HM_CUDA(cudaFuncSetAttribute(k_qr_smem<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)qr32_smem));
+    else if (cu.max_rows > QR_WARP_ROWS)
+        HM_CUDA(cudaFuncSetAttribute(k_qr_smem<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)qr64_smem));
     // tall-skinny blocks (the same for the Y and the Z tiles)
     DBuf ts_cnt, ts_off, blk_tile, blk_row0, blk_rows, rstack, taus;
     int64_t nblk = 0;
@@ -904,11 +915,11 @@ Err bases_and_cores(hm_ctx *c, int level) {
                 HM_LAUNCH("tall-skinny qr");
             }
             // tiles up to 256 rows with 128 threads, taller ones with 512
-            k_qr32<<<(int)np, 128, qr32_smem, st>>>(g.pair_alpha.as<int>(), cu.int_idx.as<int>(),
+            k_qr_smem<float><<<(int)np, 128, qr32_smem, st>>>(g.pair_alpha.as<int>(), cu.int_idx.as<int>(),
                                                     g.pair_color.as<int>(), cu.ent.as<int>(), n, r, cap, c->rank_fixed,
                                                     c->tol, T, kk, 0, std::min(256, qr32_rows)); ::hm::count_launch();
             if (cu.max_rows > 256 && qr32_rows > 256) {
-                k_qr32<<<(int)np, 512, qr32_smem, st>>>(g.pair_alpha.as<int>(), cu.int_idx.as<int>(),
+                k_qr_smem<float><<<(int)np, 512, qr32_smem, st>>>(g.pair_alpha.as<int>(), cu.int_idx.as<int>(),
                                                         g.pair_color.as<int>(), cu.ent.as<int>(), n, r, cap,
                                                         c->rank_fixed, c->tol, T, kk, 256, qr32_rows); ::hm::count_launch();
             }
@@ -916,6 +927,12 @@ Err bases_and_cores(hm_ctx *c, int level) {
             k_qr_warp<<<ceil_div(np, 4), 128, 0, st>>>(g.pair_alpha.as<int>(), cu.int_idx.as<int>(),
                                                        g.pair_color.as<int>(), cu.ent.as<int>(), n, r, cap,
                                                        c->rank_fixed, c->tol, T, kk, np); ::hm::count_launch();
+            if (cu.max_rows > QR_WARP_ROWS && qr64_rows > QR_WARP_ROWS) {
+                k_qr_smem<double><<<(int)np, 512, qr64_smem, st>>>(g.pair_alpha.as<int>(), cu.int_idx.as<int>(),
+                                                                   g.pair_color.as<int>(), cu.ent.as<int>(), n, r,
+                                                                   cap, c->rank_fixed, c->tol, T, kk, QR_WARP_ROWS,
+                                                                   qr64_rows); ::hm::count_launch();
+            }
         }
     }
     HM_LAUNCH("qr_tiles");

@@ -45,10 +45,11 @@ __global__ void k_to_df(const double *in, dfloat *out, int64_t n) {
 }
 
 // a live T slot of (ancestor A, colour c) for the double-float update: the
-// pair's factor offset in its arena, the slot, and the rank of the factor
+// pair's factor offset in its arena, the first row of its T (kout rows of
+// cols) in the compact T arena, and the rank of the factor
 struct PeelRec {
     int64_t foff;
-    int slot;
+    int trow;
     int kout;
 };
 
@@ -130,12 +131,14 @@ __global__ void k_anc_mark(const int *tile_alpha, const int *tile_color, int64_t
 // One warp per (A, c) combination of level j; for every entry t of A's
 // interaction list: W = sum of X_{q,gamma} over the gammas of colour c in the
 // other box, T[slot] = B W (Y side, B is kout x kin) or B^T W (Z side).
-// With rec != nullptr (double-float mode) it also writes the live slots of
-// each (A, c), in list order, as records rec[base[e] ..] and their count cnt[e].
+// With rec != nullptr (double-float mode) T is compact: only the live slots of
+// (A, c) are stored, kout rows each from row trow[e] on, and the records
+// rec[base[e] ..] (in list order) point at them; cnt[e] receives their number.
 template <typename R>
 __global__ void __launch_bounds__(WARPS * 32) k_peel_T(CoarseT<R> C, int64_t ncomb, int chi, int side, int cols,
                                                      int kcap, const int *pt2ent_l, const int *act_ptr,
-                                                     const int *act_box, PeelRec *rec, int *cnt) {
+                                                     const int *act_box, PeelRec *rec, int *cnt,
+                                                     const int64_t *trow) {
     extern __shared__ __align__(16) unsigned char sm_raw[];
     R *sm = reinterpret_cast<R *>(sm_raw);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -148,6 +151,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_peel_T(CoarseT<R> C, int64_t nco
     const int a0 = act_ptr[c], a1 = act_ptr[c + 1];
     const int t0 = C.int_ptr[A];
     int nlive = 0;
+    int64_t row = rec ? trow[e] : 0;  // next free row of the compact T
     for (int t = t0; t < C.int_ptr[A + 1]; ++t) {
         const int64_t slot = s0 + (t - t0);
         const int q = side ? C.pairT[t] : t;
@@ -168,7 +172,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_peel_T(CoarseT<R> C, int64_t nco
                 }
                 __syncwarp();
                 const R *Bq = C.B + C.offB[q];
-                R *To = C.T + slot * kcap * cols;
+                R *To = rec ? C.T + row * cols : C.T + slot * kcap * cols;
                 for (int o = lane; o < kout * cols; o += 32) {
                     const int u = o / cols, col = o % cols;
                     R sacc = R(0);
@@ -181,12 +185,37 @@ __global__ void __launch_bounds__(WARPS * 32) k_peel_T(CoarseT<R> C, int64_t nco
         }
         const bool live = kin > 0 && kout > 0 && lo < hi;  // the same in every lane
         if (lane == 0) {
-            C.live[slot] = live ? 1 : 0;
-            if (rec && live) rec[s0 + nlive] = PeelRec{side ? C.offV[q] : C.offU[q], (int)slot, kout};
+            if (C.live) C.live[slot] = live ? 1 : 0;
+            if (rec && live) rec[s0 + nlive] = PeelRec{side ? C.offV[q] : C.offU[q], (int)row, kout};
         }
         nlive += live ? 1 : 0;
+        if (live) row += kout;
     }
     if (rec && lane == 0) cnt[e] = nlive;
+}
+
+// Size of the compact T of every (A, c) (double-float mode): the sum of kout
+// over its live slots (the liveness rule of k_peel_T), one thread per (A, c).
+template <typename R>
+__global__ void k_peel_rows(CoarseT<R> C, int64_t ncomb, int chi, int side, const int *pt2ent_l,
+                            const int *act_ptr, const int *act_box, int64_t *rows) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= ncomb) return;
+    int64_t tot = 0;
+    if (C.base[e + 1] > C.base[e]) {
+        const int A = (int)(e / chi), c = (int)(e % chi);
+        const int a0 = act_ptr[c], a1 = act_ptr[c + 1];
+        for (int t = C.int_ptr[A]; t < C.int_ptr[A + 1]; ++t) {
+            const int q = side ? C.pairT[t] : t;
+            const int kin = side ? C.kU[q] : C.kV[q], kout = side ? C.kV[q] : C.kU[q];
+            if (kin == 0 || kout == 0) continue;
+            const int *eo = C.ent + (int64_t)C.int_idx[t] * ENT_FIELDS;
+            const int kb = pt2ent_l[eo[3]], ke = pt2ent_l[eo[4] - 1] + 1;
+            const int lo = lower_bound(act_box, a0, a1, kb);
+            if (lo < a1 && act_box[lo] < ke) tot += kout;
+        }
+    }
+    rows[e] = tot;
 }
 
 // work items of the update: chunks of gr rows of every tile
@@ -452,7 +481,7 @@ __global__ void __launch_bounds__(128) k_peel_gemm_df(const CoarseDF *cl, int nc
         const PeelRec rc = C.rec[lv_s0[lv] + (s - lv_first[lv])];
         const int kout = rc.kout;
         const dfloat *F = C.F + rc.foff + (int64_t)lv_rowoff[lv] * kout;
-        const dfloat *T = C.T + (int64_t)rc.slot * kcap * cols;
+        const dfloat *T = C.T + (int64_t)rc.trow * cols;
         dfloat *fs = Fs + b * kcap * LDF, *ts = Ts + b * kcap * MAXC;
         const int nf = rows * kout;
         for (int o = tid; o < GEMM64_ROWS * kout; o += 128) {
@@ -767,8 +796,6 @@ template <typename R> static Err peel_level_t(hm_ctx *c, int level, bool leaf) {
                 X.as<R>());
             count_launch();
             HM_LAUNCH("peel_x");
-            HM_TRY(alloc(T, std::max<int64_t>(nslots[i], 1) * r * cols * sizeof(R)));
-            HM_TRY(alloc(live, std::max<int64_t>(nslots[i], 1)));
             pm::CoarseT<R> co;
             co.ent = cj.ent.as<int>();
             co.pt2ent = cj.pt2ent.as<int>();
@@ -786,22 +813,41 @@ template <typename R> static Err peel_level_t(hm_ctx *c, int level, bool leaf) {
             co.xoff = xo.as<int64_t>();
             co.X = X.as<R>();
             co.base = bases[i].as<int64_t>();
-            co.T = T.as<R>();
-            co.live = live.as<unsigned char>();
+            co.live = nullptr;
             const int64_t ncomb = (int64_t)cj.nc * chi;
-            DBuf recb, cntb;
+            DBuf recb, cntb, trow;
             if (kDF) {
+                // compact T: kout rows per live slot only
                 if (nslots[i] >= (1ll << 31)) return fail(HM_ENOTSUP, "peel: more than 2^31 T slots in one level");
+                DBuf rows;
+                HM_TRY(alloc(rows, (ncomb + 1) * sizeof(int64_t)));
+                HM_TRY(alloc(trow, (ncomb + 1) * sizeof(int64_t)));
+                pm::k_peel_rows<R><<<ceil_div(ncomb, 128), 128, 0, st>>>(co, ncomb, chi, side, cl.pt2ent.as<int>(),
+                                                                          g.act_ptr.as<int>(), g.act_box.as<int>(),
+                                                                          rows.as<int64_t>());
+                count_launch();
+                HM_LAUNCH("peel_rows");
+                HM_TRY(scan_exclusive(rows.as<int64_t>(), trow.as<int64_t>(), ncomb, st));
+                int64_t trows = 0;
+                HM_TRY(read_scalar(trows, trow.as<int64_t>() + ncomb, st));
+                if (trows >= (1ll << 31)) return fail(HM_ENOTSUP, "peel: more than 2^31 rows of T in one level");
+                HM_TRY(alloc(T, std::max<int64_t>(trows, 1) * cols * sizeof(R)));
                 HM_TRY(alloc(recb, std::max<int64_t>(nslots[i], 1) * sizeof(pm::PeelRec)));
                 HM_TRY(alloc(cntb, std::max<int64_t>(ncomb, 1) * sizeof(int)));
                 HM_CUDA(cudaMemsetAsync(cntb.p, 0, std::max<int64_t>(ncomb, 1) * sizeof(int), st));
+            } else {
+                HM_TRY(alloc(T, std::max<int64_t>(nslots[i], 1) * r * cols * sizeof(R)));
+                HM_TRY(alloc(live, std::max<int64_t>(nslots[i], 1)));
+                co.live = live.as<unsigned char>();
             }
+            co.T = T.as<R>();
             if (nslots[i] > 0) {
                 const size_t smem = (size_t)pm::WARPS * r * cols * sizeof(R);
                 HM_CUDA(cudaFuncSetAttribute(pm::k_peel_T<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
                 pm::k_peel_T<R><<<ceil_div(ncomb, pm::WARPS), pm::WARPS * 32, smem, st>>>(
                     co, ncomb, chi, side, cols, r, cl.pt2ent.as<int>(), g.act_ptr.as<int>(), g.act_box.as<int>(),
-                    kDF ? recb.as<pm::PeelRec>() : nullptr, kDF ? cntb.as<int>() : nullptr);
+                    kDF ? recb.as<pm::PeelRec>() : nullptr, kDF ? cntb.as<int>() : nullptr,
+                    kDF ? trow.as<int64_t>() : nullptr);
                 count_launch();
                 HM_LAUNCH("peel_T");
             }
@@ -817,6 +863,7 @@ template <typename R> static Err peel_level_t(hm_ctx *c, int level, bool leaf) {
                 dtab.push_back(d);
                 keep.push_back(std::move(recb));
                 keep.push_back(std::move(cntb));
+                keep.push_back(std::move(trow));
             }
             tab.push_back(co);
             keep.push_back(std::move(X));
