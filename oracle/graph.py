@@ -137,3 +137,64 @@ def brute_force_edges(vbeta, vS):
             if vbeta[u] != vbeta[v] and (vbeta[u] in vS[v] or vbeta[v] in vS[u]):
                 edges.add((u, v))
     return edges
+
+
+@dataclass
+class BoxColoring:
+    """Colouring of the box constraint sets of uniform H^1 sampling (Section 4.2)."""
+    boxes: np.ndarray         # cut index of every vertex (boxes with a non-empty interaction list)
+    n_colors: int
+    n_edges: int
+    color: np.ndarray         # colour of every vertex
+    degree: np.ndarray
+    inter: list               # int(alpha) of every vertex (sorted cut indices)
+
+    def active(self, c: int) -> list:
+        """Boxes that carry random rows in colour c: the union of int(alpha)
+        over the boxes alpha of that colour (eq. unifh1constraints)."""
+        out = set()
+        for v in np.flatnonzero(self.color == c):
+            out.update(self.inter[v])
+        return sorted(out)
+
+
+def color_boxes(tree, l: int) -> BoxColoring:
+    """Uniform H^1, first sampling stage of cut l (Section 4.2): one vertex per
+    box alpha with a non-empty interaction list, in cut order; it asks for
+    G_beta on every beta in int(alpha) and zeros on near(alpha).  Two vertices
+    conflict when one asks for random rows on a box the other asks to be zero;
+    DSatur as for the pair graphs."""
+    boxes = [a for a in range(len(tree.cuts[l])) if tree.inter[l][a]]
+    nv = len(boxes)
+    inter = [sorted(tree.inter[l][a]) for a in boxes]
+    near = [sorted(tree.near[l][a]) for a in boxes]
+    g_ptr = np.zeros(nv + 1, dtype=np.int64)
+    z_ptr = np.zeros(nv + 1, dtype=np.int64)
+    for v in range(nv):
+        g_ptr[v + 1] = g_ptr[v] + len(inter[v])
+        z_ptr[v + 1] = z_ptr[v] + len(near[v])
+    g_idx = np.array([b for s in inter for b in s], dtype=np.int32)
+    z_idx = np.array([b for s in near for b in s], dtype=np.int32)
+    color = np.empty(nv, dtype=np.int32)
+    degree = np.empty(nv, dtype=np.int32)
+    n_edges = ctypes.c_int64(0)
+    lib = _native()
+    lib.oracle_color_sets.restype = ctypes.c_int
+    lib.oracle_color_sets.argtypes = [ctypes.c_int, ctypes.c_int] + [ctypes.c_void_p] * 7
+    nc = lib.oracle_color_sets(nv, len(tree.cuts[l]), g_ptr.ctypes.data, g_idx.ctypes.data if nv else None,
+                               z_ptr.ctypes.data, z_idx.ctypes.data if nv else None, color.ctypes.data,
+                               ctypes.addressof(n_edges), degree.ctypes.data)
+    if nc < 0:
+        raise MemoryError("oracle_color_sets failed")
+    return BoxColoring(np.array(boxes, dtype=np.int64), nc, int(n_edges.value), color.astype(np.int64),
+                       degree.astype(np.int64), inter)
+
+
+def brute_force_set_edges(gsets, zsets):
+    """Edges of set constraints straight from the definition, O(V^2)."""
+    edges = set()
+    for u in range(len(gsets)):
+        for v in range(u + 1, len(gsets)):
+            if set(gsets[u]) & set(zsets[v]) or set(gsets[v]) & set(zsets[u]):
+                edges.add((u, v))
+    return edges

@@ -43,7 +43,7 @@ from . import graph as og
 from . import tree as ot
 from .philox import gaussian_block
 
-SIDE_OMEGA, SIDE_PSI, SIDE_START = 0, 1, 2
+SIDE_OMEGA, SIDE_PSI, SIDE_START, SIDE_MIX = 0, 1, 2, 3
 
 
 # ----------------------------------------------------------------------------
@@ -159,7 +159,12 @@ class H1Matrix:
 
     def floats(self) -> int:
         s = 0
-        for lf in self.levels.values():
+        bases = getattr(self, "bases", None)
+        for l, lf in self.levels.items():
+            if bases and l in bases:  # uniform: one U and one V per box, a B per pair
+                U, V = bases[l]
+                s += sum(u.size for u in U.values()) + sum(v.size for v in V.values()) + sum(b.size for b in lf.B)
+                continue
             s += sum(u.size for u in lf.U) + sum(b.size for b in lf.B) + sum(v.size for v in lf.V)
         if self.leaf is not None:
             s += sum(d.size for d in self.leaf.D)
@@ -369,6 +374,112 @@ def compress(tree, op, r: int, rank: int = 0, tol: float = 0.0, seed: int = 0,
     if levels_only:
         return H
     H.leaf = extract_leaf(H, op, keep_samples)
+    return H
+
+
+def compress_uniform(tree, op, r: int, rank: int = 0, tol: float = 0.0, seed: int = 0,
+                     levels_only: bool = False, oversample: int = 10) -> H1Matrix:
+    """Randomized compression of a uniform H^1 matrix (Section 4.2; Algorithm
+    2.2's two stages applied to every box at once), level by level:
+
+      1. colour the box constraint sets (graph.color_boxes: G_beta on int(alpha),
+         zeros on near(alpha)); Y = A Omega - A^(l-1) Omega with Gaussian Omega;
+         U_alpha = qr(Y(I_alpha, colour of alpha)): Algorithm 2.2 orthonormalizes
+         the whole sample, all r = k + p columns (at most |I_alpha| and the
+         sampled block's width), with no truncation;
+      2. colour the pair constraint sets (the non-uniform graph) and fill the
+         test matrices with the bases instead of Gaussians: Psi(I_alpha) =
+         U_alpha; Z = A^* Psi - A^(l-1)* Psi, so the tile of the pair (beta,
+         alpha) gives T_ab = Z(I_beta, :k_alpha) = A_ab^* U_alpha;
+      3. V_beta = qr(sum over alpha in int(beta) of T_ab M_a, k), B_ab =
+         T_ab^T V_beta.  Section 4.2 sums the T_ab themselves, which spans the
+         row space of A(union of I_alpha, I_beta) when every U_alpha has r
+         columns; on an adaptive tree a box smaller than r has a narrower
+         basis and the plain sum can lose dimensions.  Reading: each term is
+         first mixed by its own Gaussian k_alpha x r matrix M_a (Philox, side
+         SIDE_MIX, keyed by the box alpha), a randomized sketch of the
+         concatenation [T_a1 ... T_am] with r columns.  The truncation (fixed
+         rank or tolerance, qr(Y, k) of Section 2.4) applies here, with the p
+         columns of oversampling.
+
+    A_ab ~ U_alpha B_ab V_beta^T.  The bases are shared by all pairs of a box;
+    the per-pair lists of the result hold references to them, so apply_levels
+    and the peel work unchanged.  Rank caps: k <= min(|I_beta|, rows of the
+    sampled block) always, and k <= r - p with a tolerance (k <= rank too when
+    both are given).  The leaf blocks are extracted as in Section 4.1.3."""
+    if rank <= 0 and tol <= 0.0:
+        raise ValueError("a tolerance or a rank is needed")
+    kcap = (min(r - oversample, rank) if rank > 0 else r - oversample) if tol > 0.0 else r
+    rank_fixed = 0 if tol > 0.0 else rank
+    H = H1Matrix(tree, {}, None, r)
+    H.uniform = True
+    H.bases = {}
+    L = tree.L
+    for l in range(2, L + 1):
+        pairs = ot.admissible_pairs(tree, l)
+        lf = LevelFactors(l, pairs, [tree.rng(l, a) for a, _ in pairs], [tree.rng(l, b) for _, b in pairs])
+        if not pairs:
+            H.levels[l] = lf
+            continue
+        coarse = sorted(H.levels)
+        # stage 1: column bases of every box
+        bcol = og.color_boxes(tree, l)
+        GO = gaussians(tree, l, SIDE_OMEGA, r, seed)
+        Om = np.zeros((tree.n, bcol.n_colors * r))
+        for c in range(bcol.n_colors):
+            for b in bcol.active(c):
+                s_, e_ = tree.rng(l, b)
+                Om[s_:e_, c * r:(c + 1) * r] = GO[s_:e_]
+        Y = op.apply(Om) - apply_levels(H, coarse, Om)
+        H.matvec_cols += Om.shape[1]
+        U = {}
+        for v, a in enumerate(bcol.boxes):
+            a = int(a)
+            a0, a1 = tree.rng(l, a)
+            c = int(bcol.color[v])
+            width = sum(tree.rng(l, b)[1] - tree.rng(l, b)[0] for b in bcol.inter[v])
+            kU = min(r, a1 - a0, width)
+            U[a] = qr_trunc(Y[a0:a1, c * r:(c + 1) * r], kU, 0.0, kU)
+        kmax = max(1, max(u.shape[1] for u in U.values()))
+        # stage 2: A_ab^* U_alpha for every pair, from the pair colouring
+        col = og.color_level(tree, l)
+        Psi = np.zeros((tree.n, col.n_colors * kmax))
+        for c in range(col.n_colors):
+            for b in col.active(c):
+                s_, e_ = tree.rng(l, b)
+                Psi[s_:e_, c * kmax:c * kmax + U[b].shape[1]] = U[b]
+        Z = op.apply_t(Psi) - apply_levels(H, coarse, Psi, transpose=True)
+        H.matvec_cols += Psi.shape[1]
+        pcol = col.pair_color
+        pindex = {pq: i for i, pq in enumerate(pairs)}
+        T = []
+        W = {}
+        mix = {}
+        for i, (a, b) in enumerate(pairs):
+            b0, b1 = lf.rng_b[i]
+            ct = pcol[pindex[(b, a)]]             # Psi of the pair (b, a) holds U_a on I_a
+            Tab = Z[b0:b1, ct * kmax:ct * kmax + U[a].shape[1]]
+            T.append(Tab)
+            if a not in mix:
+                mix[a] = gaussian_block(seed, SIDE_MIX, l, tree.box(l, a).gid, U[a].shape[1], r)
+            acc = W.setdefault(b, np.zeros((b1 - b0, r)))
+            acc += Tab @ mix[a]
+        V = {}
+        for b, Wb in W.items():
+            b0, b1 = tree.rng(l, b)
+            rows = sum(tree.rng(l, a)[1] - tree.rng(l, a)[0] for a in tree.inter[l][b])
+            V[b] = qr_trunc(Wb, rank_fixed, tol, min(kcap, b1 - b0, rows))
+        for i, (a, b) in enumerate(pairs):
+            lf.U.append(U[a])
+            lf.B.append(T[i].T @ V[b])
+            lf.V.append(V[b])
+        lf.coloring = col
+        lf.box_coloring = bcol
+        H.bases[l] = (U, V)
+        H.levels[l] = lf
+    if levels_only:
+        return H
+    H.leaf = extract_leaf(H, op)
     return H
 
 
