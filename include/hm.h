@@ -104,7 +104,23 @@ typedef struct {
     int precision;        /* hm_precision */
     int keep_samples;     /* non-zero: keep every level's peeled samples for hm_export */
     uint64_t seed;        /* Philox4x32-10 key of all test matrices */
+    int format;           /* HM_FORMAT_H1 (per-block bases, Section 4.1) or
+                             HM_FORMAT_UNIFORM_H1 (one column and one row basis per
+                             box and level, Section 4.2) */
 } hm_config;
+
+/* Formats of the compressed operator (hm_config.format). */
+enum {
+    HM_FORMAT_H1 = 0,          /* Algorithm 4.1: A_ab ~ U_ab B_ab V_ab^T, bases per pair */
+    HM_FORMAT_UNIFORM_H1 = 1   /* Section 4.2: A_ab ~ U_a B_ab V_b^T.  Stage 1 samples every
+                                  box's interactions at once (box colouring, Gaussian test
+                                  matrices) and keeps the whole r-column sample basis U_a;
+                                  stage 2 fills the pair test matrices with the bases,
+                                  Z(I_b) = A_ab^* U_a, and V_b = qr(sum over a of
+                                  A_ab^* U_a M_a, k) with Gaussian k_a x r mixes M_a,
+                                  B_ab = (A_ab^* U_a)^T V_b.  The truncation (rank or tol)
+                                  applies to V.  QR and the mixing in FP64 in every mode */
+};
 
 /*
  * User black box (Section 1): Y = A X when trans == 0, Y = A^* X when trans == 1.
@@ -210,6 +226,20 @@ hm_status hm_tree_build(hm_ctx *ctx, const double *points_dev, int64_t n, int le
 hm_status hm_color(hm_ctx *ctx, int level, int *n_colors);
 
 /*
+ * Section 4.2 (uniform H^1, first stage): the incompatibility graph of the box
+ * constraint sets of cut `level` (2..L) -- box alpha, with a non-empty
+ * interaction list, asks for random rows on int(alpha) and zeros on
+ * near(alpha); two boxes conflict when one's random boxes meet the other's
+ * zero boxes -- coloured with DSatur (Algorithm 2.3, ties by degree then
+ * id).  hm_compress does this itself in HM_FORMAT_UNIFORM_H1; the call exposes
+ * the stage (and hm_export its result) for tests.  *n_colors (host, may be
+ * NULL) receives chi.  Errors: HM_EINVAL (null ctx, level out of range),
+ * HM_ESTATE (no tree), HM_ENOTSUP (more than 2^20 boxes or 1024 colours),
+ * HM_ENOMEM, HM_ECUDA.
+ */
+hm_status hm_color_boxes(hm_ctx *ctx, int level, int *n_colors);
+
+/*
  * Algorithm 4.1, sampling step of one level: draw the colour-masked Gaussian
  * test matrices Omega_l and Psi_l (identity blocks for HM_LEVEL_LEAF) and store
  * Y = A Omega_l and Z = A^* Psi_l (not yet peeled) in the context.
@@ -285,7 +315,11 @@ enum {
     HM_X_FACTORS = 13,    /* double: U arena, V arena, B arena concatenated */
     HM_X_FACTOR_OFFS = 14,/* int64[n_pairs][3]: offsets of U, V, B in their arenas */
     HM_X_LEAF_D = 15,     /* double: leaf blocks, row-major |I_a| x |I_b| per neighbour pair */
-    HM_X_VERTEX_DEGREE = 16 /* int32[n_vertices] */
+    HM_X_VERTEX_DEGREE = 16,/* int32[n_vertices] */
+    HM_X_BOX_VERTEX_BOX = 17, /* int32[n_box_vertices]: cut entry of every vertex of the
+                                 uniform H^1 box graph of cut `level` (hm_color_boxes) */
+    HM_X_BOX_COLOR = 18,    /* int32[n_box_vertices]: its colour */
+    HM_X_BOX_DEGREE = 19    /* int32[n_box_vertices]: its degree */
 };
 
 /*

@@ -21,15 +21,17 @@ HM_OK, HM_EINVAL, HM_ENOMEM, HM_ESTATE, HM_ECUDA, HM_EOP, HM_ETIMEOUT, HM_ENOTSU
 STATUS_NAMES = ["HM_OK", "HM_EINVAL", "HM_ENOMEM", "HM_ESTATE", "HM_ECUDA", "HM_EOP", "HM_ETIMEOUT",
                 "HM_ENOTSUP"]
 HM_FP64, HM_MIXED_BF16X6, HM_MIXED_BF16X6_F32 = 0, 1, 2
+HM_FORMAT_H1, HM_FORMAT_UNIFORM_H1 = 0, 1
 HM_K_LOG, HM_K_LAPLACE3D, HM_K_INVR, HM_K_EXP = 1, 2, 3, 4
 HM_OP_KERNEL, HM_OP_DENSE, HM_OP_CALLBACK = 0, 1, 2
 HM_LEVEL_LEAF = -1
 (HM_X_PERM, HM_X_LEVEL_BOXES, HM_X_CUT, HM_X_NEAR, HM_X_INTER, HM_X_PAIR_VERTEX, HM_X_VERTEX_COLOR,
  HM_X_VERTEX_BETA, HM_X_GAUSS, HM_X_SAMPLE_Y, HM_X_SAMPLE_Z, HM_X_PAIR_RANKS, HM_X_FACTORS,
- HM_X_FACTOR_OFFS, HM_X_LEAF_D, HM_X_VERTEX_DEGREE) = range(1, 17)
+ HM_X_FACTOR_OFFS, HM_X_LEAF_D, HM_X_VERTEX_DEGREE, HM_X_BOX_VERTEX_BOX, HM_X_BOX_COLOR,
+ HM_X_BOX_DEGREE) = range(1, 20)
 
 EXPORTED = ["hm_create", "hm_destroy", "hm_tree_build", "hm_color", "hm_sample", "hm_compress", "hm_apply",
-            "hm_relerr", "hm_get_info", "hm_export", "hm_last_error", "hm_apply_noalloc",
+            "hm_relerr", "hm_get_info", "hm_export", "hm_last_error", "hm_apply_noalloc", "hm_color_boxes",
             "hm_server_create", "hm_server_submit", "hm_server_wait", "hm_server_apply", "hm_server_release",
             "hm_server_get_info", "hm_server_destroy"]
 HM_JOB_QUEUED, HM_JOB_RUNNING, HM_JOB_READY, HM_JOB_FAILED = range(4)
@@ -39,7 +41,8 @@ class hm_config(ctypes.Structure):
     _fields_ = [("d", ctypes.c_int), ("leaf_size", ctypes.c_int), ("uniform_depth", ctypes.c_int),
                 ("r", ctypes.c_int), ("oversample", ctypes.c_int), ("rank", ctypes.c_int),
                 ("tol", ctypes.c_double),
-                ("precision", ctypes.c_int), ("keep_samples", ctypes.c_int), ("seed", ctypes.c_uint64)]
+                ("precision", ctypes.c_int), ("keep_samples", ctypes.c_int), ("seed", ctypes.c_uint64),
+                ("format", ctypes.c_int)]
 
 
 HM_APPLY_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
@@ -103,6 +106,7 @@ def _load():
         "hm_destroy": [P],
         "hm_tree_build": [P, P, I64, I],
         "hm_color": [P, I, ctypes.POINTER(I)],
+        "hm_color_boxes": [P, I, ctypes.POINTER(I)],
         "hm_sample": [P, ctypes.POINTER(hm_op), I],
         "hm_compress": [P, ctypes.POINTER(hm_op), D, I],
         "hm_apply": [P, P, P, I64, I],
@@ -166,6 +170,12 @@ def hm_tree_build(ctx, points_dev: int, n: int, leaf_size: int = 0):
 def hm_color(ctx, level: int) -> int:
     nc = ctypes.c_int(0)
     _check(ctx, _lib.hm_color(ctx, level, ctypes.byref(nc)), "hm_color")
+    return nc.value
+
+
+def hm_color_boxes(ctx, level: int) -> int:
+    nc = ctypes.c_int(0)
+    _check(ctx, _lib.hm_color_boxes(ctx, level, ctypes.byref(nc)), "hm_color_boxes")
     return nc.value
 
 
@@ -265,10 +275,11 @@ class Settings:
     precision: int = HM_FP64
     keep_samples: bool = False
     seed: int = 0
+    format: int = HM_FORMAT_H1
 
     def to_c(self) -> hm_config:
         return hm_config(self.d, self.leaf_size, self.uniform_depth, self.r, self.oversample, self.rank,
-                         self.tol, self.precision, int(self.keep_samples), self.seed)
+                         self.tol, self.precision, int(self.keep_samples), self.seed, self.format)
 
 
 class Compressor:
@@ -301,6 +312,9 @@ class Compressor:
 
     def color(self, level: int) -> int:
         return hm_color(self.ctx, level)
+
+    def color_boxes(self, level: int) -> int:
+        return hm_color_boxes(self.ctx, level)
 
     def sample(self, op: hm_op, level: int):
         hm_sample(self.ctx, op, level)

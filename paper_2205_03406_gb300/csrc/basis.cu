@@ -94,7 +94,8 @@ constexpr int QR32_MAX_ROWS = 1600;  // FP32 shared-memory QR: at most this many
 // on exit the first k columns hold Q_k with R_jj >= 0.
 __global__ void __launch_bounds__(256) k_qr_tiles(const int *tile_alpha, const int *tile_beta, const int *tile_color,
                                                   const int *ent, int64_t n, int r, int cap, int rank, double tol,
-                                                  double *Ybase, int *kout, int min_rows) {
+                                                  double *Ybase, int *kout, int min_rows,
+                                                  const int *tile_cap = nullptr) {
     __shared__ double red[8][64];
     __shared__ double nrm[64], tau[64], beta[64];
     __shared__ int sh_piv, sh_stop;
@@ -107,7 +108,7 @@ __global__ void __launch_bounds__(256) k_qr_tiles(const int *tile_alpha, const i
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int *eb = ent + (int64_t)tile_beta[p] * ENT_FIELDS;
     // the block A(I_alpha, I_beta) has rank <= min(|I_alpha|, |I_beta|)
-    const int kmax = min(min(m, eb[4] - eb[3]), min(r, cap));
+    const int kmax = min(min(min(m, eb[4] - eb[3]), min(r, cap)), tile_cap ? tile_cap[p] : r);
     int k = 0;
     for (int s = 0; s < kmax; ++s) {
         // exact norms of the trailing columns
@@ -243,7 +244,8 @@ constexpr int QR_WARP_ROWS = QR_WARP_ROWS_DECL;
 
 __global__ void __launch_bounds__(128) k_qr_warp(const int *tile_alpha, const int *tile_beta, const int *tile_color,
                                                  const int *ent, int64_t n, int r, int cap, int rank, double tol,
-                                                 double *Ybase, int *kout, int64_t ntiles) {
+                                                 double *Ybase, int *kout, int64_t ntiles,
+                                                 const int *tile_cap = nullptr) {
     __shared__ double s_tau[4][64], s_beta[4][64];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t p = (int64_t)blockIdx.x * 4 + warp;
@@ -253,7 +255,7 @@ __global__ void __launch_bounds__(128) k_qr_warp(const int *tile_alpha, const in
     if (m > QR_WARP_ROWS) return;  // the block kernel factors this tile
     double *A = Ybase + ((int64_t)tile_color[p] * n + e[3]) * r;
     const int *eb = ent + (int64_t)tile_beta[p] * ENT_FIELDS;
-    const int kmax = min(min(m, eb[4] - eb[3]), min(r, cap));
+    const int kmax = min(min(min(m, eb[4] - eb[3]), min(r, cap)), tile_cap ? tile_cap[p] : r);
     double *tau = s_tau[warp], *beta = s_beta[warp];
     const int c0 = lane, c1 = lane + 32;
     double n0 = 0.0;
@@ -477,7 +479,8 @@ __device__ int qr_pivoted_smem(T *qa, int m, int r, int kmax, int rank, double t
 template <typename T>
 __global__ void __launch_bounds__(512) k_qr_smem(const int *tile_alpha, const int *tile_beta, const int *tile_color,
                                               const int *ent, int64_t n, int r, int cap, int rank, double tol,
-                                              double *Ybase, int *kout, int min_rows, int max_rows) {
+                                              double *Ybase, int *kout, int min_rows, int max_rows,
+                                              const int *tile_cap = nullptr) {
     extern __shared__ __align__(16) unsigned char qa_raw[];
     T *qa = reinterpret_cast<T *>(qa_raw);  // m x r, leading dimension r
     const int64_t p = blockIdx.x;
@@ -486,7 +489,7 @@ __global__ void __launch_bounds__(512) k_qr_smem(const int *tile_alpha, const in
     if (m <= min_rows || m > max_rows) return;  // another launch factors this tile
     double *Ag = Ybase + ((int64_t)tile_color[p] * n + e[3]) * r;
     const int *eb = ent + (int64_t)tile_beta[p] * ENT_FIELDS;
-    const int kmax = min(min(m, eb[4] - eb[3]), min(r, cap));
+    const int kmax = min(min(min(m, eb[4] - eb[3]), min(r, cap)), tile_cap ? tile_cap[p] : r);
     for (int o = threadIdx.x; o < m * r; o += blockDim.x) qa[o] = (T)Ag[o];
     __syncthreads();
     const int k = qr_pivoted_smem<T>(qa, m, r, kmax, rank, tol);
@@ -806,6 +809,30 @@ static Err launch_core(int64_t np, int nsplit, int r, int kc, cudaStream_t st, c
         r, kc, np, nsplit, kU, kV, offB, static_cast<const TP *>(Mpart), static_cast<const TP *>(S1part),
         static_cast<const TP *>(S2part), B);
     ::hm::count_launch();
+    return ok();
+}
+
+Err qr_tiles_fp64(hm_ctx *c, int level, const int *tile_box, const int *tile_color, const int *tile_cap, int64_t nt,
+                  int max_rows, double *base, int cap, int rank, double tol, int *kout) {
+    if (nt == 0) return ok();
+    cudaStream_t st = c->st;
+    const int r = c->cfg.r;
+    const int64_t n = c->n;
+    const int *ent = c->cuts[level].ent.as<int>();
+    const int qr64_rows = (200 * 1024) / (8 * r);
+    // the box is its own partner (tile_beta = tile_box): the caps come from tile_cap
+    k_qr_warp<<<ceil_div(nt, 4), 128, 0, st>>>(tile_box, tile_box, tile_color, ent, n, r, cap, rank, tol, base, kout,
+                                               nt, tile_cap); ::hm::count_launch();
+    if (max_rows > QR_WARP_ROWS) {
+        const size_t smem = (size_t)std::min(qr64_rows, max_rows) * r * sizeof(double);
+        HM_CUDA(cudaFuncSetAttribute(k_qr_smem<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_qr_smem<double><<<(unsigned)nt, 512, smem, st>>>(tile_box, tile_box, tile_color, ent, n, r, cap, rank, tol,
+                                                           base, kout, QR_WARP_ROWS, qr64_rows, tile_cap); ::hm::count_launch();
+    }
+    if (max_rows > qr64_rows)
+        k_qr_tiles<<<(unsigned)nt, 256, 0, st>>>(tile_box, tile_box, tile_color, ent, n, r, cap, rank, tol, base, kout,
+                                                 qr64_rows, tile_cap); ::hm::count_launch();
+    HM_LAUNCH("qr_tiles_fp64");
     return ok();
 }
 

@@ -158,6 +158,89 @@ __global__ void k_edges(int64_t nv, const int *vertex_pair, const int *vertex_be
     }
 }
 
+// Uniform H^1 (Section 4.2, eq. unifh1constraints): box alpha asks for random
+// rows on int(alpha) and zeros on near(alpha); u ~ v iff int(a_u) meets
+// near(a_v) or near(a_u) meets int(a_v).  By the symmetry of both lists the
+// neighbours of u are the vertex boxes in near(d) for d in int(a_u) and in
+// int(d) for d in near(a_u).  vid: box -> vertex id (-1: no interaction list).
+__global__ void k_box_edges(int64_t nv, const int *vbox, const int *vid, const int *near_ptr, const int *near_idx,
+                            const int *int_ptr, const int *int_idx, int pass, int *deg, const int64_t *adj_ptr,
+                            int *adj) {
+    extern __shared__ unsigned int bm[];
+    __shared__ int wsum[32];
+    __shared__ int pre[1024];
+    const int u = blockIdx.x;
+    const int nw = (int)((nv + 31) >> 5);
+    for (int i = threadIdx.x; i < nw; i += blockDim.x) bm[i] = 0u;
+    __syncthreads();
+    const int a = vbox[u];
+    for (int h = 0; h < 2; ++h) {
+        const int *p1 = h ? near_ptr : int_ptr, *i1 = h ? near_idx : int_idx;   // d in int(a), then near(a)
+        const int *p2 = h ? int_ptr : near_ptr, *i2 = h ? int_idx : near_idx;   // b in near(d), then int(d)
+        for (int t = p1[a]; t < p1[a + 1]; ++t) {
+            const int d = i1[t];
+            for (int q = p2[d] + threadIdx.x; q < p2[d + 1]; q += blockDim.x) {
+                const int v = vid[i2[q]];
+                if (v >= 0 && v != u) atomicOr(&bm[v >> 5], 1u << (v & 31));
+            }
+        }
+    }
+    __syncthreads();
+    const int per = (nw + blockDim.x - 1) / blockDim.x;
+    const int w0 = threadIdx.x * per, w1 = min(nw, w0 + per);
+    int c = 0;
+    for (int w = w0; w < w1; ++w) c += __popc(bm[w]);
+    if (!pass) {
+        c = block_sum(c, wsum);
+        if (threadIdx.x == 0) deg[u] = c;
+        return;
+    }
+    pre[threadIdx.x] = c;
+    __syncthreads();
+    for (int o = 1; o < blockDim.x; o <<= 1) {
+        int v = (threadIdx.x >= o) ? pre[threadIdx.x - o] : 0;
+        __syncthreads();
+        pre[threadIdx.x] += v;
+        __syncthreads();
+    }
+    int64_t o = adj_ptr[u] + pre[threadIdx.x] - c;
+    for (int w = w0; w < w1; ++w) {
+        unsigned int x = bm[w];
+        while (x) {
+            const int bit = __ffs(x) - 1;
+            x &= x - 1;
+            adj[o++] = w * 32 + bit;
+        }
+    }
+}
+
+__global__ void k_box_vertices(const int *int_ptr, int nc, const int64_t *vscan, int *vbox, int *vid) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nc) return;
+    const bool has = int_ptr[b + 1] > int_ptr[b];
+    vid[b] = has ? (int)vscan[b] : -1;
+    if (has) vbox[vscan[b]] = b;
+}
+
+__global__ void k_box_has_int(const int *int_ptr, int nc, int64_t *flag) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < nc) flag[b] = int_ptr[b + 1] > int_ptr[b] ? 1 : 0;
+}
+
+// active (colour, box): every box of int(alpha) for the vertex boxes alpha of the colour
+__global__ void k_act_mark_box(const int *vbox, const int *vertex_color, int64_t nv, const int *int_ptr,
+                               const int *int_idx, int nc, unsigned char *act) {
+    int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (v >= nv) return;
+    const int a = vbox[v];
+    for (int t = int_ptr[a]; t < int_ptr[a + 1]; ++t) act[(int64_t)vertex_color[v] * nc + int_idx[t]] = 1;
+}
+
+__global__ void k_iota(int *x, int64_t n) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) x[i] = (int)i;
+}
+
 __global__ void k_dsatur_init(int64_t nv, const int *deg, unsigned long long *key, unsigned int *forb) {
     int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (v >= nv) return;
@@ -381,6 +464,122 @@ __global__ void k_act_rows(const int *act_box, int64_t na, const int *ent, const
     for (int r = e[3] + lane; r < e[4]; r += 32) rows[rowoff[i] + (r - e[3])] = r;
 }
 
+// DSatur over the adjacency (adj_ptr, adj), then the tables the sampler and
+// the peel read: pair colours, active boxes per colour (the beta of every
+// vertex, or int(alpha) of every vertex box for the uniform box graph),
+// colours per box, active rows and output rows per colour.
+static Err color_tail(Coloring &g, const Cut &cu, DBuf &adj_ptr, DBuf &adj, bool boxes, cudaStream_t st,
+                      DBuf &scan_tmp) {
+    const int nc = cu.nc;
+    const int64_t np = g.n_pairs, nv = g.n_vertices;
+    // DSatur
+    DBuf key, forb, status;
+    HM_TRY(alloc(key, nv * sizeof(unsigned long long)));
+    HM_TRY(alloc(forb, nv * FORB_WORDS * sizeof(unsigned int)));
+    HM_TRY(alloc(status, 2 * sizeof(int)));
+    HM_CUDA(cudaMemsetAsync(status.p, 0, 2 * sizeof(int), st));
+    k_dsatur_init<<<ceil_div(nv, 256), 256, 0, st>>>(nv, g.vertex_degree.as<int>(), key.as<unsigned long long>(),
+                                                      forb.as<unsigned int>()); ::hm::count_launch();
+    k_dsatur<<<1, 1024, 0, st>>>(nv, adj_ptr.as<int64_t>(), adj.as<int>(), key.as<unsigned long long>(),
+                                 forb.as<unsigned int>(), g.vertex_color.as<int>(), status.as<int>()); ::hm::count_launch();
+    HM_LAUNCH("dsatur");
+    int hs[2];
+    HM_CUDA(cudaStreamSynchronize(st));  // DSatur first, then the pageable copy (see to_host)
+    HM_CUDA(cudaMemcpyAsync(hs, status.p, sizeof(hs), cudaMemcpyDeviceToHost, st));
+    HM_CUDA(cudaStreamSynchronize(st));
+    if (hs[1]) return fail(HM_ENOTSUP, "colour: more than 1024 colours");
+    g.n_colors = hs[0];
+    const int chi = g.n_colors;
+    k_pair_color<<<ceil_div(np, 256), 256, 0, st>>>(g.pair_vertex.as<int>(), g.vertex_color.as<int>(), np,
+                                                    g.pair_color.as<int>()); ::hm::count_launch();
+    HM_LAUNCH("pair_color");
+
+    // active tables
+    DBuf act, cnt, off64;
+    HM_TRY(alloc(act, (size_t)chi * nc));
+    HM_CUDA(cudaMemsetAsync(act.p, 0, (size_t)chi * nc, st));
+    if (boxes)
+        k_act_mark_box<<<ceil_div(nv, 256), 256, 0, st>>>(g.pair_alpha.as<int>(), g.vertex_color.as<int>(), nv,
+                                                           cu.int_ptr.as<int>(), cu.int_idx.as<int>(), nc,
+                                                           act.as<unsigned char>());
+    else
+        k_act_mark<<<ceil_div(nv, 256), 256, 0, st>>>(g.vertex_beta.as<int>(), g.vertex_color.as<int>(), nv, nc,
+                                                       act.as<unsigned char>());
+    ::hm::count_launch();
+    HM_TRY(alloc(cnt, std::max(chi, nc) * sizeof(int)));
+    HM_TRY(alloc(off64, (std::max(chi, nc) + 1) * sizeof(int64_t)));
+    k_act_by_color<<<chi, 1024, 0, st>>>(act.as<unsigned char>(), nc, 0, cnt.as<int>(), nullptr, nullptr); ::hm::count_launch();
+    HM_TRY(scan_counts_i32(cnt.as<int>(), off64.as<int64_t>(), chi, st, scan_tmp));
+    std::vector<int64_t> hoff;
+    HM_TRY(to_host(hoff, off64.p, chi + 1, st));
+    const int64_t na = hoff[chi];
+    HM_TRY(alloc(g.act_box, na * sizeof(int)));
+    k_act_by_color<<<chi, 1024, 0, st>>>(act.as<unsigned char>(), nc, 1, nullptr, off64.as<int64_t>(),
+                                         g.act_box.as<int>()); ::hm::count_launch();
+    HM_LAUNCH("act_by_color");
+    {
+        std::vector<int> h32(hoff.begin(), hoff.end());
+        HM_TRY(to_dev(g.act_ptr, h32, st));
+    }
+    k_act_by_entry<<<ceil_div(nc, 128), 128, 0, st>>>(act.as<unsigned char>(), nc, chi, 0, cnt.as<int>(), nullptr,
+                                                      nullptr); ::hm::count_launch();
+    HM_TRY(scan_counts_i32(cnt.as<int>(), off64.as<int64_t>(), nc, st, scan_tmp));
+    {
+        std::vector<int64_t> h;
+        HM_TRY(to_host(h, off64.p, nc + 1, st));
+        HM_TRY(alloc(g.ent_col, std::max<int64_t>(h[nc], 1) * sizeof(int)));
+        k_act_by_entry<<<ceil_div(nc, 128), 128, 0, st>>>(act.as<unsigned char>(), nc, chi, 1, nullptr,
+                                                          off64.as<int64_t>(), g.ent_col.as<int>()); ::hm::count_launch();
+        HM_LAUNCH("act_by_entry");
+        std::vector<int> h32(h.begin(), h.end());
+        HM_TRY(to_dev(g.ent_cptr, h32, st));
+    }
+    // rows of each colour
+    {
+        DBuf sz, rowoff;
+        HM_TRY(alloc(sz, std::max<int64_t>(na, 1) * sizeof(int)));
+        HM_TRY(alloc(rowoff, (na + 1) * sizeof(int64_t)));
+        k_act_sizes<<<ceil_div(na, 256), 256, 0, st>>>(g.act_box.as<int>(), na, cu.ent.as<int>(), sz.as<int>()); ::hm::count_launch();
+        HM_TRY(scan_counts_i32(sz.as<int>(), rowoff.as<int64_t>(), na, st, scan_tmp));
+        std::vector<int64_t> hro;
+        HM_TRY(to_host(hro, rowoff.p, na + 1, st));
+        g.n_act_rows = hro[na];
+        HM_TRY(alloc(g.act_rows, std::max<int64_t>(g.n_act_rows, 1) * sizeof(int)));
+        k_act_rows<<<ceil_div(na * 32, 256), 256, 0, st>>>(g.act_box.as<int>(), na, cu.ent.as<int>(),
+                                                           rowoff.as<int64_t>(), g.act_rows.as<int>()); ::hm::count_launch();
+        HM_LAUNCH("act_rows");
+        std::vector<int64_t> crp(chi + 1);
+        for (int k = 0; k <= chi; ++k) crp[k] = hro[hoff[k]];
+        HM_TRY(to_dev(g.act_rows_ptr, crp, st));
+    }
+    // output rows of each colour (rows of the alpha boxes of its pairs)
+    {
+        DBuf tcnt, tptr, tile_box, sz, rowoff;
+        HM_TRY(alloc(tcnt, chi * sizeof(int)));
+        HM_TRY(alloc(tptr, (chi + 1) * sizeof(int64_t)));
+        HM_TRY(alloc(tile_box, np * sizeof(int)));
+        k_pairs_by_color<<<chi, 1024, 0, st>>>(g.pair_color.as<int>(), g.pair_alpha.as<int>(), np, 0,
+                                               tcnt.as<int>(), nullptr, nullptr); ::hm::count_launch();
+        HM_TRY(scan_counts_i32(tcnt.as<int>(), tptr.as<int64_t>(), chi, st, scan_tmp));
+        k_pairs_by_color<<<chi, 1024, 0, st>>>(g.pair_color.as<int>(), g.pair_alpha.as<int>(), np, 1, nullptr,
+                                               tptr.as<int64_t>(), tile_box.as<int>()); ::hm::count_launch();
+        HM_LAUNCH("pairs_by_color");
+        HM_TRY(alloc(sz, np * sizeof(int)));
+        HM_TRY(alloc(rowoff, (np + 1) * sizeof(int64_t)));
+        k_act_sizes<<<ceil_div(np, 256), 256, 0, st>>>(tile_box.as<int>(), np, cu.ent.as<int>(), sz.as<int>()); ::hm::count_launch();
+        HM_TRY(scan_counts_i32(sz.as<int>(), rowoff.as<int64_t>(), np, st, scan_tmp));
+        HM_TRY(alloc(g.out_rows_ptr, (chi + 1) * sizeof(int64_t)));
+        k_gather_ptr<<<ceil_div(chi + 1, 128), 128, 0, st>>>(rowoff.as<int64_t>(), tptr.as<int64_t>(), chi,
+                                                             g.out_rows_ptr.as<int64_t>()); ::hm::count_launch();
+        HM_TRY(to_host(g.h_out_rows_ptr, g.out_rows_ptr.p, chi + 1, st));
+        HM_TRY(alloc(g.out_rows, std::max<int64_t>(g.h_out_rows_ptr[chi], 1) * sizeof(int)));
+        k_act_rows<<<ceil_div(np * 32, 256), 256, 0, st>>>(tile_box.as<int>(), np, cu.ent.as<int>(),
+                                                           rowoff.as<int64_t>(), g.out_rows.as<int>()); ::hm::count_launch();
+        HM_LAUNCH("out_rows");
+    }
+    return ok();
+}
+
 Err color_cut(hm_ctx *c, int level, bool leaf) { return color_cut(c, level, leaf, c->st, c->scan_tmp); }
 
 // Everything runs on `st`, with `scan_tmp` as the scan scratch, and the call
@@ -484,105 +683,75 @@ Err color_cut(hm_ctx *c, int level, bool leaf, cudaStream_t st, DBuf &scan_tmp) 
                                             adj.as<int>()); ::hm::count_launch();
     HM_LAUNCH("edges fill");
 
-    // DSatur
-    DBuf key, forb, status;
-    HM_TRY(alloc(key, nv * sizeof(unsigned long long)));
-    HM_TRY(alloc(forb, nv * FORB_WORDS * sizeof(unsigned int)));
-    HM_TRY(alloc(status, 2 * sizeof(int)));
-    HM_CUDA(cudaMemsetAsync(status.p, 0, 2 * sizeof(int), st));
-    k_dsatur_init<<<ceil_div(nv, 256), 256, 0, st>>>(nv, g.vertex_degree.as<int>(), key.as<unsigned long long>(),
-                                                      forb.as<unsigned int>()); ::hm::count_launch();
-    k_dsatur<<<1, 1024, 0, st>>>(nv, adj_ptr.as<int64_t>(), adj.as<int>(), key.as<unsigned long long>(),
-                                 forb.as<unsigned int>(), g.vertex_color.as<int>(), status.as<int>()); ::hm::count_launch();
-    HM_LAUNCH("dsatur");
-    int hs[2];
-    HM_CUDA(cudaStreamSynchronize(st));  // DSatur first, then the pageable copy (see to_host)
-    HM_CUDA(cudaMemcpyAsync(hs, status.p, sizeof(hs), cudaMemcpyDeviceToHost, st));
+    HM_TRY(color_tail(g, cu, adj_ptr, adj, false, st, scan_tmp));
     HM_CUDA(cudaStreamSynchronize(st));
-    if (hs[1]) return fail(HM_ENOTSUP, "colour: more than 1024 colours");
-    g.n_colors = hs[0];
-    const int chi = g.n_colors;
-    k_pair_color<<<ceil_div(np, 256), 256, 0, st>>>(g.pair_vertex.as<int>(), g.vertex_color.as<int>(), np,
-                                                    g.pair_color.as<int>()); ::hm::count_launch();
-    HM_LAUNCH("pair_color");
+    g.done = true;
+    return ok();
+}
 
-    // active tables
-    DBuf act, cnt, off64;
-    HM_TRY(alloc(act, (size_t)chi * nc));
-    HM_CUDA(cudaMemsetAsync(act.p, 0, (size_t)chi * nc, st));
-    k_act_mark<<<ceil_div(nv, 256), 256, 0, st>>>(g.vertex_beta.as<int>(), g.vertex_color.as<int>(), nv, nc,
-                                                   act.as<unsigned char>()); ::hm::count_launch();
-    HM_TRY(alloc(cnt, std::max(chi, nc) * sizeof(int)));
-    HM_TRY(alloc(off64, (std::max(chi, nc) + 1) * sizeof(int64_t)));
-    k_act_by_color<<<chi, 1024, 0, st>>>(act.as<unsigned char>(), nc, 0, cnt.as<int>(), nullptr, nullptr); ::hm::count_launch();
-    HM_TRY(scan_counts_i32(cnt.as<int>(), off64.as<int64_t>(), chi, st, scan_tmp));
-    std::vector<int64_t> hoff;
-    HM_TRY(to_host(hoff, off64.p, chi + 1, st));
-    const int64_t na = hoff[chi];
-    HM_TRY(alloc(g.act_box, na * sizeof(int)));
-    k_act_by_color<<<chi, 1024, 0, st>>>(act.as<unsigned char>(), nc, 1, nullptr, off64.as<int64_t>(),
-                                         g.act_box.as<int>()); ::hm::count_launch();
-    HM_LAUNCH("act_by_color");
-    {
-        std::vector<int> h32(hoff.begin(), hoff.end());
-        HM_TRY(to_dev(g.act_ptr, h32, st));
+// Uniform H^1, first sampling stage of cut `level` (Section 4.2): one vertex
+// per box with a non-empty interaction list (cut order); its "pair" is the box
+// itself (pair_alpha = the box), so the sampler, the peel and the QR see the
+// tiles Y(I_alpha, colour of alpha).  Written to c->box_colorings[level].
+Err color_boxes(hm_ctx *c, int level, cudaStream_t st, DBuf &scan_tmp) {
+    if (level < 2 || level > c->L) return fail(HM_EINVAL, "colour boxes: level out of range");
+    const Cut &cu = c->cuts[level];
+    if ((int)c->box_colorings.size() < c->L + 1) return fail(HM_ESTATE, "colour boxes: build the tree first");
+    Coloring &g = c->box_colorings[level];
+    g = Coloring();
+    g.level = level;
+    g.m_cols = c->cfg.r;
+    const int nc = cu.nc;
+    DBuf flag, vscan, vid;
+    HM_TRY(alloc(flag, ((size_t)nc + 1) * sizeof(int64_t)));
+    HM_TRY(alloc(vscan, ((size_t)nc + 1) * sizeof(int64_t)));
+    HM_TRY(alloc(vid, (size_t)std::max(nc, 1) * sizeof(int)));
+    k_box_has_int<<<ceil_div(nc, 128), 128, 0, st>>>(cu.int_ptr.as<int>(), nc, flag.as<int64_t>()); ::hm::count_launch();
+    HM_TRY(scan_exclusive(flag.as<int64_t>(), vscan.as<int64_t>(), nc, st));
+    int64_t nv = 0;
+    HM_TRY(read_scalar(nv, vscan.as<int64_t>() + nc, st));
+    g.n_pairs = g.n_vertices = nv;
+    if (nv == 0) {
+        g.done = true;
+        std::vector<int> z(1, 0);
+        HM_TRY(to_dev(g.act_ptr, z, st));
+        std::vector<int> zc(nc + 1, 0);
+        HM_TRY(to_dev(g.ent_cptr, zc, st));
+        std::vector<int64_t> z64(1, 0);
+        HM_TRY(to_dev(g.act_rows_ptr, z64, st));
+        return ok();
     }
-    k_act_by_entry<<<ceil_div(nc, 128), 128, 0, st>>>(act.as<unsigned char>(), nc, chi, 0, cnt.as<int>(), nullptr,
-                                                      nullptr); ::hm::count_launch();
-    HM_TRY(scan_counts_i32(cnt.as<int>(), off64.as<int64_t>(), nc, st, scan_tmp));
-    {
-        std::vector<int64_t> h;
-        HM_TRY(to_host(h, off64.p, nc + 1, st));
-        HM_TRY(alloc(g.ent_col, std::max<int64_t>(h[nc], 1) * sizeof(int)));
-        k_act_by_entry<<<ceil_div(nc, 128), 128, 0, st>>>(act.as<unsigned char>(), nc, chi, 1, nullptr,
-                                                          off64.as<int64_t>(), g.ent_col.as<int>()); ::hm::count_launch();
-        HM_LAUNCH("act_by_entry");
-        std::vector<int> h32(h.begin(), h.end());
-        HM_TRY(to_dev(g.ent_cptr, h32, st));
-    }
-    // rows of each colour
-    {
-        DBuf sz, rowoff;
-        HM_TRY(alloc(sz, std::max<int64_t>(na, 1) * sizeof(int)));
-        HM_TRY(alloc(rowoff, (na + 1) * sizeof(int64_t)));
-        k_act_sizes<<<ceil_div(na, 256), 256, 0, st>>>(g.act_box.as<int>(), na, cu.ent.as<int>(), sz.as<int>()); ::hm::count_launch();
-        HM_TRY(scan_counts_i32(sz.as<int>(), rowoff.as<int64_t>(), na, st, scan_tmp));
-        std::vector<int64_t> hro;
-        HM_TRY(to_host(hro, rowoff.p, na + 1, st));
-        g.n_act_rows = hro[na];
-        HM_TRY(alloc(g.act_rows, std::max<int64_t>(g.n_act_rows, 1) * sizeof(int)));
-        k_act_rows<<<ceil_div(na * 32, 256), 256, 0, st>>>(g.act_box.as<int>(), na, cu.ent.as<int>(),
-                                                           rowoff.as<int64_t>(), g.act_rows.as<int>()); ::hm::count_launch();
-        HM_LAUNCH("act_rows");
-        std::vector<int64_t> crp(chi + 1);
-        for (int k = 0; k <= chi; ++k) crp[k] = hro[hoff[k]];
-        HM_TRY(to_dev(g.act_rows_ptr, crp, st));
-    }
-    // output rows of each colour (rows of the alpha boxes of its pairs)
-    {
-        DBuf tcnt, tptr, tile_box, sz, rowoff;
-        HM_TRY(alloc(tcnt, chi * sizeof(int)));
-        HM_TRY(alloc(tptr, (chi + 1) * sizeof(int64_t)));
-        HM_TRY(alloc(tile_box, np * sizeof(int)));
-        k_pairs_by_color<<<chi, 1024, 0, st>>>(g.pair_color.as<int>(), g.pair_alpha.as<int>(), np, 0,
-                                               tcnt.as<int>(), nullptr, nullptr); ::hm::count_launch();
-        HM_TRY(scan_counts_i32(tcnt.as<int>(), tptr.as<int64_t>(), chi, st, scan_tmp));
-        k_pairs_by_color<<<chi, 1024, 0, st>>>(g.pair_color.as<int>(), g.pair_alpha.as<int>(), np, 1, nullptr,
-                                               tptr.as<int64_t>(), tile_box.as<int>()); ::hm::count_launch();
-        HM_LAUNCH("pairs_by_color");
-        HM_TRY(alloc(sz, np * sizeof(int)));
-        HM_TRY(alloc(rowoff, (np + 1) * sizeof(int64_t)));
-        k_act_sizes<<<ceil_div(np, 256), 256, 0, st>>>(tile_box.as<int>(), np, cu.ent.as<int>(), sz.as<int>()); ::hm::count_launch();
-        HM_TRY(scan_counts_i32(sz.as<int>(), rowoff.as<int64_t>(), np, st, scan_tmp));
-        HM_TRY(alloc(g.out_rows_ptr, (chi + 1) * sizeof(int64_t)));
-        k_gather_ptr<<<ceil_div(chi + 1, 128), 128, 0, st>>>(rowoff.as<int64_t>(), tptr.as<int64_t>(), chi,
-                                                             g.out_rows_ptr.as<int64_t>()); ::hm::count_launch();
-        HM_TRY(to_host(g.h_out_rows_ptr, g.out_rows_ptr.p, chi + 1, st));
-        HM_TRY(alloc(g.out_rows, std::max<int64_t>(g.h_out_rows_ptr[chi], 1) * sizeof(int)));
-        k_act_rows<<<ceil_div(np * 32, 256), 256, 0, st>>>(tile_box.as<int>(), np, cu.ent.as<int>(),
-                                                           rowoff.as<int64_t>(), g.out_rows.as<int>()); ::hm::count_launch();
-        HM_LAUNCH("out_rows");
-    }
+    if (nv > (int64_t)VID_MASK) return fail(HM_ENOTSUP, "colour boxes: more than 2^20 boxes");
+    HM_TRY(alloc(g.pair_alpha, nv * sizeof(int)));
+    HM_TRY(alloc(g.pair_vertex, nv * sizeof(int)));
+    HM_TRY(alloc(g.pair_color, nv * sizeof(int)));
+    HM_TRY(alloc(g.vertex_pair, nv * sizeof(int)));
+    HM_TRY(alloc(g.vertex_color, nv * sizeof(int)));
+    HM_TRY(alloc(g.vertex_degree, nv * sizeof(int)));
+    k_box_vertices<<<ceil_div(nc, 128), 128, 0, st>>>(cu.int_ptr.as<int>(), nc, vscan.as<int64_t>(),
+                                                      g.pair_alpha.as<int>(), vid.as<int>()); ::hm::count_launch();
+    k_iota<<<ceil_div(nv, 256), 256, 0, st>>>(g.pair_vertex.as<int>(), nv); ::hm::count_launch();
+    k_iota<<<ceil_div(nv, 256), 256, 0, st>>>(g.vertex_pair.as<int>(), nv); ::hm::count_launch();
+    HM_LAUNCH("box vertices");
+    const size_t bm_bytes = (size_t)((nv + 31) / 32) * 4;
+    if (bm_bytes > 200 * 1024) return fail(HM_ENOTSUP, "colour boxes: vertex bitmap exceeds shared memory");
+    HM_CUDA(cudaFuncSetAttribute(k_box_edges, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    DBuf adj_ptr, adj;
+    HM_TRY(alloc(adj_ptr, (nv + 1) * sizeof(int64_t)));
+    k_box_edges<<<(int)nv, 256, bm_bytes, st>>>(nv, g.pair_alpha.as<int>(), vid.as<int>(), cu.near_ptr.as<int>(),
+                                                cu.near_idx.as<int>(), cu.int_ptr.as<int>(), cu.int_idx.as<int>(), 0,
+                                                g.vertex_degree.as<int>(), nullptr, nullptr); ::hm::count_launch();
+    HM_LAUNCH("box edges count");
+    HM_TRY(scan_counts_i32(g.vertex_degree.as<int>(), adj_ptr.as<int64_t>(), nv, st, scan_tmp));
+    int64_t n_adj = 0;
+    HM_TRY(read_scalar(n_adj, adj_ptr.as<int64_t>() + nv, st));
+    g.n_edges = n_adj / 2;
+    HM_TRY(alloc(adj, std::max<int64_t>(n_adj, 1) * sizeof(int)));
+    k_box_edges<<<(int)nv, 256, bm_bytes, st>>>(nv, g.pair_alpha.as<int>(), vid.as<int>(), cu.near_ptr.as<int>(),
+                                                cu.near_idx.as<int>(), cu.int_ptr.as<int>(), cu.int_idx.as<int>(), 1,
+                                                nullptr, adj_ptr.as<int64_t>(), adj.as<int>()); ::hm::count_launch();
+    HM_LAUNCH("box edges fill");
+    HM_TRY(color_tail(g, cu, adj_ptr, adj, true, st, scan_tmp));
     HM_CUDA(cudaStreamSynchronize(st));
     g.done = true;
     return ok();

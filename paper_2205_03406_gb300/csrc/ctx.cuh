@@ -143,12 +143,18 @@ struct hm_ctx {
     std::vector<int> level_off;     // gid offset of each level
 
     std::vector<hm::Coloring> colorings;   // index l (2..L); index L+1 = leaf
+    std::vector<hm::Coloring> box_colorings;  // uniform H^1: box colouring of cut l (index l)
     std::vector<hm::Factors> factors;      // index l
     hm::Leaf leaf;
     std::vector<hm::Samples> kept;         // per level when cfg.keep_samples
     hm::Samples cur;                       // the current level's samples
     hm::DBuf GO, GP;                       // current level's Gaussians [n][r]
     int gauss_level = -100;
+    // uniform H^1: the colouring whose tiles the sampler, the peel and the QR
+    // of the current level work on when it is not the pair colouring (the box
+    // colouring of stage 1), and the sides the peel updates (1 = Y, 2 = Z)
+    const hm::Coloring *cur_tiles = nullptr;
+    int peel_sides = 3;
 
     // scratch
     hm::DBuf scratch_a, scratch_b, scratch_c, scratch_d, scan_tmp;
@@ -180,8 +186,12 @@ Err build_tree(hm_ctx *c, const double *points_dev, int64_t n);
 // color.cu
 Err color_cut(hm_ctx *c, int level, bool leaf);  // on c->st
 Err color_cut(hm_ctx *c, int level, bool leaf, cudaStream_t st, DBuf &scan_tmp);
+Err color_boxes(hm_ctx *c, int level, cudaStream_t st, DBuf &scan_tmp);  // uniform H^1, stage 1
 // sample.cu
 Err make_gaussians(hm_ctx *c, int level);
+// uniform H^1: the Gaussian k_a x r mixes M_a of the boxes vbox[0..nv) (Philox
+// side 3, keyed like G), M_a at moff[v] row-major
+Err make_mix(hm_ctx *c, int level, const int *vbox, int64_t nv, const int *kbox, const int64_t *moff, double *M);
 Err sample_level(hm_ctx *c, const hm_op *op, int level, bool leaf);
 Err op_apply_dense_vectors(hm_ctx *c, const hm_op *op, const double *x_sorted, double *y_sorted,
                            int nrhs, int trans);
@@ -196,7 +206,14 @@ Err peel_level_fp64(hm_ctx *c, int level, bool leaf);   // the same structure in
 Err peel_level_df(hm_ctx *c, int level, bool leaf);     // double-float products (HM_MIXED_BF16X6)
 // basis.cu
 Err bases_and_cores(hm_ctx *c, int level);
+// FP64 column-pivoted QR of tiles base[color[p]][I_box[p]][0:r] in place (the
+// dispatch of bases_and_cores' FP64 modes); k <= tile_cap[p] (nullable) and
+// <= cap; fixed rank when rank > 0, else tolerance tol; ranks into kout
+Err qr_tiles_fp64(hm_ctx *c, int level, const int *tile_box, const int *tile_color, const int *tile_cap, int64_t nt,
+                  int max_rows, double *base, int cap, int rank, double tol, int *kout);
 Err extract_leaf(hm_ctx *c);
+// uniform.cu
+Err uniform_level(hm_ctx *c, const hm_op *op, int level, double *phase_secs);
 // apply.cu
 Err build_apply_plan(hm_ctx *c);
 // y = A~ x (trans 0) or A~^* x for row-major sorted [n][nrhs] vectors; t holds

@@ -127,6 +127,7 @@ hm_status hm_create(hm_ctx **out, const hm_config *cfg, void *stream) {
     if (cfg->precision != HM_FP64 && cfg->precision != HM_MIXED_BF16X6 && cfg->precision != HM_MIXED_BF16X6_F32)
         return HM_EINVAL;
     if (cfg->uniform_depth < 0 || cfg->uniform_depth > QBITS) return HM_EINVAL;
+    if (cfg->format != HM_FORMAT_H1 && cfg->format != HM_FORMAT_UNIFORM_H1) return HM_EINVAL;
     hm_ctx *c = new (std::nothrow) hm_ctx();
     if (!c) return HM_ENOMEM;
     c->cfg = *cfg;
@@ -179,6 +180,8 @@ hm_status hm_tree_build(hm_ctx *c, const double *points_dev, int64_t n, int leaf
     Err e = build_tree(c, points_dev, n);
     if (e) return finish(c, e);
     c->colorings.resize(c->L + 2);
+    c->box_colorings.clear();
+    c->box_colorings.resize(c->L + 1);
     c->factors.resize(c->L + 1);
     c->stage = 1;
     return HM_OK;
@@ -194,6 +197,18 @@ hm_status hm_color(hm_ctx *c, int level, int *n_colors) {
     Err e = color_cut(c, level, leaf);
     if (e) return finish(c, e);
     if (n_colors) *n_colors = c->colorings[leaf ? c->L + 1 : level].n_colors;
+    return HM_OK;
+}
+
+hm_status hm_color_boxes(hm_ctx *c, int level, int *n_colors) {
+    if (!c) return HM_EINVAL;
+    if (c->stage < 1) return bad(c, HM_ESTATE, "color_boxes: build the tree first");
+    if (level < 2 || level > c->L) return bad(c, HM_EINVAL, "color_boxes: level out of range");
+    DeviceScope ds(c->dev);
+    StreamScope ss(c->st);
+    Err e = color_boxes(c, level, c->st, c->scan_tmp);
+    if (e) return finish(c, e);
+    if (n_colors) *n_colors = c->box_colorings[level].n_colors;
     return HM_OK;
 }
 
@@ -290,6 +305,8 @@ private:
             if (!e && stop_) e = fail(HM_ECUDA, "colour: cancelled");
             if (!e && !c_->colorings[idx].done)
                 e = color_cut(c_, leaf ? 0 : idx, leaf, c_->color_st[w], c_->color_scan_tmp[w]);
+            if (!e && !leaf && c_->cfg.format == HM_FORMAT_UNIFORM_H1 && !c_->box_colorings[idx].done)
+                e = color_boxes(c_, idx, c_->color_st[w], c_->color_scan_tmp[w]);
             {
                 std::lock_guard<std::mutex> lk(m_);
                 state_[idx] = e ? 2 : 1;
@@ -354,6 +371,7 @@ static Err compress_all(hm_ctx *c, const hm_op *op) {
     Err err;
     int64_t cols_total = 0;
     double color_wait = 0.0;
+    double phase_uniform[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // uniform levels time their phases themselves
     ColorAhead ahead(c);
     err = ahead.start();
     for (int l = 2; l <= c->L && !err; ++l) {
@@ -362,6 +380,11 @@ static Err compress_all(hm_ctx *c, const hm_op *op) {
         if (g.n_pairs == 0 || g.n_colors == 0) {
             c->factors[l] = Factors();
             c->factors[l].done = true;
+            continue;
+        }
+        if (c->cfg.format == HM_FORMAT_UNIFORM_H1) {  // Section 4.2: two stages per level
+            if ((err = uniform_level(c, op, l, phase_uniform))) break;
+            cols_total += (int64_t)c->box_colorings[l].n_colors * c->cfg.r + (int64_t)g.n_colors * g.m_cols;
             continue;
         }
         PHASE(1, make_gaussians(c, l));
@@ -390,7 +413,7 @@ static Err compress_all(hm_ctx *c, const hm_op *op) {
     if (cur_start) cudaEventDestroy(cur_start);
     cudaError_t ce = cudaStreamSynchronize(c->st);
     if (!err && ce != cudaSuccess) err = fail(HM_ECUDA, std::string("compress: ") + cudaGetErrorString(ce));
-    double phase[8] = {color_wait, 0, 0, 0, 0, 0, 0, 0};
+    double phase[8] = {color_wait, phase_uniform[1], phase_uniform[2], phase_uniform[3], phase_uniform[4], 0, 0, 0};
     for (auto &e : ev) {
         float ms = 0.f;
         if (cudaEventElapsedTime(&ms, e.second.first, e.second.second) == cudaSuccess) phase[e.first] += ms * 1e-3;
@@ -625,6 +648,17 @@ hm_status hm_export(hm_ctx *c, int what, int level, void *host_buf, size_t *byte
         if (what == HM_X_VERTEX_COLOR) parts.push_back({g.vertex_color.p, (size_t)g.n_vertices * sizeof(int)});
         if (what == HM_X_VERTEX_BETA) parts.push_back({g.vertex_beta.p, (size_t)g.n_vertices * sizeof(int)});
         if (what == HM_X_VERTEX_DEGREE) parts.push_back({g.vertex_degree.p, (size_t)g.n_vertices * sizeof(int)});
+        break;
+    }
+    case HM_X_BOX_VERTEX_BOX:
+    case HM_X_BOX_COLOR:
+    case HM_X_BOX_DEGREE: {
+        if (level < 2 || level >= (int)c->box_colorings.size() || !c->box_colorings[level].done)
+            return bad(c, HM_ESTATE, "export: boxes of that level not coloured");
+        const Coloring &g = c->box_colorings[level];
+        const void *src = what == HM_X_BOX_VERTEX_BOX ? g.pair_alpha.p
+                          : (what == HM_X_BOX_COLOR ? g.vertex_color.p : g.vertex_degree.p);
+        parts.push_back({src, (size_t)g.n_vertices * sizeof(int)});
         break;
     }
     case HM_X_GAUSS:

@@ -170,7 +170,7 @@ __global__ void __launch_bounds__(128) k_peel_update(PeelLevel P, int side, cons
 Err peel_level(hm_ctx *c, int level, bool leaf) {
     const int l = leaf ? c->L : level;
     const int idx = leaf ? c->L + 1 : level;
-    const Coloring &g = c->colorings[idx];
+    const Coloring &g = (!leaf && c->cur_tiles) ? *c->cur_tiles : c->colorings[idx];
     if (g.n_pairs == 0 || g.n_colors == 0) return ok();
     const int cols = g.m_cols;
     // up to 64 columns per colour: T = B W once per (coarse pair, colour) and a

@@ -707,7 +707,7 @@ template <typename R> static Err peel_level_t(hm_ctx *c, int level, bool leaf) {
     constexpr bool kDF = std::is_same<R, dfloat>::value;  // compacted records + double-float update
     const int l = leaf ? c->L : level;
     const int idx = leaf ? c->L + 1 : level;
-    const Coloring &g = c->colorings[idx];
+    const Coloring &g = (!leaf && c->cur_tiles) ? *c->cur_tiles : c->colorings[idx];
     if (g.n_pairs == 0 || g.n_colors == 0) return ok();
     const int cols = g.m_cols;
     const int jmax = leaf ? c->L : level - 1;
@@ -764,6 +764,7 @@ template <typename R> static Err peel_level_t(hm_ctx *c, int level, bool leaf) {
     }
 
     for (int side = 0; side < (leaf ? 1 : 2); ++side) {
+        if (!leaf && !(c->peel_sides & (1 << side))) continue;  // uniform H^1 peels one side per stage
         std::vector<pm::CoarseT<R>> tab;
         std::vector<pm::CoarseDF> dtab;
         std::vector<DBuf> keep;  // X, offsets, T, live flags and records of every coarse level

@@ -277,6 +277,24 @@ static Err sample_callback(hm_ctx *c, const hm_op *op, const Coloring &g, bool l
     return ok();
 }
 
+// M_a (k_a x r) of box vertex v: entry (u, j) = gauss(seed, 3, level, gid(a), u, j)
+__global__ void k_mix_gauss(const int *vbox, int64_t nv, const int *kbox, const int64_t *moff, const int *ent,
+                            int level, int r, unsigned long long seed, double *M) {
+    const int64_t v = blockIdx.x;
+    if (v >= nv) return;
+    const int gid = ent[(int64_t)vbox[v] * ENT_FIELDS + 2];
+    for (int o = threadIdx.x; o < kbox[v] * r; o += blockDim.x)
+        M[moff[v] + o] = gauss(seed, 3, level, gid, o / r, o % r);
+}
+
+Err make_mix(hm_ctx *c, int level, const int *vbox, int64_t nv, const int *kbox, const int64_t *moff, double *M) {
+    if (nv == 0) return ok();
+    k_mix_gauss<<<(unsigned)nv, 128, 0, c->st>>>(vbox, nv, kbox, moff, c->cuts[level].ent.as<int>(), level,
+                                                  c->cfg.r, (unsigned long long)c->cfg.seed, M); ::hm::count_launch();
+    HM_LAUNCH("mix_gauss");
+    return ok();
+}
+
 static OpDev make_opdev(const hm_ctx *c, const hm_op *op) {
     OpDev o;
     o.kind = op->kind;
@@ -290,7 +308,7 @@ static OpDev make_opdev(const hm_ctx *c, const hm_op *op) {
 
 Err sample_level(hm_ctx *c, const hm_op *op, int level, bool leaf) {
     const int idx = leaf ? c->L + 1 : level;
-    const Coloring &g = c->colorings[idx];
+    const Coloring &g = (!leaf && c->cur_tiles) ? *c->cur_tiles : c->colorings[idx];
     const int chi = g.n_colors, cols = g.m_cols;
     const int64_t n = c->n;
     Samples &S = c->cur;

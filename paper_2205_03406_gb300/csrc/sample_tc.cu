@@ -685,7 +685,7 @@ bool tc_supported(const hm_ctx *c) {
 Err sample_tc(hm_ctx *c, int level, int kernel) {
     using namespace tc;
     cudaStream_t st = c->st;
-    const Coloring &g = c->colorings[level];
+    const Coloring &g = c->cur_tiles ? *c->cur_tiles : c->colorings[level];
     const int chi = g.n_colors, r = c->cfg.r;
     const int64_t n = c->n;
     HM_TRY(make_xdf(c));  // the pack and main kernels read the double-float points

@@ -10,10 +10,11 @@ def hm():
     return m
 
 
-def settings_for(w: W.Workload, precision: int = 0, keep: bool = True):
+def settings_for(w: W.Workload, precision: int = 0, keep: bool = True, fmt: int = 0):
     m = hm()
     return m.Settings(d=w.d, leaf_size=w.leaf_size, r=w.r, oversample=w.oversample, rank=w.rank, tol=w.tol,
-                      uniform_depth=w.uniform_depth, precision=precision, keep_samples=keep, seed=w.seed)
+                      uniform_depth=w.uniform_depth, precision=precision, keep_samples=keep, seed=w.seed,
+                      format=fmt)
 
 
 def op_for(w: W.Workload, dense_keep: list):
@@ -28,10 +29,10 @@ def op_for(w: W.Workload, dense_keep: list):
     return m.kernel_op(w.kernel)
 
 
-def run_gpu(w: W.Workload, precision: int = 0, keep: bool = True, compress: bool = True):
+def run_gpu(w: W.Workload, precision: int = 0, keep: bool = True, compress: bool = True, fmt: int = 0):
     import torch
     m = hm()
-    comp = m.Compressor(settings_for(w, precision, keep))
+    comp = m.Compressor(settings_for(w, precision, keep, fmt))
     comp.tree_build(torch.from_numpy(w.points).cuda())
     keepalive = []
     op = op_for(w, keepalive)
@@ -79,8 +80,9 @@ def factors(comp, level, rng_a, rng_b):
     ranks = i32(comp.export(m.HM_X_PAIR_RANKS, level)).reshape(-1, 2)
     offs = np.frombuffer(comp.export(m.HM_X_FACTOR_OFFS, level), dtype=np.int64).reshape(-1, 3)
     arena = f64(comp.export(m.HM_X_FACTORS, level))
-    nU = int(offs[-1, 0] + (rng_a[-1][1] - rng_a[-1][0]) * ranks[-1, 0])
-    nV = int(offs[-1, 1] + (rng_b[-1][1] - rng_b[-1][0]) * ranks[-1, 1])
+    # arena lengths: the largest block end (uniform H^1 shares one block among a box's pairs)
+    nU = max(int(offs[p, 0] + (a1 - a0) * ranks[p, 0]) for p, (a0, a1) in enumerate(rng_a))
+    nV = max(int(offs[p, 1] + (b1 - b0) * ranks[p, 1]) for p, (b0, b1) in enumerate(rng_b))
     U_ar, V_ar, B_ar = arena[:nU], arena[nU:nU + nV], arena[nU + nV:]
     out = []
     for p, ((a0, a1), (b0, b1)) in enumerate(zip(rng_a, rng_b)):
