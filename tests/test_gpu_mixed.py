@@ -93,3 +93,91 @@ def test_mixed_compression_matches_oracle(name, precision):
         e = np.linalg.norm(y - yr) / np.linalg.norm(yr)
         assert e <= max(TOL_MIXED, w.tol), (trans, e)
     comp.close()
+
+
+def _level_block_errors(comp, H):
+    """Per level: ranks (GPU, oracle) and the aggregate relative error of the
+    blocks U B V^T, sqrt(sum ||blk - ref||^2 / sum ||ref||^2)."""
+    from gpu_helpers import factors
+    out = {}
+    for l, lf in H.levels.items():
+        if not lf.pairs:
+            continue
+        ranks, fac = factors(comp, l, lf.rng_a, lf.rng_b)
+        ref_ranks = np.array([[u.shape[1], v.shape[1]] for u, v in zip(lf.U, lf.V)])
+        num = den = 0.0
+        for (U, B, V), Ur, Br, Vr in zip(fac, lf.U, lf.B, lf.V):
+            if U.shape[1] == Ur.shape[1] and V.shape[1] == Vr.shape[1]:
+                ref = Ur @ Br @ Vr.T
+                num += np.sum((U @ B @ V.T - ref) ** 2)
+                den += np.sum(ref ** 2)
+        out[l] = (ranks, ref_ranks, np.sqrt(num / max(den, 1e-300)))
+    return out
+
+
+@pytest.mark.parametrize("name", ["grid_log_r40", "cube_exp_r8", "line_tall_r16", "torus_6k"])
+def test_mixed_blocks_match_oracle(name):
+    """Block by block (Algorithm 4.1 per admissible pair) in the spec precision:
+    with a fixed rank the ranks are identical and the blocks U B V^T agree with
+    the oracle's to 1e-5 per level (FP32-class samples, a basis perturbed by
+    the sample error over the spectral gap at k); with a tolerance a rank may
+    move by one where a pivot norm sits within the samples' rounding of the
+    threshold (1.5 % of the pairs at level 3 of the 6k torus; at most 5 %
+    allowed), and the blocks of equal rank agree to the same bound."""
+    w = mixed_workloads()[name]
+    comp, _ = run_gpu(w, precision=MIXED, keep=False)
+    t = ot.build_tree(w.points, w.leaf_size, w.uniform_depth)
+    H = oh1.compress(t, oracle_op(w, t), w.r, rank=w.rank, tol=w.tol, seed=w.seed, oversample=w.oversample)
+    rows = []
+    for l, (ranks, ref_ranks, e) in _level_block_errors(comp, H).items():
+        d = np.abs(ranks - ref_ranks)
+        rows.append((l, int(d.max()), float(np.mean(d > 0)), float(e)))
+    print(name, "level, max rank move, fraction moved, block error:", rows)
+    for l, dmax, frac, e in rows:
+        if w.rank and not w.tol:
+            assert dmax == 0, l
+        else:
+            assert dmax <= 1 and frac <= 0.05, (l, dmax, frac)
+        assert e <= 1e-5, (l, e)
+    comp.close()
+
+
+def deep_1d_workloads():
+    return {
+        "line_log": W.Workload("line_log", W.line1d(8000, 11), W.K_LOG, leaf_size=64, r=16, rank=12, seed=11),
+        "line_exp": W.Workload("line_exp", W.line1d(8000, 11), W.K_EXP, leaf_size=64, r=16, rank=12, seed=11),
+    }
+
+
+# measured: 2.1e-6 (log) and 2.5e-6 (exp) with FP64 solves, 1.0e-5 and 1.3e-5
+# with FP32 solves
+DEEP_1D_BOUND = {MIXED: 5e-6, MIXED_F32: 2e-5}
+
+
+@pytest.mark.parametrize("precision", [MIXED, MIXED_F32], ids=["fp64-solves", "fp32-solves"])
+@pytest.mark.parametrize("name", list(deep_1d_workloads()))
+def test_mixed_deep_1d_non_decaying_kernels(name, precision):
+    """log|x-y| and exp(-|x-y|) on an 8-level 1D tree: the far field does not
+    decay, so the coarser levels' contribution that the peel removes is far
+    larger than the level's own blocks, and the FP32-class rounding of the
+    raw samples (about 1e-7 of the raw sample) is amplified in the peeled
+    tiles.  The stated bound for this case, relative on the applied operator,
+    is 5e-6 in the spec precision (FP64 solves) and 2e-5 with FP32 solves
+    (1e-6 holds for kernels that decay, tested above); the raw samples
+    themselves still meet 1e-6 on the tile rows."""
+    import torch
+    w = deep_1d_workloads()[name]
+    comp, _ = run_gpu(w, precision=precision, keep=False)
+    t = ot.build_tree(w.points, w.leaf_size, w.uniform_depth)
+    assert t.L >= 7
+    H = oh1.compress(t, oracle_op(w, t), w.r, rank=w.rank, tol=w.tol, seed=w.seed, oversample=w.oversample)
+    x = np.random.default_rng(1).standard_normal((w.n, 3))
+    errs = []
+    for trans in (0, 1):
+        y = comp.apply(torch.from_numpy(x).cuda(), trans=trans).cpu().numpy()
+        yr = np.empty_like(x)
+        yr[t.perm] = oh1.apply_h1(H, x[t.perm], transpose=bool(trans))
+        errs.append(np.linalg.norm(y - yr) / np.linalg.norm(yr))
+    print(f"{name} precision {precision}: apply error vs oracle {errs}")
+    assert max(errs) <= DEEP_1D_BOUND[precision], errs
+    comp.close()
