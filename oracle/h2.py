@@ -24,8 +24,14 @@ in three ways, taken here in the paper's order, level by level l = 2..L:
 
 Readings of points where the paper is silent or inconsistent:
   * G_k is printed k x k, but it multiplies the k-column U_tau S_tau and is
-    added to an r-column sample: G is k_tau x r (Philox, side SIDE_AUG_U for U
-    and SIDE_AUG_V for V, level l, keyed by the child box).
+    added to an r-column sample, so it is k_tau x r.  Reading: G = U_tau^T
+    Gamma_tau, with Gamma_tau an |I_tau| x r Philox Gaussian (side SIDE_AUG_U
+    for U and SIDE_AUG_V for V, level l, keyed by the parent box tau).  With
+    orthonormal U_tau this G is exactly a k_tau x r standard Gaussian, and the
+    augmentation U_tau S_tau U_tau^T Gamma_tau does not depend on the signs of
+    the singular vectors or on the basis chosen inside a cluster of equal
+    singular values, so two implementations that differ by rounding draw the
+    same sketch.
   * The nesting step of Algorithm 4.2 is listed for "boxes alpha in level l",
     but eq. nested_basis expresses a box through its children; the text says
     it is done once the children's long bases exist.  Reading: after the
@@ -39,8 +45,10 @@ Readings of points where the paper is silent or inconsistent:
     and <= rank when both are given), k = rank with a fixed rank; always
     k <= |I_alpha| and k <= r.  Each singular vector is signed so that its
     entry of largest magnitude (the first on ties) is positive.
-  * The stage-2 tiles are summed with the same Gaussian mixes M_a as the
-    uniform H^1 oracle (h1.compress_uniform); B_ab = T_ab^T V_beta.
+  * The stage-2 tiles are summed with Gaussian mixes as in the uniform H^1
+    oracle (h1.compress_uniform), for the same reason in the same basis-free
+    form: M_a = U_a^T Gamma'_a, Gamma'_a an |I_a| x r Philox Gaussian (side
+    SIDE_MIX_H2, level l, keyed by the box a).  B_ab = T_ab^T V_beta.
   * The leaf blocks are extracted as in Section 4.1.3, peeling every level.
 
 Storage of the result: long bases of cut L, short bases (transfer matrices) of
@@ -52,10 +60,10 @@ import numpy as np
 
 from . import graph as og
 from . import tree as ot
-from .h1 import (H1Matrix, LevelFactors, SIDE_MIX, SIDE_OMEGA, apply_levels, extract_leaf, gaussians)
+from .h1 import H1Matrix, LevelFactors, SIDE_OMEGA, apply_levels, extract_leaf, gaussians
 from .philox import gaussian_block
 
-SIDE_AUG_U, SIDE_AUG_V = 4, 5
+SIDE_AUG_U, SIDE_AUG_V, SIDE_MIX_H2 = 4, 5, 6
 
 
 def svd_trunc(P: np.ndarray, rank: int, tol: float, cap: int):
@@ -138,6 +146,18 @@ def _expand(tree, l: int, U: dict, short: dict):
     return out
 
 
+def _aug_gauss(tree, l: int, Bprev: dict, side: int, r: int, seed: int):
+    """G_tau = B_tau^T Gamma_tau for every box tau of cut l-1 with a basis
+    (reading in the module docstring)."""
+    out = {}
+    for tau, B in Bprev.items():
+        if B.shape[1] == 0:
+            continue
+        t0, t1 = tree.rng(l - 1, tau)
+        out[tau] = B.T @ gaussian_block(seed, side, l, tree.box(l - 1, tau).gid, t1 - t0, r)
+    return out
+
+
 def compress_h2(tree, op, r: int, rank: int = 0, tol: float = 0.0, seed: int = 0,
                 levels_only: bool = False, oversample: int = 10) -> H2Matrix:
     """Randomized compression of an H^2 matrix (Section 4.3, Algorithm 4.2)."""
@@ -170,6 +190,8 @@ def compress_h2(tree, op, r: int, rank: int = 0, tol: float = 0.0, seed: int = 0
             Y = op.apply(Om) - apply_levels(H, coarse, Om)
             H.matvec_cols += Om.shape[1]
         vcolor = {int(a): int(bcol.color[v]) for v, a in enumerate(bcol.boxes)} if Y is not None else {}
+        aug_u = _aug_gauss(tree, l, Uprev, SIDE_AUG_U, r, seed)
+        aug_v = _aug_gauss(tree, l, Vprev, SIDE_AUG_V, r, seed)
         U, Sin = {}, {}
         for a in range(nc):
             a0, a1 = tree.rng(l, a)
@@ -180,8 +202,7 @@ def compress_h2(tree, op, r: int, rank: int = 0, tol: float = 0.0, seed: int = 0
             tau = tree.cut_parent[l][a]
             if tau in Uprev and Uprev[tau].shape[1] > 0:
                 t0 = tree.rng(l - 1, tau)[0]
-                G = gaussian_block(seed, SIDE_AUG_U, l, tree.box(l, a).gid, Uprev[tau].shape[1], r)
-                P += Uprev[tau][a0 - t0:a1 - t0] @ (Sin_prev[tau][:, None] * G)
+                P += Uprev[tau][a0 - t0:a1 - t0] @ (Sin_prev[tau][:, None] * aug_u[tau])
             if a in vcolor or (tau in Uprev and Uprev[tau].shape[1] > 0):
                 U[a], Sin[a] = svd_trunc(P, rank_fixed, tol, kcap)
         # stage 2: Z = A^* Psi - A^(l-1)* Psi with Psi(I_alpha) = U_alpha on the pair colouring
@@ -204,7 +225,8 @@ def compress_h2(tree, op, r: int, rank: int = 0, tol: float = 0.0, seed: int = 0
                 Tab = Z[b0:b1, ct * kmax:ct * kmax + U[a].shape[1]]
                 T.append(Tab)
                 if a not in mix:
-                    mix[a] = gaussian_block(seed, SIDE_MIX, l, tree.box(l, a).gid, U[a].shape[1], r)
+                    a0, a1 = tree.rng(l, a)
+                    mix[a] = U[a].T @ gaussian_block(seed, SIDE_MIX_H2, l, tree.box(l, a).gid, a1 - a0, r)
                 acc = W.setdefault(b, np.zeros((b1 - b0, r)))
                 acc += Tab @ mix[a]
             lf.coloring = col
@@ -219,8 +241,7 @@ def compress_h2(tree, op, r: int, rank: int = 0, tol: float = 0.0, seed: int = 0
             Wb = W.get(b, np.zeros((b1 - b0, r))).copy()
             if has_parent:
                 t0 = tree.rng(l - 1, tau)[0]
-                G = gaussian_block(seed, SIDE_AUG_V, l, tree.box(l, b).gid, Vprev[tau].shape[1], r)
-                Wb += Vprev[tau][b0 - t0:b1 - t0] @ (Sout_prev[tau][:, None] * G)
+                Wb += Vprev[tau][b0 - t0:b1 - t0] @ (Sout_prev[tau][:, None] * aug_v[tau])
             V[b], Sout[b] = svd_trunc(Wb, rank_fixed, tol, kcap)
         for i, (a, b) in enumerate(pairs):
             lf.U.append(U[a])

@@ -167,3 +167,25 @@ def test_h2_compression_of_a_kernel_matrix():
     e = np.linalg.norm(h2.apply_h2(H, np.eye(w.n)) - A, 2) / np.linalg.norm(A, 2)
     assert e <= 1e-5, e
     assert H.floats() < Hu.floats()
+
+
+def test_result_does_not_depend_on_singular_vector_signs(monkeypatch):
+    """The augmentation and the stage-2 mixes are written through the bases
+    themselves (G = U_tau^T Gamma_tau, M_a = U_a^T Gamma'_a), so flipping the
+    sign of every singular vector leaves the compressed operator unchanged to
+    rounding: rounding-level differences in a basis cannot change a sketch."""
+    w = W.torus_laplace(n=2000, tol=1e-6, r=32)
+    t = ot.build_tree(w.points, 32)
+    op = h1.KernelOp(w.points[t.perm], w.kernel)
+    X = np.random.default_rng(4).standard_normal((w.n, 2))
+    H = h2.compress_h2(t, op, 32, tol=1e-6, seed=w.seed)
+    ref = h2.apply_h2(H, X)
+    base = h2.svd_trunc
+
+    def flipped(P, rank, tol, cap):
+        U, s = base(P, rank, tol, cap)
+        return -U, s
+
+    monkeypatch.setattr(h2, "svd_trunc", flipped)
+    Hf = h2.compress_h2(t, op, 32, tol=1e-6, seed=w.seed)
+    assert np.linalg.norm(h2.apply_h2(Hf, X) - ref) <= 1e-12 * np.linalg.norm(ref)
