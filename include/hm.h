@@ -104,15 +104,16 @@ typedef struct {
     int precision;        /* hm_precision */
     int keep_samples;     /* non-zero: keep every level's peeled samples for hm_export */
     uint64_t seed;        /* Philox4x32-10 key of all test matrices */
-    int format;           /* HM_FORMAT_H1 (per-block bases, Section 4.1) or
+    int format;           /* HM_FORMAT_H1 (per-block bases, Section 4.1),
                              HM_FORMAT_UNIFORM_H1 (one column and one row basis per
-                             box and level, Section 4.2) */
+                             box and level, Section 4.2) or HM_FORMAT_H2 (nested
+                             bases, Section 4.3) */
 } hm_config;
 
 /* Formats of the compressed operator (hm_config.format). */
 enum {
     HM_FORMAT_H1 = 0,          /* Algorithm 4.1: A_ab ~ U_ab B_ab V_ab^T, bases per pair */
-    HM_FORMAT_UNIFORM_H1 = 1   /* Section 4.2: A_ab ~ U_a B_ab V_b^T.  Stage 1 samples every
+    HM_FORMAT_UNIFORM_H1 = 1,  /* Section 4.2: A_ab ~ U_a B_ab V_b^T.  Stage 1 samples every
                                   box's interactions at once (box colouring, Gaussian test
                                   matrices) and keeps the whole r-column sample basis U_a;
                                   stage 2 fills the pair test matrices with the bases,
@@ -120,6 +121,18 @@ enum {
                                   A_ab^* U_a M_a, k) with Gaussian k_a x r mixes M_a,
                                   B_ab = (A_ab^* U_a)^T V_b.  The truncation (rank or tol)
                                   applies to V.  QR and the mixing in FP64 in every mode */
+    HM_FORMAT_H2 = 2           /* Section 4.3, Algorithm 4.2: as HM_FORMAT_UNIFORM_H1, but
+                                  every basis is a truncated SVD of its sample augmented by
+                                  the parent's far field, U_t(I_a) S_t (U_t^T Gamma_t) with
+                                  a Gaussian Gamma_t of the parent's rows (the same on the
+                                  row side), the stage-2 mixes are U_a^T Gamma'_a, and once
+                                  a cut's bases exist the previous cut is nested: its short
+                                  bases U~_t = U_a^T U_t (eq. nested_basis).  The operator
+                                  keeps the long bases of the finest cut, the short bases,
+                                  the cores and the leaf blocks; hm_apply runs the upward
+                                  and downward passes of Algorithm 4.3.  SVD, nesting and
+                                  mixing in FP64 in every mode.  hm_apply_noalloc and
+                                  keep_samples are not supported (HM_ENOTSUP) */
 };
 
 /*
@@ -319,7 +332,11 @@ enum {
     HM_X_BOX_VERTEX_BOX = 17, /* int32[n_box_vertices]: cut entry of every vertex of the
                                  uniform H^1 box graph of cut `level` (hm_color_boxes) */
     HM_X_BOX_COLOR = 18,    /* int32[n_box_vertices]: its colour */
-    HM_X_BOX_DEGREE = 19    /* int32[n_box_vertices]: its degree */
+    HM_X_BOX_DEGREE = 19,   /* int32[n_box_vertices]: its degree */
+    HM_X_H2_RANKS = 20,     /* int32[2][nc] of cut `level` (HM_FORMAT_H2): k of the column
+                               basis of every entry, then of its row basis (0: none) */
+    HM_X_H2_SIGMA = 21      /* double[nc][2][r]: S^in then S^out of every entry (the
+                               first k valid) */
 };
 
 /*

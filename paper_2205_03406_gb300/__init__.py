@@ -21,14 +21,14 @@ HM_OK, HM_EINVAL, HM_ENOMEM, HM_ESTATE, HM_ECUDA, HM_EOP, HM_ETIMEOUT, HM_ENOTSU
 STATUS_NAMES = ["HM_OK", "HM_EINVAL", "HM_ENOMEM", "HM_ESTATE", "HM_ECUDA", "HM_EOP", "HM_ETIMEOUT",
                 "HM_ENOTSUP"]
 HM_FP64, HM_MIXED_BF16X6, HM_MIXED_BF16X6_F32 = 0, 1, 2
-HM_FORMAT_H1, HM_FORMAT_UNIFORM_H1 = 0, 1
+HM_FORMAT_H1, HM_FORMAT_UNIFORM_H1, HM_FORMAT_H2 = 0, 1, 2
 HM_K_LOG, HM_K_LAPLACE3D, HM_K_INVR, HM_K_EXP = 1, 2, 3, 4
 HM_OP_KERNEL, HM_OP_DENSE, HM_OP_CALLBACK = 0, 1, 2
 HM_LEVEL_LEAF = -1
 (HM_X_PERM, HM_X_LEVEL_BOXES, HM_X_CUT, HM_X_NEAR, HM_X_INTER, HM_X_PAIR_VERTEX, HM_X_VERTEX_COLOR,
  HM_X_VERTEX_BETA, HM_X_GAUSS, HM_X_SAMPLE_Y, HM_X_SAMPLE_Z, HM_X_PAIR_RANKS, HM_X_FACTORS,
  HM_X_FACTOR_OFFS, HM_X_LEAF_D, HM_X_VERTEX_DEGREE, HM_X_BOX_VERTEX_BOX, HM_X_BOX_COLOR,
- HM_X_BOX_DEGREE) = range(1, 20)
+ HM_X_BOX_DEGREE, HM_X_H2_RANKS, HM_X_H2_SIGMA) = range(1, 22)
 
 EXPORTED = ["hm_create", "hm_destroy", "hm_tree_build", "hm_color", "hm_sample", "hm_compress", "hm_apply",
             "hm_relerr", "hm_get_info", "hm_export", "hm_last_error", "hm_apply_noalloc", "hm_color_boxes",

@@ -385,41 +385,10 @@ static Err launch_level(const ApplyLevel &a, int max_rows, int64_t np, const int
     return ok();
 }
 
-Err apply_sorted_into(hm_ctx *c, const double *x, double *y, int nrhs, int trans, double *t) {
+Err apply_near(hm_ctx *c, const double *x, double *y, int nrhs, int trans) {
     cudaStream_t st = c->st;
     const ApplyPlan &P = c->plan;
-    if (!P.ready) return fail(HM_ESTATE, "apply: no apply plan (compress first)");
-    const int nb = nrhs >= 4 ? 4 : nrhs;  // right-hand sides per CTA: 1, 2 or 4
-    HM_CUDA(cudaMemsetAsync(y, 0, (size_t)c->n * nrhs * sizeof(double), st));
-    for (int l = 2; l <= c->L; ++l) {
-        if (l >= (int)c->factors.size() || !c->factors[l].done || c->factors[l].n_pairs == 0) continue;
-        const Factors &f = c->factors[l];
-        const Coloring &g = c->colorings[l];
-        const Cut &cu = c->cuts[l];
-        ApplyLevel a;
-        a.ent = cu.ent.as<int>();
-        a.int_ptr = cu.int_ptr.as<int>();
-        a.int_idx = cu.int_idx.as<int>();
-        a.pair_alpha = g.pair_alpha.as<int>();
-        a.pairT = g.pair_T.as<int>();
-        a.kU = f.kU.as<int>();
-        a.kV = f.kV.as<int>();
-        a.offU = f.offU.as<int64_t>();
-        a.offV = f.offV.as<int64_t>();
-        a.offB = f.offB.as<int64_t>();
-        a.U = f.U.as<double>();
-        a.V = f.V.as<double>();
-        a.B = f.B.as<double>();
-        a.toffU = P.toffU[l].as<int64_t>();
-        a.toffV = P.toffV[l].as<int64_t>();
-        if (f.max_k > 64) return fail(HM_ENOTSUP, "apply: rank above 64");
-        const int ld = std::max(1, P.maxk[l]) | 1;
-        switch (nb) {
-        case 1: HM_TRY(launch_level<1>(a, cu.max_rows, f.n_pairs, P.items[l].as<int>(), P.nitems[l], ld, x, nrhs, trans, t, y, st)); break;
-        case 2: HM_TRY(launch_level<2>(a, cu.max_rows, f.n_pairs, P.items[l].as<int>(), P.nitems[l], ld, x, nrhs, trans, t, y, st)); break;
-        default: HM_TRY(launch_level<4>(a, cu.max_rows, f.n_pairs, P.items[l].as<int>(), P.nitems[l], ld, x, nrhs, trans, t, y, st));
-        }
-    }
+    const int nb = nrhs >= 4 ? 4 : nrhs;
     const Cut &cl = c->cuts[c->L];
     const Coloring &gl = c->colorings[c->L + 1];
     if (c->leaf.done && c->leaf.n_pairs > 0 && P.nitems[c->L] > 0) {
@@ -456,8 +425,49 @@ Err apply_sorted_into(hm_ctx *c, const double *x, double *y, int nrhs, int trans
     return ok();
 }
 
+
+Err apply_sorted_into(hm_ctx *c, const double *x, double *y, int nrhs, int trans, double *t) {
+    cudaStream_t st = c->st;
+    const ApplyPlan &P = c->plan;
+    if (!P.ready) return fail(HM_ESTATE, "apply: no apply plan (compress first)");
+    if (c->cfg.format == HM_FORMAT_H2) return apply_h2_into(c, x, y, nrhs, trans, t);
+    const int nb = nrhs >= 4 ? 4 : nrhs;  // right-hand sides per CTA: 1, 2 or 4
+    HM_CUDA(cudaMemsetAsync(y, 0, (size_t)c->n * nrhs * sizeof(double), st));
+    for (int l = 2; l <= c->L; ++l) {
+        if (l >= (int)c->factors.size() || !c->factors[l].done || c->factors[l].n_pairs == 0) continue;
+        const Factors &f = c->factors[l];
+        const Coloring &g = c->colorings[l];
+        const Cut &cu = c->cuts[l];
+        ApplyLevel a;
+        a.ent = cu.ent.as<int>();
+        a.int_ptr = cu.int_ptr.as<int>();
+        a.int_idx = cu.int_idx.as<int>();
+        a.pair_alpha = g.pair_alpha.as<int>();
+        a.pairT = g.pair_T.as<int>();
+        a.kU = f.kU.as<int>();
+        a.kV = f.kV.as<int>();
+        a.offU = f.offU.as<int64_t>();
+        a.offV = f.offV.as<int64_t>();
+        a.offB = f.offB.as<int64_t>();
+        a.U = f.U.as<double>();
+        a.V = f.V.as<double>();
+        a.B = f.B.as<double>();
+        a.toffU = P.toffU[l].as<int64_t>();
+        a.toffV = P.toffV[l].as<int64_t>();
+        if (f.max_k > 64) return fail(HM_ENOTSUP, "apply: rank above 64");
+        const int ld = std::max(1, P.maxk[l]) | 1;
+        switch (nb) {
+        case 1: HM_TRY(launch_level<1>(a, cu.max_rows, f.n_pairs, P.items[l].as<int>(), P.nitems[l], ld, x, nrhs, trans, t, y, st)); break;
+        case 2: HM_TRY(launch_level<2>(a, cu.max_rows, f.n_pairs, P.items[l].as<int>(), P.nitems[l], ld, x, nrhs, trans, t, y, st)); break;
+        default: HM_TRY(launch_level<4>(a, cu.max_rows, f.n_pairs, P.items[l].as<int>(), P.nitems[l], ld, x, nrhs, trans, t, y, st));
+        }
+    }
+    return apply_near(c, x, y, nrhs, trans);
+}
+
 Err apply_sorted(hm_ctx *c, const double *x, double *y, int nrhs, int trans) {
-    HM_TRY(ensure(c->apply_t, (size_t)std::max<int64_t>(c->plan.t_max, 1) * nrhs * sizeof(double)));
+    const int64_t per = c->cfg.format == HM_FORMAT_H2 ? h2_scratch_elems(c) : c->plan.t_max;
+    HM_TRY(ensure(c->apply_t, (size_t)std::max<int64_t>(per, 1) * nrhs * sizeof(double)));
     return apply_sorted_into(c, x, y, nrhs, trans, c->apply_t.as<double>());
 }
 

@@ -90,6 +90,10 @@ extern "C" hm_status hm_apply_noalloc(hm_ctx *c, const double *x_dev, double *y_
         c->last_error = "apply_noalloc: bad vectors";
         return HM_EINVAL;
     }
+    if (c->cfg.format == HM_FORMAT_H2) {
+        c->last_error = "apply_noalloc: not available for HM_FORMAT_H2 (use hm_apply)";
+        return HM_ENOTSUP;
+    }
     hm::DeviceScope ds(c->dev);  // the scratch address and the kernels are those of the context's device
     hm::Err e = hm::apply_noalloc(c, x_dev, y_dev, (int)nrhs, trans ? 1 : 0);
     if (e) {

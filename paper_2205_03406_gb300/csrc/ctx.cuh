@@ -76,6 +76,22 @@ struct Factors {
     DBuf U2, V2, B2;          // double-float copies for the HM_MIXED_BF16X6 peel (made on first use)
     int64_t nU = 0, nV = 0, nB = 0;
     int max_k = 0;
+    // H^2 (Section 4.3): the bases are per cut entry (a box of cut l), U and V
+    // hold them at eoffU / eoffV (|I_e| x k_e row-major; the pairs' offU / offV
+    // point at them); eS holds S^in and S^out ([nc][2][r], the first k valid);
+    // Ut / Vt hold the short bases of this cut's entries in terms of their
+    // children in cut l + 1: the block of child a (k_a x k_parent, row-major)
+    // at offUt[a] / offVt[a], indexed by the child entry
+    bool has_bases = false;
+    int nc = 0;
+    DBuf ekU, ekV;            // int32 [nc]
+    DBuf eoffU, eoffV;        // int64 [nc + 1]
+    DBuf eS;                  // double [nc][2][r]
+    DBuf Ut, Vt;
+    DBuf offUt, offVt;        // int64 [nc of cut l + 1, + 1]
+    int64_t nUt = 0, nVt = 0;
+    int64_t sumkU = 0, sumkV = 0;  // sum of ekU / ekV over the entries
+    DBuf epU, epV;            // int64 [nc + 1]: prefix sums of ekU / ekV (apply expansions)
 };
 
 struct Leaf {
@@ -214,6 +230,22 @@ Err qr_tiles_fp64(hm_ctx *c, int level, const int *tile_box, const int *tile_col
 Err extract_leaf(hm_ctx *c);
 // uniform.cu
 Err uniform_level(hm_ctx *c, const hm_op *op, int level, double *phase_secs);
+// per-pair tables of a level whose bases are stored per box (uniform H^1, H^2):
+// pair p = (a, b) takes k_U, offset of box vid[a] and k_V, offset of box
+// vid[b]; then B_p = T^T V_b from the stage-2 tiles T = Z(I_b, 0:k_a)
+Err box_pairs_and_cores(hm_ctx *c, int level, const int *vid, const int *kUb, const int *kVb,
+                        const int64_t *offUb, const int64_t *offVb);
+// W(I_b, :) = sum over the entries t of int(b) of Z[colour of pair t](I_b, 0:k_a) M_a
+// (a = int_idx[t], looked up through vid) for the boxes vbox[0..nv); W is [n][r]
+Err mix_sum(hm_ctx *c, int level, const int *vbox, int64_t nv, const int *vid, const int *kU, const int64_t *moff,
+            const double *M, double *W);
+// h2.cu
+Err h2_level(hm_ctx *c, const hm_op *op, int level, double *phase_secs);
+Err h2_finish(hm_ctx *c);  // after the leaf: keep the long bases of cut L and the short bases
+Err apply_h2_into(hm_ctx *c, const double *x_sorted, double *y_sorted, int nrhs, int trans, double *t);
+int64_t h2_scratch_elems(const hm_ctx *c);  // t of apply_h2_into, per right-hand side
+// apply.cu: the leaf neighbour blocks, y += D x (or D^* x), on c->st
+Err apply_near(hm_ctx *c, const double *x_sorted, double *y_sorted, int nrhs, int trans);
 // apply.cu
 Err build_apply_plan(hm_ctx *c);
 // y = A~ x (trans 0) or A~^* x for row-major sorted [n][nrhs] vectors; t holds

@@ -1,6 +1,7 @@
 // C ABI of include/hm.h: argument checks, call-order state machine, the
 // level loop of Algorithm 4.1, apply, the Section 5 error estimate and exports.
 #include "ctx.cuh"
+#include "philox.cuh"
 
 #include <algorithm>
 #include <chrono>
@@ -54,22 +55,7 @@ __global__ void k_start_vector(int64_t n, unsigned long long seed, double *x) {
     // Philox Gaussian start vector, counter (0, i, 0, 2 << 8), duplicated in both columns
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const unsigned int M0 = 0xD2511F53u, M1 = 0xCD9E8D57u, W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
-    uint4 c = make_uint4(0u, (unsigned)i, 0u, 2u << 8);
-    uint2 k = make_uint2((unsigned)(seed & 0xffffffffu), (unsigned)(seed >> 32));
-    for (int r = 0; r < 10; ++r) {
-        if (r) {
-            k.x += W0;
-            k.y += W1;
-        }
-        const unsigned int hi0 = __umulhi(M0, c.x), lo0 = M0 * c.x;
-        const unsigned int hi1 = __umulhi(M1, c.z), lo1 = M1 * c.z;
-        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
-    }
-    const unsigned long long a = ((unsigned long long)c.y << 32) | c.x, b = ((unsigned long long)c.w << 32) | c.z;
-    const double u1 = __dmul_rn(__dadd_rn((double)(a >> 12), 0.5), 0x1.0p-52);
-    const double u2 = __dmul_rn(__dadd_rn((double)(b >> 12), 0.5), 0x1.0p-52);
-    const double z = __dmul_rn(sqrt(__dmul_rn(-2.0, log(u1))), cos(__dmul_rn(2.0 * M_PI, u2)));
+    const double z = gauss(seed, 2, 0, 0, (int)i, 0);
     x[i * 2] = z;
     x[i * 2 + 1] = z;
 }
@@ -127,7 +113,9 @@ hm_status hm_create(hm_ctx **out, const hm_config *cfg, void *stream) {
     if (cfg->precision != HM_FP64 && cfg->precision != HM_MIXED_BF16X6 && cfg->precision != HM_MIXED_BF16X6_F32)
         return HM_EINVAL;
     if (cfg->uniform_depth < 0 || cfg->uniform_depth > QBITS) return HM_EINVAL;
-    if (cfg->format != HM_FORMAT_H1 && cfg->format != HM_FORMAT_UNIFORM_H1) return HM_EINVAL;
+    if (cfg->format != HM_FORMAT_H1 && cfg->format != HM_FORMAT_UNIFORM_H1 && cfg->format != HM_FORMAT_H2)
+        return HM_EINVAL;
+    if (cfg->format == HM_FORMAT_H2 && cfg->keep_samples) return HM_ENOTSUP;
     hm_ctx *c = new (std::nothrow) hm_ctx();
     if (!c) return HM_ENOMEM;
     c->cfg = *cfg;
@@ -305,7 +293,7 @@ private:
             if (!e && stop_) e = fail(HM_ECUDA, "colour: cancelled");
             if (!e && !c_->colorings[idx].done)
                 e = color_cut(c_, leaf ? 0 : idx, leaf, c_->color_st[w], c_->color_scan_tmp[w]);
-            if (!e && !leaf && c_->cfg.format == HM_FORMAT_UNIFORM_H1 && !c_->box_colorings[idx].done)
+            if (!e && !leaf && c_->cfg.format != HM_FORMAT_H1 && !c_->box_colorings[idx].done)
                 e = color_boxes(c_, idx, c_->color_st[w], c_->color_scan_tmp[w]);
             {
                 std::lock_guard<std::mutex> lk(m_);
@@ -377,6 +365,12 @@ static Err compress_all(hm_ctx *c, const hm_op *op) {
     for (int l = 2; l <= c->L && !err; ++l) {
         if ((err = ahead.wait(l, &color_wait))) break;
         const Coloring &g = c->colorings[l];
+        if (c->cfg.format == HM_FORMAT_H2) {  // Section 4.3: every cut, also one without pairs (its far field)
+            if ((err = h2_level(c, op, l, phase_uniform))) break;
+            if (g.n_pairs > 0 && g.n_colors > 0)
+                cols_total += (int64_t)c->box_colorings[l].n_colors * c->cfg.r + (int64_t)g.n_colors * g.m_cols;
+            continue;
+        }
         if (g.n_pairs == 0 || g.n_colors == 0) {
             c->factors[l] = Factors();
             c->factors[l].done = true;
@@ -408,6 +402,7 @@ static Err compress_all(hm_ctx *c, const hm_op *op) {
             if (!err) PHASE(6, extract_leaf(c));
         }
     }
+    if (!err && c->cfg.format == HM_FORMAT_H2) err = h2_finish(c);
     if (!err) err = build_apply_plan(c);
 #undef PHASE
     if (cur_start) cudaEventDestroy(cur_start);
@@ -457,7 +452,7 @@ static Err compress_all(hm_ctx *c, const hm_op *op) {
         in.pairs[l] = c->colorings[l].n_pairs;
         in.vertices[l] = c->colorings[l].n_vertices;
         const Factors &f = c->factors[l];
-        floats += f.nU + f.nV + f.nB;
+        floats += f.nU + f.nV + f.nB + f.nUt + f.nVt;
         in.max_rank = std::max(in.max_rank, f.max_k);
     }
     if (c->L + 1 < 32) {
@@ -659,6 +654,20 @@ hm_status hm_export(hm_ctx *c, int what, int level, void *host_buf, size_t *byte
         const void *src = what == HM_X_BOX_VERTEX_BOX ? g.pair_alpha.p
                           : (what == HM_X_BOX_COLOR ? g.vertex_color.p : g.vertex_degree.p);
         parts.push_back({src, (size_t)g.n_vertices * sizeof(int)});
+        break;
+    }
+    case HM_X_H2_RANKS:
+    case HM_X_H2_SIGMA: {
+        if (c->cfg.format != HM_FORMAT_H2 || c->stage < 2 || level < 2 || level > c->L ||
+            !c->factors[level].has_bases)
+            return bad(c, HM_ESTATE, "export: no H^2 bases at that level");
+        const Factors &f = c->factors[level];
+        if (what == HM_X_H2_RANKS) {
+            parts.push_back({f.ekU.p, (size_t)f.nc * sizeof(int)});
+            parts.push_back({f.ekV.p, (size_t)f.nc * sizeof(int)});
+        } else {
+            parts.push_back({f.eS.p, (size_t)f.nc * 2 * c->cfg.r * sizeof(double)});
+        }
         break;
     }
     case HM_X_GAUSS:

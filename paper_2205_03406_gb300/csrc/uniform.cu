@@ -272,7 +272,32 @@ Err uniform_level(hm_ctx *c, const hm_op *op, int l, double *phase_secs) {
     k_pack_box<<<(unsigned)nv, 128, 0, st>>>(gb.pair_alpha.as<int>(), nullptr, cu.ent.as<int>(), n, r, kVb.as<int>(),
                                             offVb.as<int64_t>(), W, f.V.as<double>(), nullptr); ::hm::count_launch();
     HM_LAUNCH("pack V");
-    // per-pair tables and cores
+    HM_TRY(box_pairs_and_cores(c, l, vid.as<int>(), kUb.as<int>(), kVb.as<int>(), offUb.as<int64_t>(),
+                               offVb.as<int64_t>()));
+    f.done = true;
+    return ok();
+}
+
+Err mix_sum(hm_ctx *c, int l, const int *vbox, int64_t nv, const int *vid, const int *kU, const int64_t *moff,
+            const double *M, double *W) {
+    if (nv == 0) return ok();
+    const Cut &cu = c->cuts[l];
+    un::k_mix_sum<<<(unsigned)nv, 128, 0, c->st>>>(vbox, nv, cu.ent.as<int>(), cu.int_ptr.as<int>(),
+                                                   cu.int_idx.as<int>(), c->colorings[l].pair_color.as<int>(), vid,
+                                                   kU, moff, M, c->cur.Z.as<double>(), c->n, c->cfg.r, W); ::hm::count_launch();
+    HM_LAUNCH("mix sum");
+    return ok();
+}
+
+Err box_pairs_and_cores(hm_ctx *c, int l, const int *vid, const int *kUb, const int *kVb, const int64_t *offUb,
+                        const int64_t *offVb) {
+    using namespace un;
+    cudaStream_t st = c->st;
+    const Coloring &gp = c->colorings[l];
+    const Cut &cu = c->cuts[l];
+    Factors &f = c->factors[l];
+    const int64_t np = gp.n_pairs, n = c->n;
+    const int r = c->cfg.r;
     HM_TRY(alloc(f.kU, np * sizeof(int)));
     HM_TRY(alloc(f.kV, np * sizeof(int)));
     HM_TRY(alloc(f.offU, (np + 1) * sizeof(int64_t)));
@@ -280,11 +305,11 @@ Err uniform_level(hm_ctx *c, const hm_op *op, int l, double *phase_secs) {
     HM_TRY(alloc(f.offB, (np + 1) * sizeof(int64_t)));
     DBuf szB;
     HM_TRY(alloc(szB, (np + 1) * sizeof(int64_t)));
-    k_pair_factors<<<ceil_div(np, 256), 256, 0, st>>>(gp.pair_alpha.as<int>(), cu.int_idx.as<int>(), np, vid.as<int>(),
-                                                      kUb.as<int>(), kVb.as<int>(), offUb.as<int64_t>(),
-                                                      offVb.as<int64_t>(), f.kU.as<int>(), f.kV.as<int>(),
+    k_pair_factors<<<ceil_div(np, 256), 256, 0, st>>>(gp.pair_alpha.as<int>(), cu.int_idx.as<int>(), np, vid, kUb, kVb,
+                                                      offUb, offVb, f.kU.as<int>(), f.kV.as<int>(),
                                                       f.offU.as<int64_t>(), f.offV.as<int64_t>(),
                                                       szB.as<int64_t>()); ::hm::count_launch();
+    HM_LAUNCH("pair factors");
     HM_TRY(scan_exclusive(szB.as<int64_t>(), f.offB.as<int64_t>(), np, st));
     HM_TRY(read_scalar(f.nB, f.offB.as<int64_t>() + np, st));
     HM_TRY(alloc(f.B, std::max<int64_t>(f.nB, 1) * sizeof(double)));
@@ -296,11 +321,10 @@ Err uniform_level(hm_ctx *c, const hm_op *op, int l, double *phase_secs) {
     HM_LAUNCH("core uniform");
     std::vector<int> hk;
     f.max_k = 0;
-    HM_TRY(to_host(hk, kUb.p, nv, st));
+    HM_TRY(to_host(hk, f.kU.p, np, st));
     for (int v : hk) f.max_k = std::max(f.max_k, v);
-    HM_TRY(to_host(hk, kVb.p, nv, st));
+    HM_TRY(to_host(hk, f.kV.p, np, st));
     for (int v : hk) f.max_k = std::max(f.max_k, v);
-    f.done = true;
     return ok();
 }
 

@@ -50,6 +50,21 @@ def test_binding_struct_layouts_match_header(tmp_path):
     assert got == want
 
 
+def test_binding_constants_match_header(tmp_path):
+    """Formats and export selectors of the binding equal the header's."""
+    import subprocess
+    import paper_2205_03406_gb300 as hm
+    names = ["HM_FORMAT_H1", "HM_FORMAT_UNIFORM_H1", "HM_FORMAT_H2", "HM_X_LEAF_D", "HM_X_BOX_DEGREE",
+             "HM_X_H2_RANKS", "HM_X_H2_SIGMA", "HM_MIXED_BF16X6", "HM_MIXED_BF16X6_F32"]
+    src = tmp_path / "consts.c"
+    src.write_text('#include <stdio.h>\n#include "hm.h"\nint main(void){'
+                   + "".join(f'printf("%d\\n", (int){n});' for n in names) + 'return 0;}\n')
+    exe = tmp_path / "consts"
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    got = [int(v) for v in subprocess.check_output([str(exe)]).split()]
+    assert got == [getattr(hm, n) for n in names]
+
+
 def test_create_rejects_bad_configs_without_gpu():
     """Argument checks happen before any CUDA work."""
     import paper_2205_03406_gb300 as hm
@@ -61,6 +76,12 @@ def test_create_rejects_bad_configs_without_gpu():
         with pytest.raises(hm.HMError) as ei:
             hm.hm_create(s.to_c())
         assert ei.value.status == hm.HM_EINVAL
+    with pytest.raises(hm.HMError) as ei:  # an H^2 operator keeps no per-level samples
+        hm.hm_create(hm.Settings(d=3, rank=4, format=hm.HM_FORMAT_H2, keep_samples=True).to_c())
+    assert ei.value.status == hm.HM_ENOTSUP
+    with pytest.raises(hm.HMError) as ei:
+        hm.hm_create(hm.Settings(d=3, rank=4, format=3).to_c())
+    assert ei.value.status == hm.HM_EINVAL
     assert hm.hm_destroy(None) == hm.HM_OK
 
 
