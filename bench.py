@@ -69,6 +69,8 @@ def parse():
                     help="only measure cuBLAS DGEMM and SGEMM (no TF32) rates on this GPU and print them")
     ap.add_argument("--no-modes", action="store_true",
                     help="skip timing the other two precision modes beside the main line")
+    ap.add_argument("--no-formats", action="store_true",
+                    help="skip timing the uniform H^1 and H^2 formats of the same job")
     ap.add_argument("--relerr-iters", type=int, default=20)
     ap.add_argument("--no-relerr", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -259,12 +261,12 @@ def rank_seed(base: int, rank: int) -> int:
     return base + rank
 
 
-def time_mode(hm, w, pts, op, precision: int, rank: int, steps: int, relerr_iters):
-    """Time-to-compress (CUDA events, after one warm-up job) and relative error
-    of the same job in another precision mode."""
+def time_mode(hm, w, pts, op, precision: int, rank: int, steps: int, relerr_iters, fmt: int = 0):
+    """Time-to-compress (CUDA events, after one warm-up job), relative error and
+    storage of the same job in another precision mode or format."""
     import torch
     s = hm.Settings(d=3, leaf_size=w.leaf_size, r=w.r, oversample=w.oversample, tol=w.tol, precision=precision,
-                    seed=rank_seed(w.seed, rank))
+                    seed=rank_seed(w.seed, rank), format=fmt)
     comp = hm.Compressor(s, torch.cuda.current_stream())
     comp.tree_build(pts)
     comp.compress(op)
@@ -278,9 +280,12 @@ def time_mode(hm, w, pts, op, precision: int, rank: int, steps: int, relerr_iter
     e1.record(stream)
     torch.cuda.synchronize()
     t = e0.elapsed_time(e1) / 1e3 / steps
+    info = comp.info()
     out = {"time_to_compress_s": round(t, 4), "steps": steps,
            "rel_error": None if relerr_iters is None else comp.relerr(op, relerr_iters),
-           "phases_s": {n: round(comp.info().seconds_phase[i], 4) for i, n in enumerate(hm.PHASES)}}
+           "floats_per_dof": round(info.factor_floats / w.n, 1), "max_rank": info.max_rank,
+           "matvec_cols": info.matvec_cols,
+           "phases_s": {n: round(info.seconds_phase[i], 4) for i, n in enumerate(hm.PHASES)}}
     comp.close()
     return out
 
@@ -491,6 +496,15 @@ def run_ours(args):
                                     relerr_iters=None if args.no_relerr else args.relerr_iters)
             modes[name]["precision"] = desc
 
+    # the same job compressed to the uniform H^1 (Section 4.2) and H^2 (Section
+    # 4.3) formats in the bench's precision mode
+    formats = None
+    if rank == 0 and world == 1 and not args.no_formats:
+        formats = {}
+        for name, fv in (("uniform_h1", hm.HM_FORMAT_UNIFORM_H1), ("h2", hm.HM_FORMAT_H2)):
+            formats[name] = time_mode(hm, w, pts, op, PRECISIONS[args.precision][0], rank, steps=3,
+                                      relerr_iters=None if args.no_relerr else args.relerr_iters, fmt=fv)
+
     if rank != 0:
         comp.close()
         if dist is not None:
@@ -524,6 +538,7 @@ def run_ours(args):
         "roofline": roof_main, "roofline_second": roof_second, "apply": apply_line,
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk, "serving": serving,
         "modes": modes,
+        "formats": formats,
     }
     print(json.dumps(out), flush=True)
     comp.close()
