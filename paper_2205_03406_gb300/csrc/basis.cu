@@ -18,6 +18,7 @@
 //       solves in shared memory (one warp per pair).
 //  K11  D_{alpha,beta} = Y_leaf(I_alpha, c m_max + [0, |I_beta|)).
 #include "ctx.cuh"
+#include "df.cuh"
 
 #include <algorithm>
 
@@ -31,8 +32,11 @@ namespace hm {
 // packed factor at offF[p] with kf = kdim[p] columns.  A chunk beyond the box
 // writes zeros; the consumer adds the chunks in order.  T is the type of the
 // products and of the sums over 32-row blocks, TA that of the sums over the
-// blocks and of the output (double and double, or float and float in the
-// HM_MIXED_BF16X6_F32 mode, whose P, U and V carry FP32-class rounding already).
+// blocks and of the output: double-float and double in the HM_MIXED_BF16X6
+// mode (products of about 48 bits on the FP32 pipe, 2^-44 relative per
+// product: FP64-class for samples with FP32-class rounding, and five times
+// the throughput of GB300's FP64 pipe), float and float in the
+// HM_MIXED_BF16X6_F32 mode, double and double in FP64.
 constexpr int GRAM_CHUNK = 1024;
 
 template <typename T, typename TA>
@@ -60,11 +64,11 @@ __global__ void __launch_bounds__(256) k_gram(const int *box, const int *ent, in
         const int mm = min(32, i_end - i0);
         for (int o = threadIdx.x; o < 32 * r; o += 256) {
             const int i = o / r, j = o % r;
-            gs[i][j] = (i < mm) ? (T)G[(int64_t)(s0 + i0 + i) * r + j] : T(0);
+            gs[i][j] = (i < mm) ? from_f64<T>(G[(int64_t)(s0 + i0 + i) * r + j]) : T(0);
         }
         for (int o = threadIdx.x; o < 32 * kf; o += 256) {
             const int i = o / kf, j = o % kf;
-            fs[i][j] = (i < mm) ? (T)Fp[(int64_t)(i0 + i) * kf + j] : T(0);
+            fs[i][j] = (i < mm) ? from_f64<T>(Fp[(int64_t)(i0 + i) * kf + j]) : T(0);
         }
         __syncthreads();
 #pragma unroll
@@ -73,8 +77,8 @@ __global__ void __launch_bounds__(256) k_gram(const int *box, const int *ent, in
             if (o < r * kf) {
                 const int a = o / kf, b = o % kf;
                 T sacc = T(0);  // the 32-row block in T, added to the TA sum
-                for (int i = 0; i < mm; ++i) sacc = fma(gs[i][a], fs[i][b], sacc);
-                acc[q] += (TA)sacc;
+                for (int i = 0; i < mm; ++i) sacc = mac(gs[i][a], fs[i][b], sacc);
+                acc[q] += widen(sacc, TA(0));
             }
         }
         __syncthreads();
@@ -96,8 +100,12 @@ __global__ void __launch_bounds__(256) k_qr_tiles(const int *tile_alpha, const i
                                                   const int *ent, int64_t n, int r, int cap, int rank, double tol,
                                                   double *Ybase, int *kout, int min_rows,
                                                   const int *tile_cap = nullptr) {
+    // thread (w, lane) owns columns lane and lane + 32 on the rows w, w + 8, ...:
+    // every pass reads whole 256-byte rows.  One FMA per element and step in
+    // the update, which also sums the squares of the updated trailing columns:
+    // the exact norms of the next step, without a separate pass.
     __shared__ double red[8][64];
-    __shared__ double nrm[64], tau[64], beta[64];
+    __shared__ double nrm[64], wv[64], tau[64], beta[64];
     __shared__ int sh_piv, sh_stop;
     __shared__ double sh_scale, sh_n0;
     const int64_t p = blockIdx.x;
@@ -105,31 +113,31 @@ __global__ void __launch_bounds__(256) k_qr_tiles(const int *tile_alpha, const i
     const int m = e[4] - e[3];
     if (m <= min_rows) return;  // a warp or shared-memory kernel factors this tile
     double *A = Ybase + ((int64_t)tile_color[p] * n + e[3]) * r;
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const int *eb = ent + (int64_t)tile_beta[p] * ENT_FIELDS;
     // the block A(I_alpha, I_beta) has rank <= min(|I_alpha|, |I_beta|)
     const int kmax = min(min(min(m, eb[4] - eb[3]), min(r, cap)), tile_cap ? tile_cap[p] : r);
+    // norms of step 0
+    for (int h = 0; h < 2; ++h) {
+        const int j = lane + 32 * h;
+        double acc = 0.0;
+        if (j < r)
+            for (int i = w; i < m; i += 8) acc = fma(A[(int64_t)i * r + j], A[(int64_t)i * r + j], acc);
+        red[w][j] = acc;
+    }
+    __syncthreads();
+    if (tid < r) {
+        double t = 0.0;
+        for (int u = 0; u < 8; ++u) t += red[u][tid];
+        nrm[tid] = t;
+    }
+    __syncthreads();
     int k = 0;
     for (int s = 0; s < kmax; ++s) {
-        // exact norms of the trailing columns
-        for (int h = 0; h < 2; ++h) {
-            const int j = lane + 32 * h;
-            double acc = 0.0;
-            if (j >= s && j < r)
-                for (int i = s + w; i < m; i += 8) acc = fma(A[(int64_t)i * r + j], A[(int64_t)i * r + j], acc);
-            red[w][j] = acc;
-        }
-        __syncthreads();
-        if (threadIdx.x < r) {
-            double t = 0.0;
-            for (int u = 0; u < 8; ++u) t += red[u][threadIdx.x];
-            nrm[threadIdx.x] = t;
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
+        if (tid == 0) {
             int piv = s;
             for (int j = s + 1; j < r; ++j)
-                if (nrm[j] > nrm[piv]) piv = j;
+                if (nrm[j] > nrm[piv]) piv = j;  // largest norm, lowest column on ties
             const double nv = sqrt(nrm[piv]);
             if (s == 0) sh_n0 = nv;
             int stop = 0;
@@ -137,20 +145,23 @@ __global__ void __launch_bounds__(256) k_qr_tiles(const int *tile_alpha, const i
             else stop = !(sh_n0 > 0.0) || !(nv > tol * sh_n0);
             sh_piv = piv;
             sh_stop = stop;
+            if (!stop && piv != s) {  // the norms move with their columns
+                const double t = nrm[s];
+                nrm[s] = nrm[piv];
+                nrm[piv] = t;
+            }
         }
         __syncthreads();
         if (sh_stop) break;
         const int piv = sh_piv;
-        if (piv != s) {
-            for (int i = threadIdx.x; i < m; i += blockDim.x) {
+        if (piv != s)
+            for (int i = tid; i < m; i += blockDim.x) {
                 const double a = A[(int64_t)i * r + s];
                 A[(int64_t)i * r + s] = A[(int64_t)i * r + piv];
                 A[(int64_t)i * r + piv] = a;
             }
-            if (threadIdx.x == 0) nrm[s] = nrm[piv];
-        }
         __syncthreads();
-        if (threadIdx.x == 0) {
+        if (tid == 0) {
             const double x0 = A[(int64_t)s * r + s];
             const double nx = sqrt(nrm[s]);
             if (nx == 0.0) {
@@ -167,9 +178,9 @@ __global__ void __launch_bounds__(256) k_qr_tiles(const int *tile_alpha, const i
         }
         __syncthreads();
         const double sc = sh_scale, ts = tau[s];
-        for (int i = s + 1 + threadIdx.x; i < m; i += blockDim.x) A[(int64_t)i * r + s] *= sc;
+        for (int i = s + 1 + tid; i < m; i += blockDim.x) A[(int64_t)i * r + s] *= sc;
         __syncthreads();
-        // apply H = I - tau v v^T (v = [1; A(s+1:m, s)]) to columns s+1..r-1
+        // H = I - tau v v^T, v = [1; A(s+1:m, s)]: w_j = A(s, j) + v(s+1:)^T A(s+1:, j)
         for (int h = 0; h < 2; ++h) {
             const int j = lane + 32 * h;
             double acc = 0.0;
@@ -178,17 +189,32 @@ __global__ void __launch_bounds__(256) k_qr_tiles(const int *tile_alpha, const i
             red[w][j] = acc;
         }
         __syncthreads();
-        if (threadIdx.x < r && threadIdx.x > s) {
-            double t = A[(int64_t)s * r + threadIdx.x];
-            for (int u = 0; u < 8; ++u) t += red[u][threadIdx.x];
-            nrm[threadIdx.x] = t;  // reuse as w_j
+        if (tid > s && tid < r) {
+            double t = A[(int64_t)s * r + tid];
+            for (int u = 0; u < 8; ++u) t += red[u][tid];
+            const double tw = ts * t;
+            wv[tid] = tw;
+            A[(int64_t)s * r + tid] -= tw;
         }
         __syncthreads();
-        for (int o = threadIdx.x; o < m * r; o += blockDim.x) {
-            const int i = o / r, j = o % r;
-            if (j <= s || i < s) continue;
-            const double vi = (i == s) ? 1.0 : A[(int64_t)i * r + s];
-            A[(int64_t)i * r + j] -= ts * vi * nrm[j];
+        for (int h = 0; h < 2; ++h) {
+            const int j = lane + 32 * h;
+            double acc = 0.0;
+            if (j > s && j < r) {
+                const double tw = wv[j];
+                for (int i = s + 1 + w; i < m; i += 8) {
+                    const double a = fma(-tw, A[(int64_t)i * r + s], A[(int64_t)i * r + j]);
+                    A[(int64_t)i * r + j] = a;
+                    acc = fma(a, a, acc);
+                }
+            }
+            red[w][j] = acc;
+        }
+        __syncthreads();
+        if (tid > s && tid < r) {  // norms over rows s+1.. for the next step
+            double t = 0.0;
+            for (int u = 0; u < 8; ++u) t += red[u][tid];
+            nrm[tid] = t;
         }
         __syncthreads();
         k = s + 1;
@@ -205,21 +231,25 @@ __global__ void __launch_bounds__(256) k_qr_tiles(const int *tile_alpha, const i
                 red[w][t] = acc;
             }
             __syncthreads();
-            if (threadIdx.x > j && threadIdx.x < k) {
-                double t = A[(int64_t)j * r + threadIdx.x];
-                for (int u = 0; u < 8; ++u) t += red[u][threadIdx.x];
-                nrm[threadIdx.x] = t;
+            if (tid > j && tid < k) {
+                double x = A[(int64_t)j * r + tid];
+                for (int u = 0; u < 8; ++u) x += red[u][tid];
+                const double tw = tj * x;
+                wv[tid] = tw;
+                A[(int64_t)j * r + tid] -= tw;
             }
             __syncthreads();
-            for (int o = threadIdx.x; o < m * k; o += blockDim.x) {
-                const int i = o / k, t = o % k;
-                if (t <= j || i < j) continue;
-                const double vi = (i == j) ? 1.0 : A[(int64_t)i * r + j];
-                A[(int64_t)i * r + t] -= tj * vi * nrm[t];
+            for (int h = 0; h < 2; ++h) {
+                const int t = lane + 32 * h;
+                if (t > j && t < k) {
+                    const double tw = wv[t];
+                    for (int i = j + 1 + w; i < m; i += 8)
+                        A[(int64_t)i * r + t] = fma(-tw, A[(int64_t)i * r + j], A[(int64_t)i * r + t]);
+                }
             }
             __syncthreads();
         }
-        for (int i = threadIdx.x; i < m; i += blockDim.x) {
+        for (int i = tid; i < m; i += blockDim.x) {
             double v;
             if (i < j) v = 0.0;
             else if (i == j) v = 1.0 - tj;
@@ -229,11 +259,12 @@ __global__ void __launch_bounds__(256) k_qr_tiles(const int *tile_alpha, const i
         __syncthreads();
     }
     // R_jj >= 0
-    for (int o = threadIdx.x; o < m * k; o += blockDim.x) {
-        const int i = o / k, j = o % k;
-        if (beta[j] < 0.0) A[(int64_t)i * r + j] = -A[(int64_t)i * r + j];
-    }
-    if (threadIdx.x == 0) kout[p] = k;
+    for (int i = w; i < m; i += 8)
+        for (int h = 0; h < 2; ++h) {
+            const int j = lane + 32 * h;
+            if (j < k && beta[j] < 0.0) A[(int64_t)i * r + j] = -A[(int64_t)i * r + j];
+        }
+    if (tid == 0) kout[p] = k;
 }
 
 // The same pivoted QR for tiles of at most QR_WARP_ROWS rows: one warp per
@@ -260,12 +291,14 @@ __global__ void __launch_bounds__(128) k_qr_warp(const int *tile_alpha, const in
     const int c0 = lane, c1 = lane + 32;
     double n0 = 0.0;
     int k = 0;
+    // exact norms of the lane's columns over rows s..m-1: a pass for step 0, then
+    // summed by the update of each step over the rows it leaves
+    double a0 = 0.0, a1 = 0.0;
+    for (int i = 0; i < m; ++i) {
+        if (c0 < r) a0 = fma(A[(int64_t)i * r + c0], A[(int64_t)i * r + c0], a0);
+        if (c1 < r) a1 = fma(A[(int64_t)i * r + c1], A[(int64_t)i * r + c1], a1);
+    }
     for (int s = 0; s < kmax; ++s) {
-        double a0 = 0.0, a1 = 0.0;
-        for (int i = s; i < m; ++i) {
-            if (c0 < r) a0 = fma(A[(int64_t)i * r + c0], A[(int64_t)i * r + c0], a0);
-            if (c1 < r) a1 = fma(A[(int64_t)i * r + c1], A[(int64_t)i * r + c1], a1);
-        }
         double best = -1.0;
         int bj = 1 << 30;
         if (c0 < r && c0 >= s) { best = a0; bj = c0; }
@@ -280,12 +313,19 @@ __global__ void __launch_bounds__(128) k_qr_warp(const int *tile_alpha, const in
         const bool stop = rank > 0 ? (s >= rank) : (!(n0 > 0.0) || !(nv > tol * n0));
         if (stop) break;
         const int piv = bj;
-        if (piv != s)
+        if (piv != s) {
             for (int i = lane; i < m; i += 32) {
                 const double t = A[(int64_t)i * r + s];
                 A[(int64_t)i * r + s] = A[(int64_t)i * r + piv];
                 A[(int64_t)i * r + piv] = t;
             }
+            // the norm of column s moves to column piv
+            const double ns = __shfl_sync(0xffffffffu, s < 32 ? a0 : a1, s & 31);
+            if (lane == (piv & 31)) {
+                if (piv < 32) a0 = ns;
+                else a1 = ns;
+            }
+        }
         __syncwarp();
         const double x0 = A[(int64_t)s * r + s];
         double t = 0.0, b = 0.0, sc = 0.0;
@@ -304,10 +344,18 @@ __global__ void __launch_bounds__(128) k_qr_warp(const int *tile_alpha, const in
         for (int h = 0; h < 2; ++h) {
             const int j = h ? c1 : c0;
             if (j <= s || j >= r) continue;
-            double w = A[(int64_t)s * r + j];
-            for (int i = s + 1; i < m; ++i) w = fma(A[(int64_t)i * r + s], A[(int64_t)i * r + j], w);
-            A[(int64_t)s * r + j] -= t * w;
-            for (int i = s + 1; i < m; ++i) A[(int64_t)i * r + j] -= t * A[(int64_t)i * r + s] * w;
+            double wj = A[(int64_t)s * r + j];
+            for (int i = s + 1; i < m; ++i) wj = fma(A[(int64_t)i * r + s], A[(int64_t)i * r + j], wj);
+            const double tw = t * wj;
+            A[(int64_t)s * r + j] -= tw;
+            double acc = 0.0;
+            for (int i = s + 1; i < m; ++i) {
+                const double a = fma(-tw, A[(int64_t)i * r + s], A[(int64_t)i * r + j]);
+                A[(int64_t)i * r + j] = a;
+                acc = fma(a, a, acc);
+            }
+            if (h) a1 = acc;
+            else a0 = acc;
         }
         __syncwarp();
         k = s + 1;
@@ -320,8 +368,9 @@ __global__ void __launch_bounds__(128) k_qr_warp(const int *tile_alpha, const in
             if (c <= j || c >= k) continue;
             double w = A[(int64_t)j * r + c];
             for (int i = j + 1; i < m; ++i) w = fma(A[(int64_t)i * r + j], A[(int64_t)i * r + c], w);
-            A[(int64_t)j * r + c] -= tj * w;
-            for (int i = j + 1; i < m; ++i) A[(int64_t)i * r + c] -= tj * A[(int64_t)i * r + j] * w;
+            const double tw = tj * w;
+            A[(int64_t)j * r + c] -= tw;
+            for (int i = j + 1; i < m; ++i) A[(int64_t)i * r + c] = fma(-tw, A[(int64_t)i * r + j], A[(int64_t)i * r + c]);
         }
         __syncwarp();
         for (int i = lane; i < m; i += 32) {
@@ -797,6 +846,16 @@ static void launch_gram(unsigned np, int nsplit, cudaStream_t st, const int *box
     ::hm::count_launch();
 }
 
+// the Gram products' arithmetic of the context's precision mode
+using GramLaunch = void (*)(unsigned, int, cudaStream_t, const int *, const int *, int, const double *, const double *,
+                            const int *, int64_t, const int64_t *, const int *, void *);
+static GramLaunch gram_launcher(const hm_ctx *c) {
+    if (c->cfg.precision == HM_MIXED_BF16X6_F32) return launch_gram<float, float>;
+    if (c->cfg.precision == HM_MIXED_BF16X6) return launch_gram<dfloat, double>;
+    return launch_gram<double, double>;
+}
+
+
 template <typename T, typename TP>
 static Err launch_core(int64_t np, int nsplit, int r, int kc, cudaStream_t st, const int *kU, const int *kV,
                        const int64_t *offB, const void *Mpart, const void *S1part, const void *S2part, double *B) {
@@ -863,7 +922,7 @@ Err bases_and_cores(hm_ctx *c, int level) {
     const int nsplit = std::max(1, ceil_div(cu.max_rows, GRAM_CHUNK));
     const size_t part_elems = (size_t)nsplit * np * r * r;
     HM_TRY(ensure(c->scratch_a, part_elems * elem));
-    (core32 ? launch_gram<float, float> : launch_gram<double, double>)((unsigned)np, nsplit, st, g.pair_alpha.as<int>(),
+    gram_launcher(c)((unsigned)np, nsplit, st, g.pair_alpha.as<int>(),
                                                          cu.ent.as<int>(), r, c->GP.as<double>(),
                                                          c->cur.Y.as<double>(), g.pair_color.as<int>(), n, nullptr,
                                                          nullptr, c->scratch_a.p);
@@ -995,10 +1054,10 @@ Err bases_and_cores(hm_ctx *c, int level) {
     HM_TRY(alloc(spart, 2 * part_elems * elem));
     void *S1part = spart.p;
     void *S2part = static_cast<unsigned char *>(spart.p) + part_elems * elem;
-    (core32 ? launch_gram<float, float> : launch_gram<double, double>)((unsigned)np, nsplit, st, g.pair_alpha.as<int>(),
+    gram_launcher(c)((unsigned)np, nsplit, st, g.pair_alpha.as<int>(),
                                                          cu.ent.as<int>(), r, c->GP.as<double>(), f.U.as<double>(),
                                                          nullptr, n, f.offU.as<int64_t>(), f.kU.as<int>(), S1part);
-    (core32 ? launch_gram<float, float> : launch_gram<double, double>)((unsigned)np, nsplit, st, cu.int_idx.as<int>(),
+    gram_launcher(c)((unsigned)np, nsplit, st, cu.int_idx.as<int>(),
                                                          cu.ent.as<int>(), r, c->GO.as<double>(), f.V.as<double>(),
                                                          nullptr, n, f.offV.as<int64_t>(), f.kV.as<int>(), S2part);
     HM_LAUNCH("gram S");

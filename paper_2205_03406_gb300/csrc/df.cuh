@@ -58,4 +58,15 @@ __device__ __forceinline__ float add(float a, float b) { return a + b; }
 __device__ __forceinline__ double add(double a, double b) { return a + b; }
 __device__ __forceinline__ dfloat add(dfloat a, dfloat b) { return df_add(a, b); }
 
+// conversions of the templated kernels: FP64 operand -> arithmetic type, and a
+// sum in the arithmetic type -> the accumulation type
+template <class T> __device__ __forceinline__ T from_f64(double x);
+template <> __device__ __forceinline__ float from_f64<float>(double x) { return (float)x; }
+template <> __device__ __forceinline__ double from_f64<double>(double x) { return x; }
+template <> __device__ __forceinline__ dfloat from_f64<dfloat>(double x) { return df_from(x); }
+__device__ __forceinline__ float widen(float a, float) { return a; }
+__device__ __forceinline__ double widen(float a, double) { return (double)a; }
+__device__ __forceinline__ double widen(double a, double) { return a; }
+__device__ __forceinline__ double widen(dfloat a, double) { return df_to(a); }
+
 }  // namespace hm
