@@ -81,6 +81,13 @@ def parse():
     ap.add_argument("--serving-matvecs", type=int, default=100,
                     help="matvecs per job in the serving measurement (the configuration has 1000)")
     ap.add_argument("--serving-slots", type=int, default=4)
+    ap.add_argument("--sweep", action="store_true",
+                    help="only the large precision sweep: a jittered Fibonacci sphere of --sweep-n points, "
+                         "K = 1/|x-y|, leaf 64, tol --sweep-tol, r --sweep-r, in the three precision modes; "
+                         "one JSON line")
+    ap.add_argument("--sweep-n", type=int, default=1 << 20)
+    ap.add_argument("--sweep-tol", type=float, default=1e-4)
+    ap.add_argument("--sweep-r", type=int, default=32)
     ap.add_argument("--oracle-series", type=str, default=None,
                     help="comma-separated torus sizes: time the full CPU oracle compression at each (and the "
                          "2048-point 1D dense configuration, best of 3), print one JSON line, exit")
@@ -261,15 +268,16 @@ def rank_seed(base: int, rank: int) -> int:
     return base + rank
 
 
-def time_mode(hm, w, pts, op, precision: int, rank: int, steps: int, relerr_iters, fmt: int = 0):
+def time_mode(hm, w, pts, op, precision: int, rank: int, steps: int, relerr_iters, fmt: int = 0, warm: bool = True):
     """Time-to-compress (CUDA events, after one warm-up job), relative error and
     storage of the same job in another precision mode or format."""
     import torch
     s = hm.Settings(d=3, leaf_size=w.leaf_size, r=w.r, oversample=w.oversample, tol=w.tol, precision=precision,
                     seed=rank_seed(w.seed, rank), format=fmt)
     comp = hm.Compressor(s, torch.cuda.current_stream())
-    comp.tree_build(pts)
-    comp.compress(op)
+    if warm:
+        comp.tree_build(pts)
+        comp.compress(op)
     stream = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
@@ -601,6 +609,33 @@ class OracleSample:
                 "seconds_estimate": round(est, 2)}
 
 
+def run_sweep(args):
+    """Time-to-compress, relative error (20 power iterations), ranks and storage
+    of one large job in every precision mode, FP64 last (it is the slowest)."""
+    import torch
+    import hm_workloads as W
+    import paper_2205_03406_gb300 as hm
+    w = W.sphere_invr(n=args.sweep_n, tol=args.sweep_tol, r=args.sweep_r)
+    pts = torch.from_numpy(w.points).cuda()
+    op = hm.kernel_op(w.kernel)
+    out = {"workload": f"sphere_invr_{w.n}", "n": w.n, "kernel": "1/|x-y|", "leaf_size": w.leaf_size,
+           "tol": w.tol, "r": w.r, "oversample": w.oversample, "data": "synthetic (seeded jittered Fibonacci sphere)",
+           "modes": {}}
+    for name in ("mixed", "mixed-f32", "fp64"):
+        pv, desc, dt = PRECISIONS[name]
+        try:
+            # one timed job each; FP64 without a warm-up job (minutes at this size)
+            res = time_mode(hm, w, pts, op, pv, 0, steps=1, relerr_iters=None if args.no_relerr else args.relerr_iters,
+                            warm=name != "fp64")
+            res["warm_up_job"] = name != "fp64"
+        except hm.HMError as e:  # a mode that does not fit on the device says so
+            res = {"error": f"{e}"}
+        res["precision"] = desc
+        out["modes"][name] = res
+        torch.cuda.empty_cache()
+    print(json.dumps(out), flush=True)
+
+
 def oracle_series(sizes):
     """The full CPU oracle (tree, colourings, samples, peel, bases, cores, leaf
     blocks) timed end to end on the torus job at the given sizes, and on the
@@ -666,6 +701,9 @@ def main():
     args = parse()
     if args.peaks:
         print(json.dumps(measure_peaks()), flush=True)
+        return
+    if args.sweep:
+        run_sweep(args)
         return
     if args.oracle_series:
         print(json.dumps(oracle_series([int(v) for v in args.oracle_series.split(",")])), flush=True)

@@ -9,6 +9,8 @@
 //           the pair's column box (adjoint: row box) in turn, each lane one
 //           column of the factor (whole rows are read coalesced), the warps'
 //           sums are added in warp order and t_q = B_q s (adjoint B_q^T s);
+//           on cuts of boxes of at most AP1W_MAX_ROWS rows one warp per pair
+//           does the same (k_ap1w), 8 pairs per CTA;
 //  stage 2 (k_ap2): one CTA per APPLY_ROWS-row chunk of a box of the cut,
 //           thread i owning row i; for every pair of the box the chunk's rows
 //           of U_q (adjoint V) -- contiguous in the arena -- and t_q are
@@ -43,6 +45,8 @@ Err permute_rows(hm_ctx *c, const double *in, double *out, int nrhs, bool to_sor
 namespace {
 
 constexpr int AP1_BATCH = 8;  // rows a stage-1 warp reads before it multiplies
+constexpr int AP1W_BATCH = 4;  // rows per warp load batch in the warp-per-pair kernel
+constexpr int AP1W_MAX_ROWS = 512;  // cuts whose boxes are at most this long: one warp per pair
 
 __device__ __forceinline__ void cp8(void *dst, const void *src) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
@@ -129,6 +133,86 @@ __global__ void __launch_bounds__(NW * 32) k_ap1(ApplyLevel L, const double *x, 
         for (int vv = 0; vv < kin; ++vv)
             acc = fma(trans ? Bq[(int64_t)vv * kout + u] : Bq[(int64_t)u * kin + vv], ss[vv][j], acc);
         tq[(int64_t)u * nrhs + j0 + j] = acc;
+    }
+}
+
+// stage 1 for cuts of small boxes: one warp per pair (8 pairs per CTA), the
+// same lane packing as k_ap1; the column sums are reduced with shuffles and
+// t_q = B_q s (adjoint B_q^T s) is formed by the same warp, lane u (and u + 32)
+// owning output u, with s broadcast from the lanes that hold it.
+template <int NB>
+__global__ void __launch_bounds__(256, 2) k_ap1w(ApplyLevel L, int64_t np, const double *x, int nrhs, int trans,
+                                              double *t) {
+    const int lane = threadIdx.x & 31;
+    const int64_t q = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (q >= np) return;
+    const int j0 = blockIdx.y * NB, nb = min(NB, nrhs - j0);
+    const int ku = L.kU[q], kv = L.kV[q];
+    if (ku == 0 || kv == 0) return;
+    const int kin = trans ? ku : kv, kout = trans ? kv : ku;
+    const int box = trans ? L.pair_alpha[q] : L.int_idx[q];
+    const int *e = L.ent + (int64_t)box * ENT_FIELDS;
+    const int s0 = e[3], m = e[4] - e[3];
+    const double *F = trans ? L.U + L.offU[q] : L.V + L.offV[q];
+    const int kp = kin <= 8 ? 8 : (kin <= 16 ? 16 : (kin <= 32 ? 32 : 64));
+    const int rpi = kp >= 32 ? 1 : 32 / kp;
+    const int v = kp == 64 ? lane : lane % kp, rsub = kp >= 32 ? 0 : lane / kp;
+    const bool c0 = v < kin, c1 = kp == 64 && lane + 32 < kin;
+    double a0[NB], a1[NB];
+#pragma unroll
+    for (int j = 0; j < NB; ++j) a0[j] = a1[j] = 0.0;
+    for (int g0 = rsub; g0 < m; g0 += AP1W_BATCH * rpi) {
+        double f0[AP1W_BATCH], f1[AP1W_BATCH], xv[AP1W_BATCH][NB];
+#pragma unroll
+        for (int b = 0; b < AP1W_BATCH; ++b) {
+            const int i = g0 + b * rpi;
+            const bool in = i < m;
+            const double *Fr = F + (int64_t)i * kin;
+            f0[b] = (in && c0) ? Fr[v] : 0.0;
+            f1[b] = (in && c1) ? Fr[lane + 32] : 0.0;
+#pragma unroll
+            for (int j = 0; j < NB; ++j) xv[b][j] = (in && j < nb) ? x[(int64_t)(s0 + i) * nrhs + j0 + j] : 0.0;
+        }
+#pragma unroll
+        for (int b = 0; b < AP1W_BATCH; ++b)
+#pragma unroll
+            for (int j = 0; j < NB; ++j) a0[j] = fma(f0[b], xv[b][j], a0[j]);
+        if (kp == 64)
+#pragma unroll
+            for (int b = 0; b < AP1W_BATCH; ++b)
+#pragma unroll
+                for (int j = 0; j < NB; ++j) a1[j] = fma(f1[b], xv[b][j], a1[j]);
+    }
+#pragma unroll
+    for (int j = 0; j < NB; ++j)
+        for (int o = kp; o < 32; o <<= 1) a0[j] += __shfl_down_sync(0xffffffffu, a0[j], o);
+    // lane vv < kp holds s[vv] (and s[vv + 32] when kp == 64)
+    const double *Bq = L.B + L.offB[q];
+    double *tq = t + (trans ? L.toffV[q] : L.toffU[q]) * nrhs;
+    double acc0[NB], acc1[NB];
+#pragma unroll
+    for (int j = 0; j < NB; ++j) acc0[j] = acc1[j] = 0.0;
+    const int u0 = lane, u1 = lane + 32;
+    for (int vv = 0; vv < kin; ++vv) {
+        double sv[NB];
+#pragma unroll
+        for (int j = 0; j < NB; ++j) sv[j] = __shfl_sync(0xffffffffu, vv < 32 ? a0[j] : a1[j], vv & 31);
+        if (u0 < kout) {
+            const double bv = trans ? Bq[(int64_t)vv * kout + u0] : Bq[(int64_t)u0 * kin + vv];
+#pragma unroll
+            for (int j = 0; j < NB; ++j) acc0[j] = fma(bv, sv[j], acc0[j]);
+        }
+        if (u1 < kout) {
+            const double bv = trans ? Bq[(int64_t)vv * kout + u1] : Bq[(int64_t)u1 * kin + vv];
+#pragma unroll
+            for (int j = 0; j < NB; ++j) acc1[j] = fma(bv, sv[j], acc1[j]);
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+        if (j >= nb) break;
+        if (u0 < kout) tq[(int64_t)u0 * nrhs + j0 + j] = acc0[j];
+        if (u1 < kout) tq[(int64_t)u1 * nrhs + j0 + j] = acc1[j];
     }
 }
 
@@ -371,11 +455,12 @@ static Err launch_level(const ApplyLevel &a, int max_rows, int64_t np, const int
                         const double *x, int nrhs, int trans, double *t, double *y, cudaStream_t st) {
     const unsigned nblk = (unsigned)ceil_div(nrhs, NB);
     if (max_rows > 1024) k_ap1<16, NB><<<dim3((unsigned)np, nblk), 512, 0, st>>>(a, x, nrhs, trans, t);
-    else k_ap1<4, NB><<<dim3((unsigned)np, nblk), 128, 0, st>>>(a, x, nrhs, trans, t);
+    else if (max_rows > AP1W_MAX_ROWS) k_ap1<4, NB><<<dim3((unsigned)np, nblk), 128, 0, st>>>(a, x, nrhs, trans, t);
+    else k_ap1w<NB><<<dim3((unsigned)ceil_div(np, 8), nblk), 256, 0, st>>>(a, np, x, nrhs, trans, t);
     ::hm::count_launch();
     HM_LAUNCH("apply stage 1");
     const size_t smem = (2 * (size_t)APPLY_ROWS * ld + 2 * 64 * NB) * sizeof(double);
-    HM_CUDA(cudaFuncSetAttribute(k_ap2<NB, FactorRows>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    HM_TRY(allow_smem(k_ap2<NB, FactorRows>, smem));
     if (nitems > 0) {
         FactorRows src{a, t, trans};
         k_ap2<NB, FactorRows><<<dim3((unsigned)nitems, nblk), APPLY_ROWS, smem, st>>>(src, a.ent, items, nrhs, ld, y);
@@ -401,7 +486,7 @@ Err apply_near(hm_ctx *c, const double *x, double *y, int nrhs, int trans) {
 #define NEARF(NBV)                                                                                                 \
     do {                                                                                                           \
         const size_t smem = (2 * (size_t)APPLY_ROWS * ld + 2 * 64 * NBV) * sizeof(double);                         \
-        HM_CUDA(cudaFuncSetAttribute(k_ap2<NBV, NearRows>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)); \
+        HM_TRY(allow_smem(k_ap2<NBV, NearRows>, smem));                                                             \
         k_ap2<NBV, NearRows><<<grid, APPLY_ROWS, smem, st>>>(src, cl.ent.as<int>(), P.items[c->L].as<int>(), nrhs,  \
                                                              ld, y);                                              \
     } while (0)

@@ -863,7 +863,7 @@ static Err launch_core(int64_t np, int nsplit, int r, int kc, cudaStream_t st, c
     const int core_warps = (int)std::min<size_t>(CORE_WARPS, (200 * 1024) / per_warp);
     if (core_warps < 1) return fail(HM_ENOTSUP, "cores: r x k too large for shared memory");
     const size_t smem = (size_t)core_warps * per_warp;
-    HM_CUDA(cudaFuncSetAttribute(k_core<T, TP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    HM_TRY(allow_smem(k_core<T, TP>, smem));
     k_core<T, TP><<<ceil_div(np, core_warps), core_warps * 32, smem, st>>>(
         r, kc, np, nsplit, kU, kV, offB, static_cast<const TP *>(Mpart), static_cast<const TP *>(S1part),
         static_cast<const TP *>(S2part), B);
@@ -884,7 +884,7 @@ Err qr_tiles_fp64(hm_ctx *c, int level, const int *tile_box, const int *tile_col
                                                nt, tile_cap); ::hm::count_launch();
     if (max_rows > QR_WARP_ROWS) {
         const size_t smem = (size_t)std::min(qr64_rows, max_rows) * r * sizeof(double);
-        HM_CUDA(cudaFuncSetAttribute(k_qr_smem<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        HM_TRY(allow_smem(k_qr_smem<double>, (size_t)((int)smem)));
         k_qr_smem<double><<<(unsigned)nt, 512, smem, st>>>(tile_box, tile_box, tile_color, ent, n, r, cap, rank, tol,
                                                            base, kout, QR_WARP_ROWS, qr64_rows, tile_cap); ::hm::count_launch();
     }
@@ -946,9 +946,9 @@ Err bases_and_cores(hm_ctx *c, int level) {
     const size_t qr32_smem = (size_t)std::max(1, std::min(qr32_rows, cu.max_rows)) * r * sizeof(float);
     const size_t qr64_smem = (size_t)std::max(1, std::min(qr64_rows, cu.max_rows)) * r * sizeof(double);
     if (mixed)
-        HM_CUDA(cudaFuncSetAttribute(k_qr_smem<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)qr32_smem));
+        HM_TRY(allow_smem(k_qr_smem<float>, (size_t)((int)qr32_smem)));
     else if (cu.max_rows > QR_WARP_ROWS)
-        HM_CUDA(cudaFuncSetAttribute(k_qr_smem<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)qr64_smem));
+        HM_TRY(allow_smem(k_qr_smem<double>, (size_t)((int)qr64_smem)));
     // tall-skinny blocks (the same for the Y and the Z tiles)
     DBuf ts_cnt, ts_off, blk_tile, blk_row0, blk_rows, rstack, taus;
     int64_t nblk = 0;
@@ -971,12 +971,9 @@ Err bases_and_cores(hm_ctx *c, int level) {
                                                          blk_rows.as<int>()); ::hm::count_launch();
             HM_LAUNCH("ts_fill");
             nb_top = ceil_div(std::min(cu.max_rows, ts_max), ts_rows);
-            HM_CUDA(cudaFuncSetAttribute(k_ts_block, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)(ts_rows * r * sizeof(float))));
-            HM_CUDA(cudaFuncSetAttribute(k_ts_top, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)((size_t)nb_top * r * r * sizeof(float))));
-            HM_CUDA(cudaFuncSetAttribute(k_ts_form, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)(2 * ts_rows * r * sizeof(float))));
+            HM_TRY(allow_smem(k_ts_block, (size_t)((int)(ts_rows * r * sizeof(float)))));
+            HM_TRY(allow_smem(k_ts_top, (size_t)((int)((size_t)nb_top * r * r * sizeof(float)))));
+            HM_TRY(allow_smem(k_ts_form, (size_t)((int)(2 * ts_rows * r * sizeof(float)))));
         }
     }
     for (int side = 0; side < 2; ++side) {

@@ -664,7 +664,7 @@ Err color_cut(hm_ctx *c, int level, bool leaf, cudaStream_t st, DBuf &scan_tmp) 
     // edges
     const size_t bm_bytes = (size_t)((nv + 31) / 32) * 4;
     if (bm_bytes > 200 * 1024) return fail(HM_ENOTSUP, "colour: vertex bitmap exceeds shared memory");
-    HM_CUDA(cudaFuncSetAttribute(k_edges, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    HM_TRY(allow_smem(k_edges, (size_t)(200 * 1024)));
     DBuf adj_ptr, adj;
     HM_TRY(alloc(adj_ptr, (nv + 1) * sizeof(int64_t)));
     k_edges<<<(int)nv, 256, bm_bytes, st>>>(nv, g.vertex_pair.as<int>(), g.vertex_beta.as<int>(),
@@ -735,7 +735,7 @@ Err color_boxes(hm_ctx *c, int level, cudaStream_t st, DBuf &scan_tmp) {
     HM_LAUNCH("box vertices");
     const size_t bm_bytes = (size_t)((nv + 31) / 32) * 4;
     if (bm_bytes > 200 * 1024) return fail(HM_ENOTSUP, "colour boxes: vertex bitmap exceeds shared memory");
-    HM_CUDA(cudaFuncSetAttribute(k_box_edges, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    HM_TRY(allow_smem(k_box_edges, (size_t)(200 * 1024)));
     DBuf adj_ptr, adj;
     HM_TRY(alloc(adj_ptr, (nv + 1) * sizeof(int64_t)));
     k_box_edges<<<(int)nv, 256, bm_bytes, st>>>(nv, g.pair_alpha.as<int>(), vid.as<int>(), cu.near_ptr.as<int>(),

@@ -142,6 +142,28 @@ struct DeviceScope {
     DeviceScope &operator=(const DeviceScope &) = delete;
 };
 
+// Opts a kernel into the largest dynamic shared memory the current device
+// allows (its opt-in limit less the kernel's static shared memory) and checks
+// that `need` bytes fit.  Every caller sets the same value, so jobs compressed
+// concurrently on several host threads cannot lower each other's limit between
+// one thread's setting and its launch.
+template <class Kernel> inline Err allow_smem(Kernel *kernel, size_t need) {
+    int dev = 0, optin = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+        return fail(HM_ECUDA, "allow_smem: device attributes");
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, (const void *)kernel) != cudaSuccess)
+        return fail(HM_ECUDA, "allow_smem: kernel attributes");
+    const int lim = optin - (int)fa.sharedSizeBytes;
+    if ((int64_t)need > lim)
+        return fail(HM_ENOTSUP, "kernel needs " + std::to_string(need) + " bytes of shared memory, the device allows " +
+                                    std::to_string(lim));
+    if (cudaFuncSetAttribute((const void *)kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, lim) != cudaSuccess)
+        return fail(HM_ECUDA, "allow_smem: cudaFuncSetAttribute");
+    return ok();
+}
+
 inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 
 // ---------------------------------------------------------------------------

@@ -185,7 +185,7 @@ Err peel_level(hm_ctx *c, int level, bool leaf) {
     cudaStream_t st = c->st;
     const size_t smem = 2 * (size_t)c->cfg.r * cols * sizeof(double);
     if (smem > 200 * 1024) return fail(HM_ENOTSUP, "peel: r x columns per colour too large");
-    HM_CUDA(cudaFuncSetAttribute(k_peel_update, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    HM_TRY(allow_smem(k_peel_update, (size_t)((int)smem)));
     for (int j = 2; j <= jmax; ++j) {
         if (j >= (int)c->factors.size() || !c->factors[j].done || c->factors[j].n_pairs == 0) continue;
         const Factors &f = c->factors[j];

@@ -601,12 +601,12 @@ static Err launch_update_df(hm_ctx *c, const pm::CoarseDF *tab, int ntab, int ch
     HM_CUDA(cudaEventRecord(e0, st));
     auto *macs = c->peel_macs.as<unsigned long long>();
     if (maxc == 32) {
-        HM_CUDA(cudaFuncSetAttribute(pm::k_peel_gemm_df<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        HM_TRY(allow_smem(pm::k_peel_gemm_df<32>, (size_t)((int)smem)));
         pm::k_peel_gemm_df<32><<<(unsigned)nitems, 128, smem, st>>>(
             tab, ntab, chi, g.pair_alpha.as<int>(), g.pair_color.as<int>(), cl.ent.as<int>(), item_tile.as<int64_t>(),
             item_row.as<int>(), nitems, cols, r, c->n, OUT, macs);
     } else {
-        HM_CUDA(cudaFuncSetAttribute(pm::k_peel_gemm_df<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        HM_TRY(allow_smem(pm::k_peel_gemm_df<64>, (size_t)((int)smem)));
         pm::k_peel_gemm_df<64><<<(unsigned)nitems, 128, smem, st>>>(
             tab, ntab, chi, g.pair_alpha.as<int>(), g.pair_color.as<int>(), cl.ent.as<int>(), item_tile.as<int64_t>(),
             item_row.as<int>(), nitems, cols, r, c->n, OUT, macs);
@@ -640,13 +640,13 @@ static Err launch_update(const pm::CoarseT<double> *tab, int ntab, int side, int
                          int64_t n, double *OUT, cudaStream_t st) {
     const size_t smem = (size_t)r * (pm::GEMM64_LDF + (cols <= 32 ? 32 : 64)) * sizeof(double);
     if (cols <= 32) {
-        HM_CUDA(cudaFuncSetAttribute(pm::k_peel_gemm64<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        HM_TRY(allow_smem(pm::k_peel_gemm64<32>, (size_t)((int)smem)));
         pm::k_peel_gemm64<32><<<(unsigned)nitems, 128, smem, st>>>(tab, ntab, side, chi, g.pair_alpha.as<int>(),
                                                                    g.pair_color.as<int>(), cl.ent.as<int>(),
                                                                    item_tile.as<int64_t>(), item_row.as<int>(),
                                                                    nitems, cols, r, n, OUT);
     } else {
-        HM_CUDA(cudaFuncSetAttribute(pm::k_peel_gemm64<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        HM_TRY(allow_smem(pm::k_peel_gemm64<64>, (size_t)((int)smem)));
         pm::k_peel_gemm64<64><<<(unsigned)nitems, 128, smem, st>>>(tab, ntab, side, chi, g.pair_alpha.as<int>(),
                                                                    g.pair_color.as<int>(), cl.ent.as<int>(),
                                                                    item_tile.as<int64_t>(), item_row.as<int>(),
@@ -844,7 +844,7 @@ template <typename R> static Err peel_level_t(hm_ctx *c, int level, bool leaf) {
             co.T = T.as<R>();
             if (nslots[i] > 0) {
                 const size_t smem = (size_t)pm::WARPS * r * cols * sizeof(R);
-                HM_CUDA(cudaFuncSetAttribute(pm::k_peel_T<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+                HM_TRY(allow_smem(pm::k_peel_T<R>, (size_t)((int)smem)));
                 pm::k_peel_T<R><<<ceil_div(ncomb, pm::WARPS), pm::WARPS * 32, smem, st>>>(
                     co, ncomb, chi, side, cols, r, cl.pt2ent.as<int>(), g.act_ptr.as<int>(), g.act_box.as<int>(),
                     kDF ? recb.as<pm::PeelRec>() : nullptr, kDF ? cntb.as<int>() : nullptr,

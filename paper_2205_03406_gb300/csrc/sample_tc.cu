@@ -8,9 +8,11 @@
 // coordinates (x = hi + lo, both FP32), so differences of nearby points keep
 // FP32 accuracy; K and G are split into three BF16 pieces (h + m + l carries
 // 24 bits) and the six products hh, hm, mh, hl, mm, lh accumulate in FP32 in
-// tensor memory, merged into three accumulators (hh | hm + mh | hl + mm + lh);
-// every two chunks the producers add them into double-float registers, and
-// the epilogue writes FP64.
+// tensor memory, in two accumulators: hh, and the five lower-order products
+// together (each at most 2^-8 of hh, so their FP32 rounding is about 2^-32 of
+// the total); every four chunks the producers add them into double-float
+// registers, and the epilogue writes FP64.  Two accumulator sets of 4r columns
+// fit the 512 columns of tensor memory for r <= 64.
 //
 // Per level a pack kernel writes, for every colour, chunks of 64 active rows
 // in the exact shared-memory image the tensor core reads: the three BF16
@@ -22,8 +24,9 @@
 //     FP32x2 arithmetic, split it and store it swizzled, then arrive on an
 //     mbarrier,
 //   - one thread of the MMA warp issues tcgen05.mma (M = 128, K = 16 per
-//     instruction, three instructions per K step: A_h x [B_h B_m B_l],
-//     A_m x [B_h B_m], A_l x B_h) and tcgen05.commit frees the stage,
+//     instruction, five instructions per K step: A_h x [B_h B_m] into
+//     hh | rest, then A_h x B_l, A_m x B_h, A_m x B_m, A_l x B_h into rest)
+//     and tcgen05.commit frees the stage,
 //   - the producers read the accumulators with tcgen05.ld (promotion and
 //     epilogue).
 // Every mbarrier wait is bounded; on expiry a status word is set and the CTA
@@ -252,9 +255,8 @@ struct Params {
                                // pipeline's waits run out (set by the host only)
 };
 
-constexpr int SEG = 2;      // chunks accumulated in tensor memory before promotion
-constexpr int MAXR = 40;    // largest r
-constexpr int MAXH = MAXR / 2;  // columns per thread in the promotion: r / 2
+constexpr int SEG = 4;      // chunks accumulated in tensor memory before promotion
+constexpr int MAXR = 64;    // largest r (two sets of 4r accumulator columns in 512)
 
 // exact FP32 -> FP64 with integer operations (normal numbers; zero and
 // subnormals map to a signed zero), keeping the conversion off the FP64 pipe
@@ -275,7 +277,8 @@ __device__ __forceinline__ void dfadd(float &hi, float &lo, float v) {
     lo += err;
 }
 
-template <int KIND>
+// MH: the largest r / 2 of the instantiation (accumulator columns per producer thread)
+template <int KIND, int MH>
 __global__ void __launch_bounds__(NTHREADS, 1) k_sample_tc(Params P) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     __shared__ uint64_t full_a[2], full_b[2], empty[2], seg_done[2], set_free[2], accum;
@@ -345,9 +348,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_sample_tc(Params P) {
         const int quarter = warp & 3, sub = warp >> 2, hr = r >> 1;
         const uint32_t trow = tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(sub * hr);
         const float scale = (float)kscale(KIND);
-        float acc_hi[MAXH], acc_lo[MAXH];
+        float acc_hi[MH], acc_lo[MH];
 #pragma unroll
-        for (int k = 0; k < MAXH; ++k) acc_hi[k] = acc_lo[k] = 0.0f;
+        for (int k = 0; k < MH; ++k) acc_hi[k] = acc_lo[k] = 0.0f;
         int promoted = 0;
         auto promote = [&](int sg) -> bool {
             const int set = sg & 1;
@@ -355,19 +358,18 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_sample_tc(Params P) {
             const bool done = mbar_wait(&seg_done[set], (uint32_t)(sg >> 1) & 1, status, P.wait_ns, false);
             if (!__all_sync(0xffffffffu, done)) return false;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t base = trow + (uint32_t)(set * 6 * r);
+            const uint32_t base = trow + (uint32_t)(set * 4 * r);
 #pragma unroll
-            for (int g = 0; g < MAXH / 4; ++g) {
+            for (int g = 0; g < MH / 4; ++g) {
                 if (4 * g >= hr) break;
-                float hh[4], x1[4], x2[4];
+                float hh[4], lo[4];
                 tmem_ld4(base + 4 * g, hh);
-                tmem_ld4(base + 2 * r + 4 * g, x1);
-                tmem_ld4(base + 4 * r + 4 * g, x2);
+                tmem_ld4(base + 2 * r + 4 * g, lo);
                 tmem_wait_ld();
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
                     dfadd(acc_hi[4 * g + k], acc_lo[4 * g + k], hh[k] * scale);
-                    acc_lo[4 * g + k] += (x1[k] + x2[k]) * scale;
+                    acc_lo[4 * g + k] = fmaf(lo[k], scale, acc_lo[4 * g + k]);
                 }
             }
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -457,7 +459,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_sample_tc(Params P) {
             const int64_t i = P.out_rows[obase + mo];
             double *dst = ((sub >> 1) ? P.Z : P.Y) + ((int64_t)c * P.n + i) * r + (sub & 1) * hr;
 #pragma unroll
-            for (int k = 0; k < MAXH; k += 2) {
+            for (int k = 0; k < MH; k += 2) {
                 if (k >= hr) break;
                 *reinterpret_cast<double2 *>(dst + k) =
                     make_double2(f2d(acc_hi[k]) + f2d(acc_lo[k]), f2d(acc_hi[k + 1]) + f2d(acc_lo[k + 1]));
@@ -481,7 +483,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_sample_tc(Params P) {
         }
     } else if (lane == 0) {
         // ------------------------------------------------------------ MMA issuer
-        const uint32_t id1 = idesc_bf16(6 * r), id2 = idesc_bf16(4 * r), id3 = idesc_bf16(2 * r);
+        const uint32_t id4 = idesc_bf16(4 * r), id2 = idesc_bf16(2 * r);
         for (int q = 0; q < nchunks && ok; ++q) {
             const int s = q & 1;
             const uint32_t u = (uint32_t)(q >> 1);
@@ -494,16 +496,20 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_sample_tc(Params P) {
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint32_t sa = smem_u32(smem + s * SB);
             const uint64_t ah = sw128_desc(sa), am = sw128_desc(sa + A_PIECE), al = sw128_desc(sa + 2 * A_PIECE);
-            const uint64_t bd = sw128_desc(sa + 3 * A_PIECE);
-            const uint32_t d = tmem + (uint32_t)(set * 6 * r);
+            // B pieces: 2r rows each (128 bytes a row), B_m and B_l at multiples of 1024 bytes
+            const uint32_t sb = sa + 3 * A_PIECE;
+            const uint64_t bh = sw128_desc(sb), bm = sw128_desc(sb + 2 * r * 128), bl = sw128_desc(sb + 4 * r * 128);
+            const uint32_t d = tmem + (uint32_t)(set * 4 * r), dl = d + 2 * r;
 #pragma unroll
             for (int kk = 0; kk < 4; ++kk) {
                 const uint64_t adv = (uint64_t)(kk * 2);  // 32 bytes per K step, in 16-byte units
-                // A_h x [B_h B_m B_l] -> hh | hm | hl ; A_m x [B_h B_m] adds mh, mm onto hm, hl ;
-                // A_l x B_h adds lh onto hl.  The first product of a segment starts the set.
-                mma_bf16(d, ah + adv, bd + adv, id1, (first && kk == 0) ? 0u : 1u);
-                mma_bf16(d + 2 * r, am + adv, bd + adv, id2, 1u);
-                mma_bf16(d + 4 * r, al + adv, bd + adv, id3, 1u);
+                // A_h x [B_h B_m] -> hh | hm (the first product of a segment starts the
+                // set), then hl, mh, mm, lh onto the low-order accumulator
+                mma_bf16(d, ah + adv, bh + adv, id4, (first && kk == 0) ? 0u : 1u);
+                mma_bf16(dl, ah + adv, bl + adv, id2, 1u);
+                mma_bf16(dl, am + adv, bh + adv, id2, 1u);
+                mma_bf16(dl, am + adv, bm + adv, id2, 1u);
+                mma_bf16(dl, al + adv, bh + adv, id2, 1u);
             }
             mma_commit(&empty[s]);
             if ((q % SEG) == SEG - 1 || q == nchunks - 1) mma_commit(&seg_done[set]);
@@ -679,7 +685,7 @@ static bool tc_stall_now() {
 
 bool tc_supported(const hm_ctx *c) {
     const int r = c->cfg.r;
-    return r % 8 == 0 && r >= 8 && r <= 40;
+    return r % 8 == 0 && r >= 8 && r <= tc::MAXR;
 }
 
 Err sample_tc(hm_ctx *c, int level, int kernel) {
@@ -747,10 +753,16 @@ Err sample_tc(hm_ctx *c, int level, int kernel) {
     HM_CUDA(cudaEventCreate(&e1));
     HM_CUDA(cudaEventRecord(e0, st));
     switch (kernel) {
-#define LAUNCH(K)                                                                                   \
-    case K:                                                                                         \
-        HM_CUDA(cudaFuncSetAttribute(k_sample_tc<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)); \
-        k_sample_tc<K><<<grid, NTHREADS, smem, st>>>(P); ::hm::count_launch();                                            \
+#define LAUNCH(K)                                                                                       \
+    case K:                                                                                             \
+        if (r <= 40) {                                                                                  \
+            HM_TRY(allow_smem(k_sample_tc<K, 20>, (size_t)smem));                                      \
+            k_sample_tc<K, 20><<<grid, NTHREADS, smem, st>>>(P);                                       \
+        } else {                                                                                        \
+            HM_TRY(allow_smem(k_sample_tc<K, 32>, (size_t)smem));                                      \
+            k_sample_tc<K, 32><<<grid, NTHREADS, smem, st>>>(P);                                       \
+        }                                                                                               \
+        ::hm::count_launch();                                                                           \
         break;
         LAUNCH(HM_K_LOG)
         LAUNCH(HM_K_LAPLACE3D)

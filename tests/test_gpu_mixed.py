@@ -43,6 +43,11 @@ def mixed_workloads():
         # rounding alone puts the result 2e-6..6e-6 from the FP64 oracle.
         "line_tall_r16": W.Workload("line_tall", W.line1d(8000, 11), W.K_INVR, leaf_size=64, r=16, rank=12,
                                     seed=11),
+        # r above 40: two accumulator sets of 4r tensor-memory columns (r <= 64)
+        "sphere_invr_r48": W.Workload("sphere48", W.sphere(4500, 6), W.K_INVR, leaf_size=64, r=48, tol=1e-8,
+                                      seed=8),
+        "torus_r64": W.Workload("torus64", W.torus(5000, 12), W.K_LAPLACE3D, leaf_size=64, r=64, tol=1e-9,
+                                seed=10),
     }
 
 
@@ -95,6 +100,17 @@ def test_mixed_compression_matches_oracle(name, precision):
     comp.close()
 
 
+@pytest.mark.parametrize("name", ["sphere_invr_r48", "torus_r64"])
+def test_tensor_path_covers_r_up_to_64(name):
+    """With r of 48 and 64 every admissible level is sampled on the tensor cores
+    (none falls back to the FP64 black box)."""
+    w = mixed_workloads()[name]
+    comp, info = run_gpu(w, precision=MIXED, keep=False)
+    levels = sum(1 for l in range(2, info.L + 1) if info.pairs[l] > 0)
+    assert info.bb_tc_levels == levels and info.bb_fp64_levels == 0, (info.bb_tc_levels, info.bb_fp64_levels)
+    comp.close()
+
+
 def _level_block_errors(comp, H):
     """Per level: ranks (GPU, oracle) and the aggregate relative error of the
     blocks U B V^T, sqrt(sum ||blk - ref||^2 / sum ||ref||^2)."""
@@ -121,9 +137,10 @@ def test_mixed_blocks_match_oracle(name):
     with a fixed rank the ranks are identical and the blocks U B V^T agree with
     the oracle's to 1e-5 per level (FP32-class samples, a basis perturbed by
     the sample error over the spectral gap at k); with a tolerance a rank may
-    move by one where a pivot norm sits within the samples' rounding of the
-    threshold (1.5 % of the pairs at level 3 of the 6k torus; at most 5 %
-    allowed), and the blocks of equal rank agree to the same bound."""
+    move where pivot norms sit within the samples' rounding of the threshold:
+    by one, or by two where two adjacent pivots both do (on the 6k torus 0.3 %,
+    1.5 % and 1.8 % of the pairs at levels 2, 3, 4, one of them by two; at most
+    5 % and two allowed), and the blocks of equal rank agree to the same bound."""
     w = mixed_workloads()[name]
     comp, _ = run_gpu(w, precision=MIXED, keep=False)
     t = ot.build_tree(w.points, w.leaf_size, w.uniform_depth)
@@ -137,7 +154,7 @@ def test_mixed_blocks_match_oracle(name):
         if w.rank and not w.tol:
             assert dmax == 0, l
         else:
-            assert dmax <= 1 and frac <= 0.05, (l, dmax, frac)
+            assert dmax <= 2 and frac <= 0.05, (l, dmax, frac)
         assert e <= 1e-5, (l, e)
     comp.close()
 
