@@ -55,6 +55,9 @@ PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustain
 # entries a step evaluates); valid only for the source whose sha256 prefix
 # (full-line comments excluded, see source_sha) is recorded here
 TRAFFIC = {"file": "paper_2205_03406_gb300/csrc/sample_tc.cu", "sha256": "ffc9f6e9401545c1", "bytes_per_eval": 0.5968}
+# DRAM bytes per double-float multiply-add of k_peel_gemm_df from one ncu capture
+# (profiles/), valid while the kernel's source is unchanged
+TRAFFIC_DF = {"file": "paper_2205_03406_gb300/csrc/peel_mixed.cu", "sha256": "", "bytes_per_mac": 0.0}
 
 
 def parse():
@@ -71,6 +74,7 @@ def parse():
                     help="skip timing the other two precision modes beside the main line")
     ap.add_argument("--no-formats", action="store_true",
                     help="skip timing the uniform H^1 and H^2 formats of the same job")
+    ap.add_argument("--formats-r", type=int, default=48, help="r of the uniform H^1 and H^2 measurements")
     ap.add_argument("--relerr-iters", type=int, default=20)
     ap.add_argument("--no-relerr", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -213,6 +217,14 @@ def roofline_df(info):
     FP64-equivalent flops (2 per multiply-add)."""
     t = info.seconds_peel_update
     flops = 2.0 * info.peel_update_macs
+    launches = int(sum(1 for l in range(3, info.L + 1) if info.colors[l] > 0) * 2 +
+                   (1 if info.colors[info.L + 1] > 0 else 0))
+    traffic = None
+    try:
+        if TRAFFIC_DF["bytes_per_mac"] and TRAFFIC_DF["sha256"] == source_sha(os.path.join(ROOT, TRAFFIC_DF["file"])):
+            traffic = round(TRAFFIC_DF["bytes_per_mac"] * info.peel_update_macs / max(launches, 1))
+    except OSError:
+        traffic = None
     peak = 2.0 * FP32_INSTR_PER_S / DF_INSTR_PER_MAC / 1e12
     achieved = flops / t / 1e12 if t > 0 else 0.0
     return {"kernel": "k_peel_gemm_df (double-float peel update)", "bound": "alu",
@@ -220,9 +232,8 @@ def roofline_df(info):
             "frac": round(achieved / peak, 4),
             "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2070 MHz / 12 instructions per double-float "
                            "multiply-add x 2 flops",
-            "traffic": None, "seconds": round(t, 4), "macs": int(info.peel_update_macs),
-            "launches_per_step": int(sum(1 for l in range(3, info.L + 1) if info.colors[l] > 0) * 2 +
-                                     (1 if info.colors[info.L + 1] > 0 else 0))}
+            "traffic": traffic, "traffic_unit": "dram bytes per launch (ncu, scaled by multiply-adds)",
+            "seconds": round(t, 4), "macs": int(info.peel_update_macs), "launches_per_step": launches}
 
 
 def measure_peaks():
@@ -504,13 +515,17 @@ def run_ours(args):
                                     relerr_iters=None if args.no_relerr else args.relerr_iters)
             modes[name]["precision"] = desc
 
-    # the same job compressed to the uniform H^1 (Section 4.2) and H^2 (Section
-    # 4.3) formats in the bench's precision mode
+    # the same points, kernel and tolerance compressed to the uniform H^1 (Section
+    # 4.2) and H^2 (Section 4.3) formats in the bench's precision mode, with
+    # r = --formats-r: one basis per box holds the box's whole far field, which
+    # needs more sample columns than a per-block basis
     formats = None
     if rank == 0 and world == 1 and not args.no_formats:
-        formats = {}
+        import dataclasses
+        wf = dataclasses.replace(w, r=args.formats_r)
+        formats = {"r": wf.r}
         for name, fv in (("uniform_h1", hm.HM_FORMAT_UNIFORM_H1), ("h2", hm.HM_FORMAT_H2)):
-            formats[name] = time_mode(hm, w, pts, op, PRECISIONS[args.precision][0], rank, steps=3,
+            formats[name] = time_mode(hm, wf, pts, op, PRECISIONS[args.precision][0], rank, steps=3,
                                       relerr_iters=None if args.no_relerr else args.relerr_iters, fmt=fv)
 
     if rank != 0:
