@@ -37,6 +37,7 @@ sys.path.insert(0, ROOT)
 METRIC = "time-to-compress (s) and jobs/s at stated rel. error; p50/p99 latency"
 
 # precision modes: (hm_precision value, description, dtype key of the JSON line)
+FORMATS = {"h1": 0, "uniform_h1": 1, "h2": 2}
 PRECISIONS = {
     "mixed": (1, "split-BF16x6 tensor-core black box; double-float (2 x FP32) peel products with the "
                  "subtraction in FP64; FP64 pivoted QR, Gram products and core solves", "bf16x6-f32acc+df64+f64"),
@@ -54,10 +55,10 @@ PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustain
 # kernel entry, from the ncu capture summarised in profiles/ (scaled by the
 # entries a step evaluates); valid only for the source whose sha256 prefix
 # (full-line comments excluded, see source_sha) is recorded here
-TRAFFIC = {"file": "paper_2205_03406_gb300/csrc/sample_tc.cu", "sha256": "ffc9f6e9401545c1", "bytes_per_eval": 0.5968}
+TRAFFIC = {"file": "paper_2205_03406_gb300/csrc/sample_tc.cu", "sha256": "599b47112ea36534", "bytes_per_eval": 0.5954}
 # DRAM bytes per double-float multiply-add of k_peel_gemm_df from one ncu capture
 # (profiles/), valid while the kernel's source is unchanged
-TRAFFIC_DF = {"file": "paper_2205_03406_gb300/csrc/peel_mixed.cu", "sha256": "", "bytes_per_mac": 0.0}
+TRAFFIC_DF = {"file": "paper_2205_03406_gb300/csrc/peel_mixed.cu", "sha256": "576366b62010b3df", "bytes_per_mac": 0.1502}
 
 
 def parse():
@@ -72,6 +73,9 @@ def parse():
                     help="only measure cuBLAS DGEMM and SGEMM (no TF32) rates on this GPU and print them")
     ap.add_argument("--no-modes", action="store_true",
                     help="skip timing the other two precision modes beside the main line")
+    ap.add_argument("--format", choices=list(FORMATS), default="h1",
+                    help="format of the main line's operator (Algorithm 4.1, Section 4.2 or Section 4.3)")
+    ap.add_argument("--r", type=int, default=0, help="sample columns of the main line (0: the workload's, 32)")
     ap.add_argument("--no-formats", action="store_true",
                     help="skip timing the uniform H^1 and H^2 formats of the same job")
     ap.add_argument("--formats-r", type=int, default=48, help="r of the uniform H^1 and H^2 measurements")
@@ -106,7 +110,7 @@ def workload(n):
 def config_of(args, w):
     return {"workload": f"torus_laplace_{w.n}", "n": w.n, "geometry": "torus R=1 rho=0.3, uniform (u,v)",
             "kernel": "1/(4 pi |x-y|), zero diagonal, on the fly", "leaf_size": w.leaf_size, "tol": w.tol,
-            "r": w.r, "oversample": w.oversample,
+            "r": w.r, "oversample": w.oversample, "format": getattr(args, "format", "h1"),
             "precision": PRECISIONS[args.precision][1],
             "l2": "working set larger than L2 (samples ~5 GB per level); no flush", "seed": w.seed}
 
@@ -402,9 +406,12 @@ def run_ours(args):
             dist.barrier()
 
     w = workload(args.n)
+    if args.r:
+        import dataclasses
+        w = dataclasses.replace(w, r=args.r)
     prec = PRECISIONS[args.precision][0]
     s = hm.Settings(d=3, leaf_size=w.leaf_size, r=w.r, oversample=w.oversample, tol=w.tol, precision=prec,
-                    seed=rank_seed(w.seed, rank))
+                    seed=rank_seed(w.seed, rank), format=FORMATS[args.format])
     stream = torch.cuda.current_stream()
     comp = hm.Compressor(s, stream)
     op = hm.kernel_op(w.kernel)
