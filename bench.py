@@ -96,6 +96,8 @@ def parse():
     ap.add_argument("--sweep-n", type=int, default=1 << 20)
     ap.add_argument("--sweep-tol", type=float, default=1e-4)
     ap.add_argument("--sweep-r", type=int, default=32)
+    ap.add_argument("--sweep-modes", type=str, default="fp64,mixed,mixed-f32",
+                    help="comma-separated precision modes of the sweep, in order (fp64 first: the reference)")
     ap.add_argument("--oracle-series", type=str, default=None,
                     help="comma-separated torus sizes: time the full CPU oracle compression at each (and the "
                          "2048-point 1D dense configuration, best of 3), print one JSON line, exit")
@@ -632,8 +634,13 @@ class OracleSample:
 
 
 def run_sweep(args):
-    """Time-to-compress, relative error (20 power iterations), ranks and storage
-    of one large job in every precision mode, FP64 last (it is the slowest)."""
+    """The large precision configuration: time-to-compress, ranks and storage of
+    one job per precision mode.  The FP64 operator is compressed first and kept;
+    every other mode's error is measured against it, ||A_mode - A_fp64|| /
+    ||A_fp64|| by 20 power iterations on the two compressed operators.  (An
+    exact error against A would need N^2 FP64 kernel evaluations per product:
+    about 25 s each at 2^20 points, 80 products for 20 iterations.)  One JSON
+    line per finished mode, then a summary line."""
     import torch
     import hm_workloads as W
     import paper_2205_03406_gb300 as hm
@@ -642,19 +649,64 @@ def run_sweep(args):
     op = hm.kernel_op(w.kernel)
     out = {"workload": f"sphere_invr_{w.n}", "n": w.n, "kernel": "1/|x-y|", "leaf_size": w.leaf_size,
            "tol": w.tol, "r": w.r, "oversample": w.oversample, "data": "synthetic (seeded jittered Fibonacci sphere)",
+           "error_metric": "||A_mode - A_fp64|| / ||A_fp64||, 20 power iterations on the compressed operators",
            "modes": {}}
-    for name in ("mixed", "mixed-f32", "fp64"):
-        pv, desc, dt = PRECISIONS[name]
+    stream = torch.cuda.current_stream()
+
+    def compress(pv, warm):
+        s = hm.Settings(d=3, leaf_size=w.leaf_size, r=w.r, oversample=w.oversample, tol=w.tol, precision=pv,
+                        seed=w.seed)
+        comp = hm.Compressor(s, stream)
+        if warm:
+            comp.tree_build(pts)
+            comp.compress(op)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        comp.tree_build(pts)
+        comp.compress(op)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        info = comp.info()
+        return comp, {"time_to_compress_s": round(e0.elapsed_time(e1) / 1e3, 3), "warm_up_job": warm,
+                      "floats_per_dof": round(info.factor_floats / w.n, 1), "max_rank": info.max_rank,
+                      "matvec_cols": info.matvec_cols, "bb_tc_levels": info.bb_tc_levels,
+                      "phases_s": {nm: round(info.seconds_phase[i], 3) for i, nm in enumerate(hm.PHASES)}}
+
+    def norm_est(apply, apply_t, iters=20):
+        g = torch.Generator(device="cuda").manual_seed(7)
+        v = torch.randn(w.n, dtype=torch.float64, device="cuda", generator=g)
+        v /= torch.linalg.norm(v)
+        lam = 0.0
+        for _ in range(iters):
+            u = apply_t(apply(v))
+            lam = float(torch.linalg.norm(u))
+            if lam == 0.0:
+                return 0.0
+            v = u / lam
+        return lam ** 0.5
+
+    ref = None
+    for name in args.sweep_modes.split(","):
+        pv, desc, _ = PRECISIONS[name]
         try:
-            # one timed job each; FP64 without a warm-up job (minutes at this size)
-            res = time_mode(hm, w, pts, op, pv, 0, steps=1, relerr_iters=None if args.no_relerr else args.relerr_iters,
-                            warm=name != "fp64")
-            res["warm_up_job"] = name != "fp64"
+            comp, res = compress(pv, warm=name != "fp64")  # FP64 once, without a warm-up job (minutes)
+            if name == "fp64":
+                ref = comp
+            elif ref is not None:
+                num = norm_est(lambda x: comp.apply(x) - ref.apply(x),
+                               lambda y: comp.apply(y, trans=1) - ref.apply(y, trans=1))
+                den = norm_est(lambda x: ref.apply(x), lambda y: ref.apply(y, trans=1))
+                res["rel_error_vs_fp64"] = num / den if den > 0 else None
+                comp.close()
         except hm.HMError as e:  # a mode that does not fit on the device says so
             res = {"error": f"{e}"}
         res["precision"] = desc
         out["modes"][name] = res
-        torch.cuda.empty_cache()
+        # one line per finished mode, so that a limit on the whole run keeps the finished ones
+        print(json.dumps({"sweep_mode": name, "workload": out["workload"], "result": res}), flush=True)
+    if ref is not None:
+        ref.close()
     print(json.dumps(out), flush=True)
 
 
