@@ -93,7 +93,7 @@ def parse():
                     help="only the large precision sweep: a jittered Fibonacci sphere of --sweep-n points, "
                          "K = 1/|x-y|, leaf 64, tol --sweep-tol, r --sweep-r, in the three precision modes; "
                          "one JSON line")
-    ap.add_argument("--sweep-n", type=int, default=1 << 20)
+    ap.add_argument("--sweep-n", type=int, default=1 << 20)  # 2^19 fits every mode's peel tables
     ap.add_argument("--sweep-tol", type=float, default=1e-4)
     ap.add_argument("--sweep-r", type=int, default=32)
     ap.add_argument("--sweep-modes", type=str, default="fp64,mixed,mixed-f32",
@@ -686,11 +686,28 @@ def run_sweep(args):
             v = u / lam
         return lam ** 0.5
 
+    # exact A x on a random sample of rows, in FP64 from the point differences
+    # (N kernel evaluations per row): the error of every mode against A itself
+    gen = torch.Generator(device="cuda").manual_seed(11)
+    xv = torch.randn(w.n, dtype=torch.float64, device="cuda", generator=gen)
+    rows = torch.randperm(w.n, device="cuda", generator=gen)[:4096]
+    xr = pts[rows]
+    exact = torch.zeros(rows.numel(), dtype=torch.float64, device="cuda")
+    for c0 in range(0, w.n, 8192):
+        d = xr[:, None, :] - pts[None, c0:c0 + 8192, :]
+        dist = torch.sqrt((d * d).sum(-1))
+        kij = torch.where(dist > 0, 1.0 / torch.where(dist > 0, dist, torch.ones_like(dist)), torch.zeros_like(dist))
+        exact += kij @ xv[c0:c0 + 8192]
+    out["sampled_rows"] = int(rows.numel())
+    out["error_metric_rows"] = "||(A x - A~ x)(S)|| / ||(A x)(S)||, x Gaussian, S 4096 random rows, A x exact in FP64"
+
     ref = None
     for name in args.sweep_modes.split(","):
         pv, desc, _ = PRECISIONS[name]
         try:
             comp, res = compress(pv, warm=name != "fp64")  # FP64 once, without a warm-up job (minutes)
+            ya = comp.apply(xv)[rows]
+            res["rel_error_rows"] = float(torch.linalg.norm(ya - exact) / torch.linalg.norm(exact))
             if name == "fp64":
                 ref = comp
             elif ref is not None:

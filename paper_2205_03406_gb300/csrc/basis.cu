@@ -582,75 +582,80 @@ __global__ void k_ts_fill(const int *tile_alpha, const int *ent, const int64_t *
 
 // (1) unpivoted QR of one block; R_b (r x r, zero below the diagonal) into
 // the stack at [blk][r][r], the reflectors over the block, tau at [blk][r]
+template <typename T>
 __global__ void __launch_bounds__(512) k_ts_block(const int *tile_alpha, const int *tile_color, const int *ent,
                                                   int64_t n, int r, double *Ybase, const int64_t *blk_tile,
-                                                  const int *blk_row0, const int *blk_rows, float *Rstack,
-                                                  float *taus) {
-    extern __shared__ float qa[];
-    __shared__ float red[16][64], nrm[64], wv[64];
+                                                  const int *blk_row0, const int *blk_rows, T *Rstack, T *taus) {
+    extern __shared__ __align__(16) unsigned char ts_raw[];
+    T *qa = reinterpret_cast<T *>(ts_raw);
+    __shared__ T red[16][64], nrm[64], wv[64];
     const int64_t blk = blockIdx.x;
     const int64_t p = blk_tile[blk];
     const int *e = ent + (int64_t)tile_alpha[p] * ENT_FIELDS;
     const int m = blk_rows[blk], t = threadIdx.x;
     double *Ag = Ybase + ((int64_t)tile_color[p] * n + e[3] + blk_row0[blk]) * r;
-    for (int o = t; o < m * r; o += blockDim.x) qa[o] = (float)Ag[o];
+    for (int o = t; o < m * r; o += blockDim.x) qa[o] = (T)Ag[o];
     __syncthreads();
     const int steps = min(m, r);
     for (int s = 0; s < steps; ++s) {
         col_dots(qa, m, r, s, 0, s, s + 1, true, red, nrm);
-        const float nv = sqrtf(nrm[s]), x0 = qa[s * r + s];
-        float ts = 0.0f, b = 0.0f, sc = 0.0f;
-        if (nv > 0.0f) {
-            b = -copysignf(nv, x0);
+        const T nv = sqrt(nrm[s]), x0 = qa[s * r + s];
+        T ts = T(0), b = T(0), sc = T(0);
+        if (nv > T(0)) {
+            b = -copysign(nv, x0);
             ts = (b - x0) / b;
-            sc = 1.0f / (x0 - b);
+            sc = T(1) / (x0 - b);
         }
         for (int i = s + 1 + t; i < m; i += blockDim.x) qa[i * r + s] *= sc;
         __syncthreads();
         if (t == 0) {
             taus[blk * r + s] = ts;
-            if (nv > 0.0f) qa[s * r + s] = b;
+            if (nv > T(0)) qa[s * r + s] = b;
         }
         col_dots(qa, m, r, s + 1, s, s + 1, r, false, red, wv);
         if (t > s && t < r) wv[t] += qa[s * r + t];
         __syncthreads();
         reflect(qa, m, r, s, r, ts, wv);
     }
-    for (int s = steps + t; s < r; s += blockDim.x) taus[blk * r + s] = 0.0f;
-    float *R = Rstack + blk * r * r;
+    for (int s = steps + t; s < r; s += blockDim.x) taus[blk * r + s] = T(0);
+    T *R = Rstack + blk * r * r;
     for (int o = t; o < r * r; o += blockDim.x) {
         const int i = o / r, j = o % r;
-        R[o] = (i <= j && i < m) ? qa[i * r + j] : 0.0f;
+        R[o] = (i <= j && i < m) ? qa[i * r + j] : T(0);
     }
     for (int o = t; o < m * r; o += blockDim.x) Ag[o] = (double)qa[o];
 }
 
 // (2) pivoted QR of the stacked R_b of one tile, in place in the stack
+template <typename T>
 __global__ void __launch_bounds__(512) k_ts_top(const int *tile_alpha, const int *tile_beta, const int *ent,
                                                 int64_t np, int r, int cap, int rank, double tol, const int64_t *off,
-                                                float *Rstack, int *kout) {
-    extern __shared__ float qa[];
+                                                T *Rstack, int *kout, const int *tile_cap = nullptr) {
+    extern __shared__ __align__(16) unsigned char ts_raw[];
+    T *qa = reinterpret_cast<T *>(ts_raw);
     const int64_t p = blockIdx.x;
     const int nb = (int)(off[p + 1] - off[p]);
     if (nb == 0) return;
     const int *e = ent + (int64_t)tile_alpha[p] * ENT_FIELDS, *eb = ent + (int64_t)tile_beta[p] * ENT_FIELDS;
     const int m = e[4] - e[3], ms = nb * r;
-    const int kmax = min(min(m, eb[4] - eb[3]), min(r, cap));
-    float *S = Rstack + off[p] * r * r;
+    const int kmax = min(min(min(m, eb[4] - eb[3]), min(r, cap)), tile_cap ? tile_cap[p] : r);
+    T *S = Rstack + off[p] * r * r;
     for (int o = threadIdx.x; o < ms * r; o += blockDim.x) qa[o] = S[o];
     __syncthreads();
-    const int k = qr_pivoted_smem<float>(qa, ms, r, kmax, rank, tol);
+    const int k = qr_pivoted_smem<T>(qa, ms, r, kmax, rank, tol);
     for (int o = threadIdx.x; o < ms * r; o += blockDim.x) S[o] = qa[o];
     if (threadIdx.x == 0) kout[p] = k;
 }
 
 // (3) U_b = Q_b [Q_S(block rows, 0:k); 0] into the block's rows, columns 0..k-1
+template <typename T>
 __global__ void __launch_bounds__(512) k_ts_form(const int *tile_alpha, const int *tile_color, const int *ent,
                                                  int64_t n, int r, double *Ybase, const int64_t *blk_tile,
-                                                 const int *blk_row0, const int *blk_rows, const float *Rstack,
-                                                 const float *taus, const int *kout) {
-    extern __shared__ float qa[];  // reflectors m x r, then X m x k (ld r)
-    __shared__ float red[16][64], wv[64];
+                                                 const int *blk_row0, const int *blk_rows, const T *Rstack,
+                                                 const T *taus, const int *kout) {
+    extern __shared__ __align__(16) unsigned char ts_raw[];
+    T *qa = reinterpret_cast<T *>(ts_raw);  // reflectors m x r, then X m x k (ld r)
+    __shared__ T red[16][64], wv[64];
     const int64_t blk = blockIdx.x;
     const int64_t p = blk_tile[blk];
     const int k = kout[p];
@@ -658,33 +663,33 @@ __global__ void __launch_bounds__(512) k_ts_form(const int *tile_alpha, const in
     const int *e = ent + (int64_t)tile_alpha[p] * ENT_FIELDS;
     const int m = blk_rows[blk], t = threadIdx.x;
     double *Ag = Ybase + ((int64_t)tile_color[p] * n + e[3] + blk_row0[blk]) * r;
-    float *X = qa + m * r;
-    const float *QS = Rstack + blk * r * r;  // this block's r rows of Q_S
+    T *X = qa + m * r;
+    const T *QS = Rstack + blk * r * r;  // this block's r rows of Q_S
     for (int o = t; o < m * r; o += blockDim.x) {
         const int i = o / r, j = o % r;
-        qa[o] = (float)Ag[o];
-        X[o] = (j < k && i < r) ? QS[i * r + j] : 0.0f;
+        qa[o] = (T)Ag[o];
+        X[o] = (j < k && i < r) ? QS[i * r + j] : T(0);
     }
     __syncthreads();
     const int steps = min(m, r);
     for (int s = steps - 1; s >= 0; --s) {
-        const float ts = taus[blk * r + s];
+        const T ts = taus[blk * r + s];
         // w_c = X(s, c) + sum_{i > s} v_i X(i, c); X(i, c) -= tau v_i w_c
         const int RP = r <= 32 ? 32 : 64, NG = (int)blockDim.x / RP, cj = t % RP, grp = t / RP;
-        float a = 0.0f;
+        T a = T(0);
         if (cj < k)
-            for (int i = s + 1 + grp; i < m; i += NG) a = fmaf(qa[i * r + s], X[i * r + cj], a);
+            for (int i = s + 1 + grp; i < m; i += NG) a = fma(qa[i * r + s], X[i * r + cj], a);
         red[grp][cj] = a;
         __syncthreads();
         if (t < k) {
-            float w = X[s * r + t];
+            T w = X[s * r + t];
             for (int g = 0; g < NG; ++g) w += red[g][t];
             wv[t] = ts * w;
         }
         __syncthreads();
         if (cj < k)
             for (int i = s + grp; i < m; i += NG) {
-                const float vi = (i == s) ? 1.0f : qa[i * r + s];
+                const T vi = (i == s) ? T(1) : qa[i * r + s];
                 X[i * r + cj] -= vi * wv[cj];
             }
         __syncthreads();
@@ -871,6 +876,23 @@ static Err launch_core(int64_t np, int nsplit, int r, int kc, cudaStream_t st, c
     return ok();
 }
 
+// the three tall-skinny QR launches of one side (block QRs, pivoted QR of each
+// tile's stacked R, composition of Q) in element type T
+template <typename T>
+static void launch_ts(const int *tile_box, const int *tile_beta, const int *tile_color, const int *tile_cap,
+                      const int *ent, int64_t n, int r, int cap, int rank, double tol, double *Y, int *kk, int64_t np,
+                      int64_t nblk, int nb_top, int ts_rows, const DBuf &ts_off, const DBuf &blk_tile,
+                      const DBuf &blk_row0, const DBuf &blk_rows, DBuf &rstack, DBuf &taus, cudaStream_t st) {
+    k_ts_block<T><<<(unsigned)nblk, 512, (size_t)ts_rows * r * sizeof(T), st>>>(
+        tile_box, tile_color, ent, n, r, Y, blk_tile.as<int64_t>(), blk_row0.as<int>(), blk_rows.as<int>(),
+        rstack.as<T>(), taus.as<T>()); ::hm::count_launch();
+    k_ts_top<T><<<(unsigned)np, 512, (size_t)nb_top * r * r * sizeof(T), st>>>(
+        tile_box, tile_beta, ent, np, r, cap, rank, tol, ts_off.as<int64_t>(), rstack.as<T>(), kk, tile_cap); ::hm::count_launch();
+    k_ts_form<T><<<(unsigned)nblk, 512, (size_t)2 * ts_rows * r * sizeof(T), st>>>(
+        tile_box, tile_color, ent, n, r, Y, blk_tile.as<int64_t>(), blk_row0.as<int>(), blk_rows.as<int>(),
+        rstack.as<T>(), taus.as<T>(), kk); ::hm::count_launch();
+}
+
 Err qr_tiles_fp64(hm_ctx *c, int level, const int *tile_box, const int *tile_color, const int *tile_cap, int64_t nt,
                   int max_rows, double *base, int cap, int rank, double tol, int *kout) {
     if (nt == 0) return ok();
@@ -888,9 +910,39 @@ Err qr_tiles_fp64(hm_ctx *c, int level, const int *tile_box, const int *tile_col
         k_qr_smem<double><<<(unsigned)nt, 512, smem, st>>>(tile_box, tile_box, tile_color, ent, n, r, cap, rank, tol,
                                                            base, kout, QR_WARP_ROWS, qr64_rows, tile_cap); ::hm::count_launch();
     }
-    if (max_rows > qr64_rows)
+    // taller tiles: the FP64 tall-skinny QR up to ts_max rows (each tile read
+    // once; these QRs run to full width, r columns, so the tall-skinny blocks
+    // add little FP64 work), the streaming block kernel beyond
+    const int ts_rows = (200 * 1024) / (16 * r) / 32 * 32, ts_max = (200 * 1024) / (8 * r * r) * ts_rows;
+    if (max_rows > qr64_rows && ts_max > qr64_rows) {
+        DBuf ts_cnt, ts_off, blk_tile, blk_row0, blk_rows, rstack, taus;
+        int64_t nblk = 0;
+        HM_TRY(alloc(ts_cnt, (nt + 1) * sizeof(int64_t)));
+        HM_TRY(alloc(ts_off, (nt + 1) * sizeof(int64_t)));
+        k_ts_count<<<ceil_div(nt, 256), 256, 0, st>>>(tile_box, ent, nt, qr64_rows, ts_max, ts_rows,
+                                                      ts_cnt.as<int64_t>()); ::hm::count_launch();
+        HM_TRY(scan_exclusive(ts_cnt.as<int64_t>(), ts_off.as<int64_t>(), nt, st));
+        HM_TRY(read_scalar(nblk, ts_off.as<int64_t>() + nt, st));
+        if (nblk > 0) {
+            HM_TRY(alloc(blk_tile, nblk * sizeof(int64_t)));
+            HM_TRY(alloc(blk_row0, nblk * sizeof(int)));
+            HM_TRY(alloc(blk_rows, nblk * sizeof(int)));
+            HM_TRY(alloc(rstack, (size_t)nblk * r * r * sizeof(double)));
+            HM_TRY(alloc(taus, (size_t)nblk * r * sizeof(double)));
+            k_ts_fill<<<ceil_div(nt, 256), 256, 0, st>>>(tile_box, ent, ts_off.as<int64_t>(), nt,
+                                                         blk_tile.as<int64_t>(), blk_row0.as<int>(),
+                                                         blk_rows.as<int>()); ::hm::count_launch();
+            const int nb_top = ceil_div(std::min(max_rows, ts_max), ts_rows);
+            HM_TRY(allow_smem(k_ts_block<double>, (size_t)ts_rows * r * sizeof(double)));
+            HM_TRY(allow_smem(k_ts_top<double>, (size_t)nb_top * r * r * sizeof(double)));
+            HM_TRY(allow_smem(k_ts_form<double>, (size_t)2 * ts_rows * r * sizeof(double)));
+            launch_ts<double>(tile_box, tile_box, tile_color, tile_cap, ent, n, r, cap, rank, tol, base, kout, nt,
+                              nblk, nb_top, ts_rows, ts_off, blk_tile, blk_row0, blk_rows, rstack, taus, st);
+        }
+    }
+    if (max_rows > std::max(qr64_rows, ts_max))
         k_qr_tiles<<<(unsigned)nt, 256, 0, st>>>(tile_box, tile_box, tile_color, ent, n, r, cap, rank, tol, base, kout,
-                                                 qr64_rows, tile_cap); ::hm::count_launch();
+                                                 std::max(qr64_rows, ts_max), tile_cap); ::hm::count_launch();
     HM_LAUNCH("qr_tiles_fp64");
     return ok();
 }
@@ -936,13 +988,20 @@ Err bases_and_cores(hm_ctx *c, int level) {
     // kernel, tiles up to ts_max rows by the FP32 tall-skinny QR, larger ones
     // by the FP64 block kernel.  FP64 modes: the warp kernel up to QR_WARP_ROWS
     // rows, the FP64 shared-memory kernel up to qr64_rows (200 KB of tile), the
-    // block kernel beyond.
+    // block kernel beyond.  Tall-skinny blocks: the block and its composed Q
+    // fit 200 KB of shared memory; the stacked R of a tile does too.
     const bool mixed = c->cfg.precision == HM_MIXED_BF16X6_F32;
+    const int esz = mixed ? (int)sizeof(float) : (int)sizeof(double);
     const int qr32_rows = mixed ? std::min(QR32_MAX_ROWS, (200 * 1024) / (4 * r)) : 0;
     const int qr64_rows = mixed ? 0 : (200 * 1024) / (8 * r);
-    const int ts_rows = (200 * 1024) / (8 * r) / 32 * 32;       // rows per tall-skinny block
-    const int ts_max = mixed ? (200 * 1024) / (4 * r * r) * ts_rows : 0;
-    const int small_rows = mixed ? std::max(qr32_rows, ts_max) : std::max(QR_WARP_ROWS, qr64_rows);
+    const int ts_rows = (200 * 1024) / (2 * esz * r) / 32 * 32;  // rows per tall-skinny block
+    // FP64 modes keep the direct pivoted QR on their tall tiles: the tall-skinny
+    // blocks factor all r columns and form Q from r reflectors, about twice the
+    // FP64 work of a pivoted QR that stops at k, which costs more on this GPU's
+    // FP64 pipe than the tile re-reads it saves (measured on the 200k torus)
+    const int ts_max = mixed ? (200 * 1024) / (esz * r * r) * ts_rows : 0;
+    const int ts_min = mixed ? qr32_rows : std::max(QR_WARP_ROWS, qr64_rows);
+    const int small_rows = std::max(ts_min, ts_max);
     const size_t qr32_smem = (size_t)std::max(1, std::min(qr32_rows, cu.max_rows)) * r * sizeof(float);
     const size_t qr64_smem = (size_t)std::max(1, std::min(qr64_rows, cu.max_rows)) * r * sizeof(double);
     if (mixed)
@@ -953,10 +1012,10 @@ Err bases_and_cores(hm_ctx *c, int level) {
     DBuf ts_cnt, ts_off, blk_tile, blk_row0, blk_rows, rstack, taus;
     int64_t nblk = 0;
     int nb_top = 0;
-    if (mixed && cu.max_rows > qr32_rows) {
+    if (cu.max_rows > ts_min && ts_max > ts_min) {
         HM_TRY(alloc(ts_cnt, (np + 1) * sizeof(int64_t)));
         HM_TRY(alloc(ts_off, (np + 1) * sizeof(int64_t)));
-        k_ts_count<<<ceil_div(np, 256), 256, 0, st>>>(g.pair_alpha.as<int>(), cu.ent.as<int>(), np, qr32_rows, ts_max,
+        k_ts_count<<<ceil_div(np, 256), 256, 0, st>>>(g.pair_alpha.as<int>(), cu.ent.as<int>(), np, ts_min, ts_max,
                                                       ts_rows, ts_cnt.as<int64_t>()); ::hm::count_launch();
         HM_TRY(scan_exclusive(ts_cnt.as<int64_t>(), ts_off.as<int64_t>(), np, st));
         HM_TRY(read_scalar(nblk, ts_off.as<int64_t>() + np, st));
@@ -964,16 +1023,22 @@ Err bases_and_cores(hm_ctx *c, int level) {
             HM_TRY(alloc(blk_tile, nblk * sizeof(int64_t)));
             HM_TRY(alloc(blk_row0, nblk * sizeof(int)));
             HM_TRY(alloc(blk_rows, nblk * sizeof(int)));
-            HM_TRY(alloc(rstack, (size_t)nblk * r * r * sizeof(float)));
-            HM_TRY(alloc(taus, (size_t)nblk * r * sizeof(float)));
+            HM_TRY(alloc(rstack, (size_t)nblk * r * r * esz));
+            HM_TRY(alloc(taus, (size_t)nblk * r * esz));
             k_ts_fill<<<ceil_div(np, 256), 256, 0, st>>>(g.pair_alpha.as<int>(), cu.ent.as<int>(), ts_off.as<int64_t>(),
                                                          np, blk_tile.as<int64_t>(), blk_row0.as<int>(),
                                                          blk_rows.as<int>()); ::hm::count_launch();
             HM_LAUNCH("ts_fill");
             nb_top = ceil_div(std::min(cu.max_rows, ts_max), ts_rows);
-            HM_TRY(allow_smem(k_ts_block, (size_t)((int)(ts_rows * r * sizeof(float)))));
-            HM_TRY(allow_smem(k_ts_top, (size_t)((int)((size_t)nb_top * r * r * sizeof(float)))));
-            HM_TRY(allow_smem(k_ts_form, (size_t)((int)(2 * ts_rows * r * sizeof(float)))));
+            if (mixed) {
+                HM_TRY(allow_smem(k_ts_block<float>, (size_t)ts_rows * r * esz));
+                HM_TRY(allow_smem(k_ts_top<float>, (size_t)nb_top * r * r * esz));
+                HM_TRY(allow_smem(k_ts_form<float>, (size_t)2 * ts_rows * r * esz));
+            } else {
+                HM_TRY(allow_smem(k_ts_block<double>, (size_t)ts_rows * r * esz));
+                HM_TRY(allow_smem(k_ts_top<double>, (size_t)nb_top * r * r * esz));
+                HM_TRY(allow_smem(k_ts_form<double>, (size_t)2 * ts_rows * r * esz));
+            }
         }
     }
     for (int side = 0; side < 2; ++side) {
@@ -984,19 +1049,14 @@ Err bases_and_cores(hm_ctx *c, int level) {
                                                 cu.ent.as<int>(), n, r, cap, c->rank_fixed, c->tol, T, kk,
                                                 small_rows); ::hm::count_launch();
         }
+        if (nblk > 0) {
+            (mixed ? launch_ts<float> : launch_ts<double>)(
+                g.pair_alpha.as<int>(), cu.int_idx.as<int>(), g.pair_color.as<int>(), nullptr, cu.ent.as<int>(), n,
+                r, cap, c->rank_fixed, c->tol, T, kk, np, nblk, nb_top, ts_rows, ts_off, blk_tile, blk_row0,
+                blk_rows, rstack, taus, st);
+            HM_LAUNCH("tall-skinny qr");
+        }
         if (mixed) {
-            if (nblk > 0) {
-                k_ts_block<<<(unsigned)nblk, 512, ts_rows * r * sizeof(float), st>>>(
-                    g.pair_alpha.as<int>(), g.pair_color.as<int>(), cu.ent.as<int>(), n, r, T, blk_tile.as<int64_t>(),
-                    blk_row0.as<int>(), blk_rows.as<int>(), rstack.as<float>(), taus.as<float>()); ::hm::count_launch();
-                k_ts_top<<<(unsigned)np, 512, (size_t)nb_top * r * r * sizeof(float), st>>>(
-                    g.pair_alpha.as<int>(), cu.int_idx.as<int>(), cu.ent.as<int>(), np, r, cap, c->rank_fixed,
-                    c->tol, ts_off.as<int64_t>(), rstack.as<float>(), kk); ::hm::count_launch();
-                k_ts_form<<<(unsigned)nblk, 512, 2 * ts_rows * r * sizeof(float), st>>>(
-                    g.pair_alpha.as<int>(), g.pair_color.as<int>(), cu.ent.as<int>(), n, r, T, blk_tile.as<int64_t>(),
-                    blk_row0.as<int>(), blk_rows.as<int>(), rstack.as<float>(), taus.as<float>(), kk); ::hm::count_launch();
-                HM_LAUNCH("tall-skinny qr");
-            }
             // tiles up to 256 rows with 128 threads, taller ones with 512
             k_qr_smem<float><<<(int)np, 128, qr32_smem, st>>>(g.pair_alpha.as<int>(), cu.int_idx.as<int>(),
                                                     g.pair_color.as<int>(), cu.ent.as<int>(), n, r, cap, c->rank_fixed,

@@ -127,8 +127,9 @@ __global__ void k_rmat(int64_t nt, const int *tiles, const int *ent, const int *
 
 // One-sided Jacobi SVD of R_p (kq rows, r columns) in shared memory: cyclic
 // sweeps in round-robin order (r/2 disjoint column pairs per round, one warp
-// each) rotate every pair whose inner product exceeds thresh sqrt(a b) until a
-// sweep rotates none (at most JAC_SWEEPS).  Then sigma_j = |column j|, sorted
+// each) rotate every pair whose inner product exceeds thresh sqrt(a b) (pairs
+// with a negligible column excepted) until a sweep rotates none (at most
+// JAC_SWEEPS).  Then sigma_j = |column j|, sorted
 // in decreasing order (lower index first on ties); W_p(:, q) = column / sigma
 // (zero where sigma is 0); k by the rank or tolerance rule.
 __global__ void __launch_bounds__(JAC_THREADS) k_jacobi(int64_t nt, const int *tiles, const int *ent, const int *kq,
@@ -151,7 +152,23 @@ __global__ void __launch_bounds__(JAC_THREADS) k_jacobi(int64_t nt, const int *t
     }
     __syncthreads();
     const int rr = r + (r & 1);  // a padding column when r is odd
-    const double thresh = 1e-15 * sqrt((double)(kr > 0 ? kr : 1));
+    // a pair is orthogonal once |a_p . a_q| <= thresh |a_p| |a_q| with thresh
+    // above the rounding of a kr-term dot product; a column whose squared norm
+    // is below 1e-30 of |R|_F^2 (invariant under the rotations) lies far below
+    // any truncation and is not rotated
+    const double thresh = 4e-16 * (double)(kr > 0 ? kr : 1);
+    if (tid < 32) {
+        double f = 0.0;
+        for (int o = tid; o < r * kr; o += 32) {
+            const double v = A[(o / kr) * MAXR + o % kr];
+            f = fma(v, v, f);
+        }
+        for (int o = 16; o > 0; o >>= 1) f += __shfl_xor_sync(0xffffffffu, f, o);
+        if (tid == 0) nrm[0] = f;
+    }
+    __syncthreads();
+    const double negligible = 1e-30 * nrm[0];
+    __syncthreads();
     for (int sweep = 0; sweep < JAC_SWEEPS; ++sweep) {
         if (tid == 0) rotated = 0;
         __syncthreads();
@@ -173,7 +190,7 @@ __global__ void __launch_bounds__(JAC_THREADS) k_jacobi(int64_t nt, const int *t
                     b += __shfl_xor_sync(0xffffffffu, b, o);
                     g += __shfl_xor_sync(0xffffffffu, g, o);
                 }
-                if (!(a > 0.0 && b > 0.0) || !(fabs(g) > thresh * sqrt(a * b))) continue;
+                if (!(a > negligible && b > negligible) || !(fabs(g) > thresh * sqrt(a * b))) continue;
                 const double zeta = (b - a) / (2.0 * g);
                 double t;
                 if (fabs(zeta) > 1e150) t = 0.5 / zeta;
