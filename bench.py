@@ -58,7 +58,7 @@ PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustain
 TRAFFIC = {"file": "paper_2205_03406_gb300/csrc/sample_tc.cu", "sha256": "599b47112ea36534", "bytes_per_eval": 0.5954}
 # DRAM bytes per double-float multiply-add of k_peel_gemm_df from one ncu capture
 # (profiles/), valid while the kernel's source is unchanged
-TRAFFIC_DF = {"file": "paper_2205_03406_gb300/csrc/peel_mixed.cu", "sha256": "576366b62010b3df", "bytes_per_mac": 0.1502}
+TRAFFIC_DF = {"file": "paper_2205_03406_gb300/csrc/peel_mixed.cu", "sha256": "4b23cb547b30be69", "bytes_per_mac": 0.1502}
 
 
 def parse():

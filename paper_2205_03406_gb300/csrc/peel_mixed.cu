@@ -21,8 +21,8 @@
 // the factors and Gaussians, and subtracts the result from the FP64 samples in
 // FP64.  Its update kernel (k_peel_gemm_df) reads compacted records of the live
 // T slots (written by k_peel_T) and stages the next slot's F and T rows in
-// shared memory with cp.async while the current one multiplies.  HM_FP64 keeps
-// FP64 products (k_peel_gemm64).
+// shared memory with cp.async while the current one multiplies.  HM_FP64 runs
+// the same compacted records and update kernel with FP64 elements.
 #include "ctx.cuh"
 #include "df.cuh"
 
@@ -321,109 +321,32 @@ __global__ void __launch_bounds__(128) k_peel_gemm(const Coarse *cl, int ncl, in
     }
 }
 
-// FP64 variant (HM_FP64 and HM_MIXED_BF16X6): one CTA of 128 threads per
-// 32-row chunk of a tile (FP64 arithmetic is the bound, so fewer padding rows
-// than the FP32 kernel's 64); thread (rg, cg) owns rows 4 rg .. 4 rg + 3 and
-// columns cg CW .. cg CW + CW - 1 (CW = MAXC / 16); F' and T staged in
-// dynamic shared memory (kcap x 36 and kcap x MAXC doubles).
+// rows per work item of the compact update, and the leading dimension of its
+// staged F' rows
 constexpr int GEMM64_ROWS = 32, GEMM64_LDF = 36;
 
-template <int MAXC>
-__global__ void __launch_bounds__(128) k_peel_gemm64(const CoarseT<double> *cl, int ncl, int side, int chi,
-                                                     const int *tile_alpha, const int *tile_color, const int *entl,
-                                                     const int64_t *item_tile, const int *item_row, int64_t nitems,
-                                                     int cols, int kcap, int64_t n, double *OUT) {
-    constexpr int CW = MAXC / 16;
-    extern __shared__ __align__(16) unsigned char sm64_raw[];
-    double *Fs = reinterpret_cast<double *>(sm64_raw);  // kcap x GEMM64_LDF
-    double *Ts = Fs + kcap * GEMM64_LDF;                  // kcap x MAXC
-    const int64_t item = blockIdx.x;
-    if (item >= nitems) return;
-    const int tid = threadIdx.x, rg = tid >> 4, cg = tid & 15;
-    const int64_t p = item_tile[item];
-    const int alpha = tile_alpha[p], c = tile_color[p];
-    const int *ea = entl + (int64_t)alpha * ENT_FIELDS;
-    const int sa = ea[3] + item_row[item];
-    const int rows = min(GEMM64_ROWS, ea[4] - sa);
-    double acc[4][CW];
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < CW; ++j) acc[i][j] = 0.0;
-    for (int lvl = 0; lvl < ncl; ++lvl) {
-        const CoarseT<double> &C = cl[lvl];
-        const int A = C.pt2ent[sa];
-        const int anc_start = C.ent[(int64_t)A * ENT_FIELDS + 3];
-        const int t0 = C.int_ptr[A], t1 = C.int_ptr[A + 1];
-        const int64_t s0 = C.base[(int64_t)A * chi + c];
-        for (int t = t0; t < t1; ++t) {
-            const int64_t slot = s0 + (t - t0);
-            if (!C.live[slot]) continue;  // uniform over the CTA
-            const int q = side ? C.pairT[t] : t;
-            const int kout = side ? C.kV[q] : C.kU[q];
-            const double *F = (side ? C.V + C.offV[q] : C.U + C.offU[q]) + (int64_t)(sa - anc_start) * kout;
-            const double *Tq = C.T + slot * kcap * cols;
-            __syncthreads();  // the previous step's reads of Fs / Ts are done
-            for (int o = tid; o < GEMM64_ROWS * kout; o += 128) {
-                const int row = o / kout, u = o % kout;
-                Fs[u * GEMM64_LDF + row] = row < rows ? F[o] : 0.0;
-            }
-            for (int o = tid; o < kout * MAXC; o += 128) {
-                const int u = o / MAXC, col = o % MAXC;
-                Ts[o] = col < cols ? Tq[u * cols + col] : 0.0;
-            }
-            __syncthreads();
-            for (int u = 0; u < kout; ++u) {
-                const double2 f01 = *reinterpret_cast<const double2 *>(&Fs[u * GEMM64_LDF + rg * 4]);
-                const double2 f23 = *reinterpret_cast<const double2 *>(&Fs[u * GEMM64_LDF + rg * 4 + 2]);
-                const double fv[4] = {f01.x, f01.y, f23.x, f23.y};
-                double tv[CW];
-#pragma unroll
-                for (int j2 = 0; j2 < CW / 2; ++j2) {
-                    const double2 x = *reinterpret_cast<const double2 *>(&Ts[u * MAXC + cg * CW + 2 * j2]);
-                    tv[2 * j2] = x.x;
-                    tv[2 * j2 + 1] = x.y;
-                }
-#pragma unroll
-                for (int i = 0; i < 4; ++i)
-#pragma unroll
-                    for (int j = 0; j < CW; ++j) acc[i][j] = fma(fv[i], tv[j], acc[i][j]);
-            }
-        }
-    }
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const int row = rg * 4 + i;
-        if (row >= rows) continue;
-        double *out = OUT + ((int64_t)c * n + sa + row) * cols;
-#pragma unroll
-        for (int j = 0; j < CW; ++j) {
-            const int col = cg * CW + j;
-            if (col < cols) out[col] -= acc[i][j];
-        }
-    }
-}
-
 // ---------------------------------------------------------------------------
-// Double-float update (HM_MIXED_BF16X6).  One CTA of 128 threads per 32-row
+// Compact update: double-float elements (HM_MIXED_BF16X6) or FP64 elements
+// (HM_FP64), E.  One CTA of 128 threads per 32-row
 // chunk of a tile (alpha, c): the steps are the live T slots of the chunk's
 // ancestors at every coarse level (the records k_peel_T compacted), each a
 // product F'(rows, 0:kout) T (kout x cols).  Step s + 1's F rows (row-major, a
 // flat copy) and T are copied into the other shared-memory stage with
 // cp.async while step s multiplies; thread (rg, cg) owns rows 4 rg .. 4 rg + 3 and columns
-// cg CW .. cg CW + CW - 1 (CW = MAXC / 16) in double-float accumulators, and
-// the FP64 tile -= hi + lo at the end.  macs (optional) receives the
+// cg CW .. cg CW + CW - 1 (CW = MAXC / 16) in accumulators of type E, and the
+// FP64 tile -= the accumulated value at the end.  macs (optional) receives the
 // multiply-adds of the valid rows and columns.
 // ---------------------------------------------------------------------------
 
-struct CoarseDF {
+template <typename E> struct CoarseC {
     const int *ent, *pt2ent;
     const int64_t *base;   // [nc_j * chi + 1]: first record of (A, c)
     const int *cnt;        // [nc_j * chi]: live records of (A, c)
     const PeelRec *rec;
-    const dfloat *F;       // U (Y side) or V (Z side) arena
-    const dfloat *T;       // [slots][kcap][cols]
+    const E *F;            // U (Y side) or V (Z side) arena
+    const E *T;            // compact T rows
 };
+using CoarseDF = CoarseC<dfloat>;
 
 constexpr int DF_MAXLV = MAX_LEVELS;
 
@@ -437,16 +360,16 @@ template <int N> __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
-template <int MAXC>
-__global__ void __launch_bounds__(128) k_peel_gemm_df(const CoarseDF *cl, int ncl, int chi, const int *tile_alpha,
+template <int MAXC, typename E>
+__global__ void __launch_bounds__(128) k_peel_gemm_df(const CoarseC<E> *cl, int ncl, int chi, const int *tile_alpha,
                                                       const int *tile_color, const int *entl, const int64_t *item_tile,
                                                       const int *item_row, int64_t nitems, int cols, int kcap,
                                                       int64_t n, double *OUT, unsigned long long *macs) {
     constexpr int CW = MAXC / 16;
     constexpr int LDF = GEMM64_LDF;
     extern __shared__ __align__(16) unsigned char smdf_raw[];
-    dfloat *Fs = reinterpret_cast<dfloat *>(smdf_raw);  // [2][kcap][LDF]: F' transposed
-    dfloat *Ts = Fs + 2 * kcap * LDF;                    // [2][kcap][MAXC]
+    E *Fs = reinterpret_cast<E *>(smdf_raw);  // [2][kcap][LDF]: F' transposed
+    E *Ts = Fs + 2 * kcap * LDF;               // [2][kcap][MAXC]
     __shared__ int lv_first[DF_MAXLV + 1], lv_n[DF_MAXLV], lv_rowoff[DF_MAXLV];
     __shared__ int64_t lv_s0[DF_MAXLV];
     const int64_t item = blockIdx.x;
@@ -458,7 +381,7 @@ __global__ void __launch_bounds__(128) k_peel_gemm_df(const CoarseDF *cl, int nc
     const int sa = ea[3] + item_row[item];
     const int rows = min(GEMM64_ROWS, ea[4] - sa);
     if (tid < ncl) {  // ancestor of the chunk at coarse level tid: its records
-        const CoarseDF &C = cl[tid];
+        const CoarseC<E> &C = cl[tid];
         const int A = C.pt2ent[sa];
         const int64_t e = (int64_t)A * chi + c;
         lv_s0[tid] = C.base[e];
@@ -477,30 +400,30 @@ __global__ void __launch_bounds__(128) k_peel_gemm_df(const CoarseDF *cl, int nc
     auto issue = [&](int s, int b) -> int {
         int lv = 0;
         while (s >= lv_first[lv + 1]) ++lv;
-        const CoarseDF &C = cl[lv];
+        const CoarseC<E> &C = cl[lv];
         const PeelRec rc = C.rec[lv_s0[lv] + (s - lv_first[lv])];
         const int kout = rc.kout;
-        const dfloat *F = C.F + rc.foff + (int64_t)lv_rowoff[lv] * kout;
-        const dfloat *T = C.T + (int64_t)rc.trow * cols;
-        dfloat *fs = Fs + b * kcap * LDF, *ts = Ts + b * kcap * MAXC;
+        const E *F = C.F + rc.foff + (int64_t)lv_rowoff[lv] * kout;
+        const E *T = C.T + (int64_t)rc.trow * cols;
+        E *fs = Fs + b * kcap * LDF, *ts = Ts + b * kcap * MAXC;
         const int nf = rows * kout;
         for (int o = tid; o < GEMM64_ROWS * kout; o += 128) {
             if (o < nf) cp_async8(&fs[o], F + o);
-            else fs[o] = dfloat(0.0f, 0.0f);
+            else fs[o] = E(0);
         }
         for (int o = tid; o < kout * MAXC; o += 128) {
             const int u = o / MAXC, col = o - u * MAXC;
             if (col < cols) cp_async8(&ts[o], T + (int64_t)u * cols + col);
-            else ts[o] = dfloat(0.0f, 0.0f);
+            else ts[o] = E(0);
         }
         cp_async_commit();
         return kout;
     };
-    dfloat acc[4][CW];
+    E acc[4][CW];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < CW; ++j) acc[i][j] = dfloat(0.0f, 0.0f);
+        for (int j = 0; j < CW; ++j) acc[i][j] = E(0);
     unsigned long long nmac = 0;
     int kcur = S > 0 ? issue(0, 0) : 0;
     for (int s = 0; s < S; ++s) {
@@ -512,21 +435,17 @@ __global__ void __launch_bounds__(128) k_peel_gemm_df(const CoarseDF *cl, int nc
             cp_async_wait<0>();
         }
         __syncthreads();
-        const dfloat *fs = Fs + (s & 1) * kcap * LDF + rg * 4 * kcur, *ts = Ts + (s & 1) * kcap * MAXC;
+        const E *fs = Fs + (s & 1) * kcap * LDF + rg * 4 * kcur, *ts = Ts + (s & 1) * kcap * MAXC;
         // warps whose rows all lie past the chunk's last row skip the products
         for (int u = 0; u < (rg * 4 < rows ? kcur : 0); ++u) {
-            const dfloat fv[4] = {fs[u], fs[kcur + u], fs[2 * kcur + u], fs[3 * kcur + u]};
-            dfloat tv[CW];
+            const E fv[4] = {fs[u], fs[kcur + u], fs[2 * kcur + u], fs[3 * kcur + u]};
+            E tv[CW];
 #pragma unroll
-            for (int j2 = 0; j2 < CW / 2; ++j2) {
-                const float4 x = *reinterpret_cast<const float4 *>(&ts[u * MAXC + cg * CW + 2 * j2]);
-                tv[2 * j2] = dfloat(x.x, x.y);
-                tv[2 * j2 + 1] = dfloat(x.z, x.w);
-            }
+            for (int j = 0; j < CW; ++j) tv[j] = ts[u * MAXC + cg * CW + j];
 #pragma unroll
             for (int i = 0; i < 4; ++i)
 #pragma unroll
-                for (int j = 0; j < CW; ++j) acc[i][j] = df_fma(fv[i], tv[j], acc[i][j]);
+                for (int j = 0; j < CW; ++j) acc[i][j] = mac(fv[i], tv[j], acc[i][j]);
         }
         nmac += (unsigned long long)rows * kcur * cols;
         __syncthreads();  // stage s & 1 is refilled in step s + 1
@@ -540,7 +459,7 @@ __global__ void __launch_bounds__(128) k_peel_gemm_df(const CoarseDF *cl, int nc
 #pragma unroll
         for (int j = 0; j < CW; ++j) {
             const int col = cg * CW + j;
-            if (col < cols) out[col] -= df_to(acc[i][j]);
+            if (col < cols) out[col] -= widen(acc[i][j], 0.0);
         }
     }
     if (macs && tid == 0 && nmac) atomicAdd(macs, nmac);
@@ -587,11 +506,14 @@ static Err factors_df(Factors &f, cudaStream_t st) {
 }
 
 // the double-float update of one side, timed by CUDA events (hm_info.seconds_peel_update)
-static Err launch_update_df(hm_ctx *c, const pm::CoarseDF *tab, int ntab, int chi, const Coloring &g, const Cut &cl,
-                            const DBuf &item_tile, const DBuf &item_row, int64_t nitems, int cols, int r, double *OUT) {
+// the compact update (double-float, or FP64 in the FP64 mode), timed by CUDA
+// events and counting its multiply-adds
+template <typename E>
+static Err launch_update_c(hm_ctx *c, const pm::CoarseC<E> *tab, int ntab, int chi, const Coloring &g, const Cut &cl,
+                           const DBuf &item_tile, const DBuf &item_row, int64_t nitems, int cols, int r, double *OUT) {
     cudaStream_t st = c->st;
     const int maxc = cols <= 32 ? 32 : 64;
-    const size_t smem = 2 * (size_t)r * (pm::GEMM64_LDF + maxc) * sizeof(dfloat);
+    const size_t smem = 2 * (size_t)r * (pm::GEMM64_LDF + maxc) * sizeof(E);
     if (smem > 220 * 1024) return fail(HM_ENOTSUP, "peel: r x columns per colour too large");
     HM_TRY(ensure(c->peel_macs, sizeof(unsigned long long)));
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -601,18 +523,18 @@ static Err launch_update_df(hm_ctx *c, const pm::CoarseDF *tab, int ntab, int ch
     HM_CUDA(cudaEventRecord(e0, st));
     auto *macs = c->peel_macs.as<unsigned long long>();
     if (maxc == 32) {
-        HM_TRY(allow_smem(pm::k_peel_gemm_df<32>, (size_t)((int)smem)));
-        pm::k_peel_gemm_df<32><<<(unsigned)nitems, 128, smem, st>>>(
+        HM_TRY(allow_smem(pm::k_peel_gemm_df<32, E>, smem));
+        pm::k_peel_gemm_df<32, E><<<(unsigned)nitems, 128, smem, st>>>(
             tab, ntab, chi, g.pair_alpha.as<int>(), g.pair_color.as<int>(), cl.ent.as<int>(), item_tile.as<int64_t>(),
             item_row.as<int>(), nitems, cols, r, c->n, OUT, macs);
     } else {
-        HM_TRY(allow_smem(pm::k_peel_gemm_df<64>, (size_t)((int)smem)));
-        pm::k_peel_gemm_df<64><<<(unsigned)nitems, 128, smem, st>>>(
+        HM_TRY(allow_smem(pm::k_peel_gemm_df<64, E>, smem));
+        pm::k_peel_gemm_df<64, E><<<(unsigned)nitems, 128, smem, st>>>(
             tab, ntab, chi, g.pair_alpha.as<int>(), g.pair_color.as<int>(), cl.ent.as<int>(), item_tile.as<int64_t>(),
             item_row.as<int>(), nitems, cols, r, c->n, OUT, macs);
     }
     count_launch();
-    HM_LAUNCH("peel_gemm_df");
+    HM_LAUNCH("peel_gemm_compact");
     HM_CUDA(cudaEventRecord(e1, st));
     return ok();
 }
@@ -632,28 +554,6 @@ static Err launch_update(const pm::CoarseT<float> *tab, int ntab, int side, int 
                                                               cols, r, n, OUT);
     count_launch();
     HM_LAUNCH("peel_gemm");
-    return ok();
-}
-
-static Err launch_update(const pm::CoarseT<double> *tab, int ntab, int side, int chi, const Coloring &g,
-                         const Cut &cl, const DBuf &item_tile, const DBuf &item_row, int64_t nitems, int cols, int r,
-                         int64_t n, double *OUT, cudaStream_t st) {
-    const size_t smem = (size_t)r * (pm::GEMM64_LDF + (cols <= 32 ? 32 : 64)) * sizeof(double);
-    if (cols <= 32) {
-        HM_TRY(allow_smem(pm::k_peel_gemm64<32>, (size_t)((int)smem)));
-        pm::k_peel_gemm64<32><<<(unsigned)nitems, 128, smem, st>>>(tab, ntab, side, chi, g.pair_alpha.as<int>(),
-                                                                   g.pair_color.as<int>(), cl.ent.as<int>(),
-                                                                   item_tile.as<int64_t>(), item_row.as<int>(),
-                                                                   nitems, cols, r, n, OUT);
-    } else {
-        HM_TRY(allow_smem(pm::k_peel_gemm64<64>, (size_t)((int)smem)));
-        pm::k_peel_gemm64<64><<<(unsigned)nitems, 128, smem, st>>>(tab, ntab, side, chi, g.pair_alpha.as<int>(),
-                                                                   g.pair_color.as<int>(), cl.ent.as<int>(),
-                                                                   item_tile.as<int64_t>(), item_row.as<int>(),
-                                                                   nitems, cols, r, n, OUT);
-    }
-    count_launch();
-    HM_LAUNCH("peel_gemm64");
     return ok();
 }
 
@@ -704,7 +604,9 @@ template <> struct PeelData<dfloat> {
 
 template <typename R> static Err peel_level_t(hm_ctx *c, int level, bool leaf) {
     using PD = PeelData<R>;
-    constexpr bool kDF = std::is_same<R, dfloat>::value;  // compacted records + double-float update
+    // compacted T records and the record-driven update: double-float (spec
+    // precision) and FP64; the FP32-solve mode keeps the dense slot table
+    constexpr bool kDF = std::is_same<R, dfloat>::value || std::is_same<R, double>::value;
     const int l = leaf ? c->L : level;
     const int idx = leaf ? c->L + 1 : level;
     const Coloring &g = (!leaf && c->cur_tiles) ? *c->cur_tiles : c->colorings[idx];
@@ -766,7 +668,7 @@ template <typename R> static Err peel_level_t(hm_ctx *c, int level, bool leaf) {
     for (int side = 0; side < (leaf ? 1 : 2); ++side) {
         if (!leaf && !(c->peel_sides & (1 << side))) continue;  // uniform H^1 peels one side per stage
         std::vector<pm::CoarseT<R>> tab;
-        std::vector<pm::CoarseDF> dtab;
+        std::vector<pm::CoarseC<R>> dtab;
         std::vector<DBuf> keep;  // X, offsets, T, live flags and records of every coarse level
         for (size_t i = 0; i < js.size(); ++i) {
             const int j = js[i];
@@ -853,14 +755,14 @@ template <typename R> static Err peel_level_t(hm_ctx *c, int level, bool leaf) {
                 HM_LAUNCH("peel_T");
             }
             if (kDF) {
-                pm::CoarseDF d;
+                pm::CoarseC<R> d;
                 d.ent = cj.ent.as<int>();
                 d.pt2ent = cj.pt2ent.as<int>();
                 d.base = bases[i].as<int64_t>();
                 d.cnt = cntb.as<int>();
                 d.rec = recb.as<pm::PeelRec>();
-                d.F = reinterpret_cast<const dfloat *>(side ? PD::V(f) : PD::U(f));
-                d.T = reinterpret_cast<const dfloat *>(T.template as<R>());
+                d.F = side ? PD::V(f) : PD::U(f);
+                d.T = T.template as<R>();
                 dtab.push_back(d);
                 keep.push_back(std::move(recb));
                 keep.push_back(std::move(cntb));
@@ -875,12 +777,12 @@ template <typename R> static Err peel_level_t(hm_ctx *c, int level, bool leaf) {
         double *OUT = side ? c->cur.Z.as<double>() : c->cur.Y.as<double>();
         DBuf tabd;
         if constexpr (kDF) {
-            HM_TRY(alloc(tabd, dtab.size() * sizeof(pm::CoarseDF)));
-            HM_CUDA(cudaMemcpyAsync(tabd.p, dtab.data(), dtab.size() * sizeof(pm::CoarseDF), cudaMemcpyHostToDevice,
+            HM_TRY(alloc(tabd, dtab.size() * sizeof(pm::CoarseC<R>)));
+            HM_CUDA(cudaMemcpyAsync(tabd.p, dtab.data(), dtab.size() * sizeof(pm::CoarseC<R>), cudaMemcpyHostToDevice,
                                     st));
             if (nitems > 0)
-                HM_TRY(launch_update_df(c, tabd.as<pm::CoarseDF>(), (int)dtab.size(), chi, g, cl, item_tile, item_row,
-                                        nitems, cols, r, OUT));
+                HM_TRY(launch_update_c<R>(c, tabd.as<pm::CoarseC<R>>(), (int)dtab.size(), chi, g, cl, item_tile,
+                                          item_row, nitems, cols, r, OUT));
         } else {
             HM_TRY(alloc(tabd, tab.size() * sizeof(pm::CoarseT<R>)));
             HM_CUDA(cudaMemcpyAsync(tabd.p, tab.data(), tab.size() * sizeof(pm::CoarseT<R>), cudaMemcpyHostToDevice,
