@@ -359,11 +359,11 @@ hm_status hm_export(hm_ctx *ctx, int what, int level, void *host_buf, size_t *by
  * array of HM_APPLY_NOALLOC_SCRATCH_BYTES inside the library, which every GPU
  * that loads the library holds until the process exits.  A request that needs
  * more returns HM_ENOTSUP (use hm_apply).  The first call on a device looks up
- * that array's address (cudaGetSymbolAddress), so it should come before any
- * stream capture.  The offsets it needs are computed by hm_compress; the call
- * reads nothing back and is asynchronous on the context's stream, like
- * hm_apply.  All calls share the array: calls that overlap on the GPU race.  Arguments, results and the other errors are those
- * of hm_apply.
+ * that array's address (cudaGetSymbolAddress) and caches it.  The offsets it
+ * needs are computed by hm_compress; the call reads nothing back and is
+ * asynchronous on the context's stream, like hm_apply.  All calls share the
+ * array: calls that overlap on the GPU race.  Arguments, results and the other
+ * errors are those of hm_apply.
  */
 #define HM_APPLY_NOALLOC_SCRATCH_BYTES (64u << 20)
 hm_status hm_apply_noalloc(hm_ctx *ctx, const double *x_dev, double *y_dev, int64_t nrhs, int trans);

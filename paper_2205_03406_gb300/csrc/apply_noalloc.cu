@@ -13,11 +13,10 @@
 //
 // The first call on a device looks up the array's device address with
 // cudaGetSymbolAddress (with that device current: the call switches to the
-// context's device) and caches it, so that first call should come before any
-// stream capture.  The call is asynchronous on the context's stream.  Every
-// call shares the array: calls that overlap on the GPU (on different streams
-// or host threads) race on it.  Each call overwrites every part of the scratch
-// it reads, so nothing has to start at zero.
+// context's device) and caches it.  The call is asynchronous on the context's
+// stream.  Every call shares the array: calls that overlap on the GPU (on
+// different streams or host threads) race on it.  Each call overwrites every
+// part of the scratch it reads, so nothing has to start at zero.
 #include "apply_kernels.cuh"
 
 #include <mutex>
